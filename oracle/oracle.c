@@ -1,0 +1,322 @@
+/*
+ * oracle.c -- TEST INFRASTRUCTURE ONLY.  A plain, slow CPU statement of what
+ * the matcher computes, used to check the GPU library.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg may load this code; the
+ * library itself never does.  It shares no code, header or table with the GPU
+ * path: it reads the same node-array input format and nothing else.
+ *
+ * Rathnayake & Thielecke, "Regular Expression Matching and Operational
+ * Semantics" (SOS 2011):
+ *
+ *   O1  -- the big-step matching relation e |v w of Fig 2.1 (rules Seq, Match,
+ *          Epsilon, Kleene1, Kleene2, Alt1, Alt2), read as the least relation
+ *          closed under the rules, memoised over (node, start index).
+ *   O2  -- the sequential lockstep machine <c; t; n; w> of Def 6.2 / Fig 6.1
+ *          with the add-unique function psi of Def 6.1, over the pointer tree
+ *          of Section 4 with the cont function of Def 4.4.
+ *   cont -- Def 4.4, computed by a walk from the root.
+ *
+ * Node array format (input interface, 12 bytes per node): kind u8 (0 CHAR,
+ * 1 EPS, 2 STAR, 3 CAT, 4 ALT), byte u8, pad u16, l i32, r i32.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <omp.h>
+
+enum { CHAR = 0, EPS = 1, STAR = 2, CAT = 3, ALT = 4 };
+
+typedef struct {
+    uint8_t kind, byte;
+    uint16_t pad;
+    int32_t l, r;
+} or_node;
+
+#define NUL (-1) /* the distinguished address null */
+
+/* ------------------------------------------------------------- cont (Def 4.4)
+ * cont(root) = null; for p1|p2 both children inherit cont(p); for p1.p2,
+ * cont(p1) = p2 and cont(p2) = cont(p); for p1*, cont(p1) = p.
+ * Returns 0, or -1 if a child index is out of range. */
+int or_cont(const or_node* nd, int nn, int root, int32_t* cont) {
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nn + 1));
+    if (!stack) return -1;
+    for (int i = 0; i < nn; i++) cont[i] = NUL;
+    int sp = 0;
+    stack[sp++] = root;
+    cont[root] = NUL;
+    int rc = 0, visits = 0;
+    while (sp > 0) {
+        int p = stack[--sp];
+        if (++visits > nn) { rc = -1; break; }
+        const or_node* x = &nd[p];
+        if (x->kind == ALT) {
+            if (x->l < 0 || x->l >= nn || x->r < 0 || x->r >= nn) { rc = -1; break; }
+            cont[x->l] = cont[p];
+            cont[x->r] = cont[p];
+            stack[sp++] = x->l;
+            stack[sp++] = x->r;
+        } else if (x->kind == CAT) {
+            if (x->l < 0 || x->l >= nn || x->r < 0 || x->r >= nn) { rc = -1; break; }
+            cont[x->l] = x->r;
+            cont[x->r] = cont[p];
+            stack[sp++] = x->l;
+            stack[sp++] = x->r;
+        } else if (x->kind == STAR) {
+            if (x->l < 0 || x->l >= nn) { rc = -1; break; }
+            cont[x->l] = p;
+            stack[sp++] = x->l;
+        }
+    }
+    free(stack);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ O1
+ * ends(e, i) = { j : e |v w[i..j) } as an (L+1)-bit set, for every node e and
+ * every start i, computed for i = L down to 0 with children before parents:
+ *   Match   a      : { i+1 } if i < L and w[i] = a, else {}
+ *   Epsilon        : { i }
+ *   Alt1/2  e1|e2  : ends(e1,i) U ends(e2,i)
+ *   Seq     e1 e2  : U_{k in ends(e1,i)} ends(e2,k)          (k >= i)
+ *   Kleene2 e*     : { i }
+ *   Kleene1 e*     : U_{k in ends(e,i)} ends(e*,k)
+ * In Kleene1 the term k = i is ends(e*,i) itself; under the least-relation
+ * reading it adds nothing, so only k > i (already computed) contributes.
+ * e |v w  iff  L in ends(root, 0).
+ * Returns 1 / 0, or -1 when the tables would exceed max_bytes. */
+static int postorder(const or_node* nd, int nn, int root, int32_t* order) {
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * nn + 2));
+    if (!stack) return -1;
+    int sp = 0, k = 0;
+    stack[sp++] = root;
+    /* reverse of a (node, right, left) preorder is a valid children-first order */
+    while (sp > 0) {
+        int p = stack[--sp];
+        if (k >= nn) { free(stack); return -1; }
+        order[k++] = p;
+        const or_node* x = &nd[p];
+        if (x->kind == CAT || x->kind == ALT) {
+            stack[sp++] = x->l;
+            stack[sp++] = x->r;
+        } else if (x->kind == STAR) {
+            stack[sp++] = x->l;
+        }
+    }
+    free(stack);
+    for (int a = 0, b = k - 1; a < b; a++, b--) {
+        int32_t t = order[a];
+        order[a] = order[b];
+        order[b] = t;
+    }
+    return k;
+}
+
+int or_o1(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, int64_t max_bytes) {
+    int64_t words = (L + 1 + 63) / 64;
+    int64_t need = (int64_t)nn * (L + 1) * words * 8;
+    if (need > max_bytes) return -1;
+    uint64_t* E = (uint64_t*)calloc((size_t)need / 8, 8);
+    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)nn);
+    if (!E || !order) { free(E); free(order); return -1; }
+    int k = postorder(nd, nn, root, order);
+    if (k < 0) { free(E); free(order); return -1; }
+#define ENDS(e, i) (E + (((int64_t)(e) * (L + 1) + (i)) * words))
+#define SETB(s, j) ((s)[(j) >> 6] |= 1ULL << ((j) & 63))
+#define GETB(s, j) (((s)[(j) >> 6] >> ((j) & 63)) & 1ULL)
+    for (int64_t i = L; i >= 0; i--) {
+        for (int q = 0; q < k; q++) {
+            int e = order[q];
+            const or_node* x = &nd[e];
+            uint64_t* dst = ENDS(e, i);
+            switch (x->kind) {
+            case CHAR:
+                if (i < L && w[i] == x->byte) SETB(dst, i + 1);
+                break;
+            case EPS:
+                SETB(dst, i);
+                break;
+            case ALT: {
+                uint64_t *a = ENDS(x->l, i), *b = ENDS(x->r, i);
+                for (int64_t z = 0; z < words; z++) dst[z] = a[z] | b[z];
+                break;
+            }
+            case CAT: {
+                uint64_t* a = ENDS(x->l, i);
+                for (int64_t kk = i; kk <= L; kk++)
+                    if (GETB(a, kk)) {
+                        uint64_t* b = ENDS(x->r, kk);
+                        for (int64_t z = 0; z < words; z++) dst[z] |= b[z];
+                    }
+                break;
+            }
+            case STAR: {
+                SETB(dst, i);
+                uint64_t* a = ENDS(x->l, i);
+                for (int64_t kk = i + 1; kk <= L; kk++)
+                    if (GETB(a, kk)) {
+                        uint64_t* b = ENDS(e, kk);
+                        for (int64_t z = 0; z < words; z++) dst[z] |= b[z];
+                    }
+                break;
+            }
+            }
+        }
+    }
+    int res = (int)GETB(ENDS(root, 0), L);
+#undef ENDS
+#undef SETB
+#undef GETB
+    free(E);
+    free(order);
+    return res;
+}
+
+/* ------------------------------------------------------------------ O2
+ * Lists are stacks whose head is the last array element.  NUL is stored as
+ * the id nn.  psi(p, l1, l2) = p::l1 if p not in l1@l2, else l1 (Def 6.1),
+ * tested by a linear scan of both lists.
+ *
+ * Fig 6.1, rule by rule (c = p::c'):
+ *   p = p1|p2 : c := psi(p2, psi(p1, c', t), t);          t := p::t
+ *   p = p1.p2 : c := psi(p1, c', t);                      t := p::t
+ *   p = p1*   : c := psi(cont p, psi(p1, c', t), t);      t := p::t
+ *               (the figure prints psi(p, ...) in the inner call; the child
+ *                p1 is meant -- Fig 4.2 moves a star to its child and to its
+ *                continuation, and the process translation of Section 7 sends
+ *                to both -- with p itself the star would never reach p1)
+ *   p = eps   : c := psi(cont p, c', t);                  t := p::t
+ *   p = null, input a w        : c := c'                 (dropped)
+ *   p = a,    input a w        : n := psi(cont p, n, []); t := p::t
+ *   p = b,    input a w, b!=a  : t := p::t                (dropped)
+ *   p = a,    input empty      : t := p::t                (dropped)
+ *   c = [], input a w, n != [] : c := n; t := []; n := []; input := w
+ * Accepting: null at the head of c with the input empty.  Anything else
+ * with no applicable rule is stuck, i.e. rejects.
+ *
+ * trace (optional, L+1 rows of nn+1 bytes each): row k marks the CHAR
+ * nodes popped during macro step k (the evolved set of Def 5.1) and, in
+ * column nn, whether null was popped.  In trace mode the last macro step
+ * keeps evolving after null is found, so its row is complete.
+ * ntrace (optional, L rows of nn+1 bytes): the list n handed to macro step
+ * k+1, i.e. the set S' of Def 5.2 after reading w[k]. */
+typedef struct {
+    int32_t* a;
+    int len;
+} olist;
+
+static int in_list(const olist* l, int32_t p) {
+    for (int i = 0; i < l->len; i++)
+        if (l->a[i] == p) return 1;
+    return 0;
+}
+/* l1 := psi(p, l1, l2) */
+static void psi(int32_t p, olist* l1, const olist* l2) {
+    if (in_list(l1, p) || in_list(l2, p)) return;
+    l1->a[l1->len++] = p;
+}
+
+static int o2_run(const or_node* nd, int nn, int root, const int32_t* cont, const uint8_t* w, int64_t L,
+                  uint8_t* trace, uint8_t* ntrace, int32_t* buf) {
+    /* every list holds distinct ids from [0, nn]; give each nn+1 slots (plus
+     * slack for null, which can be re-pushed after being dropped) */
+    int cap = 2 * (nn + 1);
+    olist c = {buf, 0}, t = {buf + cap, 0}, n = {buf + 2 * cap, 0}, empty = {NULL, 0};
+    int32_t nul = nn;
+    int accept = 0;
+    int64_t pos = 0;
+    c.a[c.len++] = root;
+    for (;;) {
+        if (c.len > 0) {
+            int32_t p = c.a[--c.len];
+            if (p == nul) {
+                if (trace) trace[pos * (nn + 1) + nn] = 1;
+                if (pos == L) {
+                    accept = 1;
+                    if (!trace) return 1;
+                }
+                continue;
+            }
+            const or_node* x = &nd[p];
+            int32_t k = cont[p] < 0 ? nul : cont[p];
+            switch (x->kind) {
+            case ALT:
+                psi(x->l, &c, &t);
+                psi(x->r, &c, &t);
+                break;
+            case CAT:
+                psi(x->l, &c, &t);
+                break;
+            case STAR:
+                psi(x->l, &c, &t);
+                psi(k, &c, &t);
+                break;
+            case EPS:
+                psi(k, &c, &t);
+                break;
+            case CHAR:
+                if (trace) trace[pos * (nn + 1) + p] = 1;
+                if (pos < L && w[pos] == x->byte) psi(k, &n, &empty);
+                break;
+            }
+            t.a[t.len++] = p;
+            continue;
+        }
+        /* c = [] */
+        if (pos < L && n.len > 0) {
+            if (ntrace)
+                for (int i = 0; i < n.len; i++) ntrace[pos * (nn + 1) + n.a[i]] = 1;
+            memcpy(c.a, n.a, sizeof(int32_t) * (size_t)n.len);
+            c.len = n.len;
+            t.len = 0;
+            n.len = 0;
+            pos++;
+            continue;
+        }
+        return accept; /* stuck */
+    }
+}
+
+int or_o2(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, uint8_t* trace, uint8_t* ntrace) {
+    int32_t* cont = (int32_t*)malloc(sizeof(int32_t) * (size_t)nn);
+    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(6 * (nn + 1)));
+    if (!cont || !buf || or_cont(nd, nn, root, cont) != 0) { free(cont); free(buf); return -1; }
+    int r = o2_run(nd, nn, root, cont, w, L, trace, ntrace, buf);
+    free(cont);
+    free(buf);
+    return r;
+}
+
+/* ------------------------------------------------------------ batches
+ * One expression against n strings (bytes + offsets[n+1]); out[i] = 0/1, or
+ * 255 when O1 declined (tables too large).  Plain loop over strings, spread
+ * over nthreads OpenMP threads (0 = runtime default). */
+int or_o2_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const int64_t* off, int64_t n,
+                uint8_t* out, int nthreads) {
+    int32_t* cont = (int32_t*)malloc(sizeof(int32_t) * (size_t)nn);
+    if (!cont || or_cont(nd, nn, root, cont) != 0) { free(cont); return -1; }
+    int failed = 0;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    {
+        int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(6 * (nn + 1)));
+        if (!buf) failed = 1;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; i++) {
+            if (!buf) continue;
+            out[i] = (uint8_t)o2_run(nd, nn, root, cont, bytes + off[i], off[i + 1] - off[i], NULL, NULL, buf);
+        }
+        free(buf);
+    }
+    free(cont);
+    return failed ? -1 : 0;
+}
+
+int or_o1_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const int64_t* off, int64_t n,
+                uint8_t* out, int64_t max_bytes, int nthreads) {
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    for (int64_t i = 0; i < n; i++) {
+        int r = or_o1(nd, nn, root, bytes + off[i], off[i + 1] - off[i], max_bytes);
+        out[i] = (uint8_t)(r < 0 ? 255 : r);
+    }
+    return 0;
+}
