@@ -1,0 +1,317 @@
+/*
+ * rx.h -- C ABI of the B300 lockstep regular-expression matcher.
+ *
+ * The library decides whole-string membership  e |v w  (Rathnayake &
+ * Thielecke, "Regular Expression Matching and Operational Semantics",
+ * SOS 2011, Section 2, Fig 2.1) for expressions over the byte alphabet
+ *     e ::= eps | a | e* | e1 e2 | e1 | e2          (Section 2)
+ * by the lockstep construction of Section 5: the expression is laid out as a
+ * pointer tree with continuation pointers (Section 4, Defs 4.1-4.4), every
+ * input byte advances the whole set of active tree positions at once
+ * (Def 5.2), and the evolution of Def 5.1 is deduplicated by node identity
+ * (pointer equality, Section 3).  A string is accepted when null is in the
+ * evolved set after the last byte (Def 5.3).
+ *
+ * Conventions for every entry point:
+ *   - No C++ exception crosses this boundary; every call that can fail
+ *     returns an rx_status, and rx_last_error() returns a thread-local
+ *     message describing the most recent failure on the calling thread.
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary (pageable or pinned) memory.
+ *   - Streams are cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls marked "async" only enqueue work on that stream; the
+ *     caller synchronises before reading results.
+ *   - Handles are owned by the library and released with rx_free(); all
+ *     other buffers are owned by the caller.
+ */
+#ifndef RX_H
+#define RX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- basic types */
+typedef enum {
+    RX_OK = 0,
+    RX_ERR_PARSE = 1,        /* pattern text is not in the syntax below        */
+    RX_ERR_INVALID_ARG = 2,  /* null pointer, bad size, malformed tree/offsets */
+    RX_ERR_TOO_LARGE = 3,    /* more nodes/positions than the limits below     */
+    RX_ERR_OOM = 4,          /* host or device allocation failed               */
+    RX_ERR_CUDA = 5,         /* a CUDA runtime call failed                     */
+    RX_ERR_TIMEOUT = 6,      /* a bounded device or host wait gave up          */
+    RX_ERR_BUSY = 7,         /* serving queue full; retry after rx_serve_poll   */
+    RX_ERR_UNSUPPORTED = 8   /* the requested variant cannot run this handle   */
+} rx_status;
+
+/* Node kinds of the abstract syntax of Section 2. */
+enum { RX_CHAR = 0, RX_EPS = 1, RX_STAR = 2, RX_CAT = 3, RX_ALT = 4 };
+
+/* One node of the heap pi of Section 4 (Def 4.3): kind, the byte of a CHAR
+ * node, and child indices l, r (-1 when absent: CHAR/EPS have none, STAR has
+ * only l).  12 bytes, little-endian, no padding beyond `pad`. */
+typedef struct {
+    uint8_t kind;
+    uint8_t byte;
+    uint16_t pad;
+    int32_t l;
+    int32_t r;
+} rx_node;
+
+typedef struct rx_regex* rx_handle;
+
+/* Limits.  Positions are the CHAR leaves of the tree (the elements the
+ * active set ranges over); the active set has positions+1 bits (null). */
+#define RX_MAX_NODES 65536
+#define RX_MAX_POSITIONS 4095
+
+/* Kernel variants (see rx_match_ex).  AUTO lets the library choose. */
+typedef enum {
+    RX_VARIANT_AUTO = 0,
+    RX_VARIANT_MEMO = 1,   /* cached macro steps: one table lookup per byte      */
+    RX_VARIANT_THREAD = 2, /* one thread per string, register bitset (<= 63 pos) */
+    RX_VARIANT_SPARSE = 3, /* one thread per string, bitset words + follow rows  */
+    RX_VARIANT_WARP = 4,   /* one warp per string, lane-owned bitset words       */
+    RX_VARIANT_PAPER = 5   /* Section 8's machine: one thread per node, c/n
+                              stamp vectors, one launch per micro-step          */
+} rx_variant;
+
+/* compile flags */
+#define RX_COMPILE_HOST_ONLY 1u /* build host tables only; the handle cannot be
+                                   matched (used to inspect the compiler)  */
+#define RX_COMPILE_NO_MEMO 2u   /* do not build the macro-step cache       */
+
+typedef struct {
+    int32_t nodes;        /* nodes reachable from the root                  */
+    int32_t positions;    /* m: CHAR leaves                                  */
+    int32_t words;        /* 32-bit words of the active-set bitset           */
+    int32_t nullable;     /* 1 iff the expression matches the empty string   */
+    int32_t memo_states;  /* cached macro-step states, 0 if no cache         */
+    uint32_t variants;    /* bit v set iff rx_variant v can run this handle  */
+    int64_t device_bytes; /* device memory held by the handle                */
+} rx_info_t;
+
+/* --------------------------------------------------------------- compiling */
+/*
+ * rx_compile -- parse pattern text into the pointer tree of Section 4, wire
+ * cont (Def 4.4), precompute the evolutions of Def 5.1 (one depth-first walk
+ * per continuation target, deduplicated by node id), build the per-byte
+ * successor tables of Def 5.2, and upload them to the current device.
+ *
+ * Text syntax (the paper fixes none): '|' binds loosest, then juxtaposition,
+ * then postfix '*'; both binary operators associate to the left.
+ * Parentheses group; an empty alternative or "()" is eps, as is "\e".
+ * "\xHH" is the byte 0xHH; "\" before any other byte is that byte literally
+ * (so "\|", "\*", "\(", "\)", "\\").  Every other byte stands for itself.
+ *
+ *   pat      host, len bytes (need not be NUL-terminated)
+ *   flags    RX_COMPILE_* bits
+ *   out      receives the handle (library-owned; release with rx_free)
+ *   err_pos  optional; on RX_ERR_PARSE receives the byte offset of the error
+ * Errors: RX_ERR_PARSE, RX_ERR_TOO_LARGE (limits above), RX_ERR_OOM,
+ * RX_ERR_CUDA.  On error *out is set to NULL.
+ */
+rx_status rx_compile(const char* pat, size_t len, uint32_t flags, rx_handle* out, size_t* err_pos);
+
+/*
+ * rx_compile_ast -- as rx_compile, from a node array (host).  The tree is
+ * the part reachable from `root`; it must be a tree (no node reachable
+ * twice, no cycles: the disjointness of Def 4.3) with valid child indices.
+ * Nodes not reachable from the root are ignored.
+ * Errors: RX_ERR_INVALID_ARG for malformed trees, otherwise as rx_compile.
+ */
+rx_status rx_compile_ast(const rx_node* nodes, size_t n, int32_t root, uint32_t flags, rx_handle* out);
+
+/* rx_info -- sizes of a compiled handle.  Errors: RX_ERR_INVALID_ARG. */
+rx_status rx_info(rx_handle h, rx_info_t* out);
+
+/* rx_free -- release a handle and its device tables (NULL is ignored).
+ * The caller must ensure no enqueued work still uses the handle. */
+void rx_free(rx_handle h);
+
+/*
+ * rx_tables -- host copies of the compiled tables, for inspection.  Any
+ * output pointer may be NULL.  Bit b of an active set is word b/32, bit b%32.
+ *   cont      [nodes]        cont of each node (Def 4.4), -1 = null, indexed
+ *                            by the preorder ids of rx_tree
+ *   pos_node  [positions]    preorder id of each position, left-to-right order
+ *   pos_bit   [positions]    bitset index of each position
+ *   null_bit                 bitset index of null
+ *   start     [words]        evolution of {root} (Def 5.1, with null)
+ *   follow    [positions*words] evolution of {cont p} for position p
+ *                            (left-to-right order), with null
+ * Errors: RX_ERR_INVALID_ARG.
+ */
+rx_status rx_tables(rx_handle h, int32_t* cont, int32_t* pos_node, int32_t* pos_bit, int32_t* null_bit,
+                    uint32_t* start, uint32_t* follow);
+
+/*
+ * rx_tree -- the tree a handle was compiled from, renumbered in preorder
+ * (root = node 0; for rx_compile this is the parsed pattern).  Writes up
+ * to cap nodes to out (host) and the node count to *n.
+ * Errors: RX_ERR_INVALID_ARG.
+ */
+rx_status rx_tree(rx_handle h, rx_node* out, size_t cap, size_t* n);
+
+/* ---------------------------------------------------------------- matching */
+/*
+ * rx_match -- one expression against n strings (async).  out[i] = 1 iff
+ * e |v w_i, else 0, where w_i = strings[offsets[i] .. offsets[i+1]).
+ *   strings  device, offsets[n] bytes, packed
+ *   offsets  device, n+1 int64, non-decreasing, offsets[0] >= 0
+ *   out      device, n bytes
+ * The input bytes are read once; a string whose active set empties is not
+ * read further (it is stuck, Fig 6.1).  Offsets are NOT validated on the
+ * device: decreasing offsets are undefined behaviour.  Scratch space is
+ * library-owned per stream and grows on demand (may synchronise the stream
+ * the first time a larger batch is seen).
+ * Errors: RX_ERR_INVALID_ARG (NULL pointers with n > 0, host-only handle),
+ * RX_ERR_OOM, RX_ERR_CUDA (launch failure).
+ */
+rx_status rx_match(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                   void* stream);
+
+typedef struct {
+    int32_t variant;    /* rx_variant; AUTO = library choice                 */
+    int32_t block;      /* threads per block, 0 = default                    */
+    int32_t sort;       /* -1 = auto, 0 = no length sort, 1 = sort by length */
+    int32_t reserved;
+} rx_match_opts;
+
+/* rx_match_ex -- rx_match with an explicit variant / launch shape.
+ * Errors: as rx_match, plus RX_ERR_UNSUPPORTED when the variant cannot run
+ * this handle (see rx_info_t.variants). */
+rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                      void* stream, const rx_match_opts* opts);
+
+/*
+ * rx_match_batch -- n (expression, string) pairs in one persistent launch
+ * (async).  handles is a HOST array of n handles (pair i uses handles[i]);
+ * strings/offsets/out as in rx_match.  Pairs are bucketed by variant and
+ * length, ordered longest first, and drained by a device work queue; the
+ * queue and the tables of all distinct handles are uploaded once per call.
+ * Errors: as rx_match.
+ */
+rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
+                         uint8_t* out, void* stream);
+
+/*
+ * rx_match_pairs -- the plain form: one kernel launch per pair, in order
+ * (async).  Same arguments and result as rx_match_batch; kept as the
+ * comparison point for the batched form.
+ */
+rx_status rx_match_pairs(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
+                         uint8_t* out, void* stream);
+
+/*
+ * rx_match_long -- one long string, exact chunked mode (async).  The input
+ * is cut into chunks; for each chunk the transfer function of the macro
+ * step (Def 5.2) over the chunk is computed in parallel from every possible
+ * incoming state -- exact because a macro step maps a set to the union of
+ * the images of its elements ("exists p in S", Defs 5.1, 5.2) -- and the
+ * functions are composed starting from the evolution of {root}.
+ *   str          device, len bytes
+ *   chunk_bytes  chunk size, 0 = automatic; any value >= 1 is valid
+ *   out          device, 1 byte: 1 iff e |v str
+ * Errors: as rx_match.
+ */
+rx_status rx_match_long(rx_handle h, const uint8_t* str, int64_t len, int64_t chunk_bytes, uint8_t* out,
+                        void* stream);
+
+/*
+ * rx_match_seq -- one string, one thread, sequential lockstep (async); the
+ * reference point for rx_match_long.  Arguments as rx_match_long.
+ */
+rx_status rx_match_seq(rx_handle h, const uint8_t* str, int64_t len, uint8_t* out, void* stream);
+
+/*
+ * rx_trace -- the active set after every byte (async; debugging aid).
+ * frontiers (device) receives (len+1) rows of `words` uint32: row k is the
+ * evolved set (Def 5.1) before reading str[k], null included; row len is
+ * the set after the last byte (null bit set iff the string is accepted).
+ * The set is not cut short when it empties.  Errors: as rx_match.
+ */
+rx_status rx_trace(rx_handle h, const uint8_t* str, int64_t len, uint32_t* frontiers, void* stream);
+
+/* ----------------------------------------------------------------- serving */
+typedef struct {
+    int64_t device_budget_bytes; /* admission cap on device bytes held by
+                                    in-flight requests (0 = 1/4 of free)   */
+    int32_t max_inflight;        /* concurrent requests on the device      */
+    int32_t queue_capacity;      /* pending requests before RX_ERR_BUSY    */
+    int64_t tick_bytes;          /* bytes each in-flight request advances
+                                    per device tick                        */
+    int32_t device_payload;      /* 1: submit() bytes are device pointers  */
+    int32_t reserved;
+} rx_serve_cfg;
+
+typedef struct {
+    uint64_t submitted, completed;
+    double p50_ns, p99_ns, p999_ns, max_ns; /* submit -> result latency */
+    double req_per_s, gb_per_s;             /* over the completed requests */
+    int64_t ticks;
+    int64_t peak_inflight;
+    int64_t peak_device_bytes;
+} rx_serve_stats_t;
+
+typedef struct rx_server rx_server;
+
+/* rx_serve_create -- start a continuous-batching server on the current
+ * device (its own host thread and CUDA stream).  Errors: RX_ERR_INVALID_ARG,
+ * RX_ERR_OOM, RX_ERR_CUDA. */
+rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out);
+
+/* rx_serve_submit -- enqueue one match (thread-safe).  `bytes` is host
+ * memory (copied before the call returns) unless cfg.device_payload, in
+ * which case it is a device pointer that must stay valid until the result
+ * is polled.  The handle must outlive the request.  *ticket identifies the
+ * result.  Errors: RX_ERR_BUSY (queue full), RX_ERR_INVALID_ARG, RX_ERR_OOM. */
+rx_status rx_serve_submit(rx_server* s, rx_handle h, const uint8_t* bytes, int64_t len, uint64_t* ticket);
+
+/* rx_serve_poll -- collect up to max finished requests (thread-safe);
+ * returns how many were written.  results[i] is 0/1, st[i] the status of
+ * that request. */
+size_t rx_serve_poll(rx_server* s, uint64_t* tickets, uint8_t* results, rx_status* st, size_t max);
+
+/* rx_serve_drain -- wait until every submitted request has completed, up
+ * to timeout_ms.  Errors: RX_ERR_TIMEOUT. */
+rx_status rx_serve_drain(rx_server* s, int64_t timeout_ms);
+
+rx_status rx_serve_stats(rx_server* s, rx_serve_stats_t* out);
+
+/* rx_serve_destroy -- stop the server thread, free its device memory.
+ * Outstanding requests are cancelled. */
+rx_status rx_serve_destroy(rx_server* s);
+
+/* -------------------------------------------------------------- profiling */
+/*
+ * rx_profile_enable -- opt-in timing of the lockstep kernels (off by
+ * default).  While on, every launch of a main lockstep kernel (the
+ * per-string, per-pair and chunk kernels, not the planners) is bracketed by
+ * two CUDA events recorded on the stream it is launched on.  Every kernel
+ * launch of the library is counted whether or not timing is on.
+ */
+rx_status rx_profile_enable(int on);
+
+/*
+ * rx_profile_read -- launches counted since the last read (all library
+ * kernels), and for the timed main kernels their count and summed device
+ * time in milliseconds (waits for the recorded events).  Resets both.
+ * Any pointer may be NULL.  Errors: RX_ERR_CUDA.
+ */
+rx_status rx_profile_read(int64_t* launches, int64_t* timed, double* kernel_ms);
+
+/* ------------------------------------------------------------------- misc */
+/* Thread-local description of the last error (never NULL). */
+const char* rx_last_error(void);
+
+/* Library version string. */
+const char* rx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RX_H */

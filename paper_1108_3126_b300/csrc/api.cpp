@@ -1,0 +1,416 @@
+// api.cpp -- the C ABI of include/rx.h: handles, device upload, per-stream
+// scratch, argument checks and dispatch to the kernels.  No exception
+// crosses the boundary: every entry point catches and returns a status.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "kernels.cuh"
+#include "rx_internal.h"
+
+namespace rx {
+
+namespace {
+thread_local std::string g_last_error = "no error";
+
+size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// per-(device, stream) scratch, grown on demand
+struct WsKey {
+    int dev;
+    cudaStream_t st;
+    bool operator<(const WsKey& o) const { return dev != o.dev ? dev < o.dev : st < o.st; }
+};
+std::mutex g_ws_mu;
+std::map<WsKey, Workspace> g_ws;
+
+rx_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return RX_ERR_CUDA;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Scratch of at least `bytes` for this stream (the buffer stays owned by the
+// library; callers on the same stream are ordered by the stream).
+rx_status get_workspace(cudaStream_t st, size_t bytes, void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    Workspace& w = g_ws[WsKey{dev, st}];
+    if (w.bytes < bytes) {
+        if (w.base) {
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(w.base);
+            w.base = nullptr;
+            w.bytes = 0;
+        }
+        size_t want = std::max<size_t>(bytes, 1 << 20);
+        want = (want + (1 << 20) - 1) & ~size_t((1 << 20) - 1);
+        e = cudaMalloc(&w.base, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("scratch allocation failed");
+            return RX_ERR_OOM;
+        }
+        w.bytes = want;
+        w.stream = st;
+        w.device = dev;
+    }
+    *out = w.base;
+    return RX_OK;
+}
+
+static rx_status upload(rx_regex* h) {
+    Compiled& C = h->host;
+    const int W = C.W;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += a16(b);
+        return o;
+    };
+    size_t o_start = take(W * 4), o_B = take((size_t)256 * W * 4), o_fol = take((size_t)C.nbits * W * 4);
+    size_t o_desc = take(256 * sizeof(uint2)), o_tt = take(std::max<size_t>(C.gl_tt.size(), 1) * 4);
+    size_t o_T = take(std::max<size_t>(C.memo_T.size(), 1) * 4), o_acc = take(std::max<size_t>(C.memo_acc.size(), 1));
+    size_t o_nd = take(C.nodes.size() * sizeof(int4));
+    size_t total = off;
+    std::vector<uint8_t> blob(total, 0);
+    auto put = [&](size_t o, const void* p, size_t b) {
+        if (b) std::memcpy(blob.data() + o, p, b);
+    };
+    put(o_start, C.start.data(), W * 4);
+    put(o_B, C.B.data(), C.B.size() * 4);
+    put(o_fol, C.follow_bit.data(), C.follow_bit.size() * 4);
+    put(o_desc, C.gl_desc.data(), 256 * sizeof(uint2));
+    put(o_tt, C.gl_tt.data(), C.gl_tt.size() * 4);
+    put(o_T, C.memo_T.data(), C.memo_T.size() * 4);
+    put(o_acc, C.memo_acc.data(), C.memo_acc.size());
+    std::vector<int4> pn(C.nodes.size());
+    for (size_t i = 0; i < C.nodes.size(); i++)
+        pn[i] = make_int4((int)C.nodes[i].kind | ((int)C.nodes[i].byte << 8), C.nodes[i].l, C.nodes[i].r, C.cont[i]);
+    put(o_nd, pn.data(), pn.size() * sizeof(int4));
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaMalloc(&h->dev_blob, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->dev_blob = nullptr;
+        set_error("device allocation for tables failed");
+        return RX_ERR_OOM;
+    }
+    e = cudaMemcpy(h->dev_blob, blob.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy tables");
+    h->dev_bytes = (int64_t)total;
+    uint8_t* b = static_cast<uint8_t*>(h->dev_blob);
+    DevTables& t = h->dev;
+    t.m = C.m;
+    t.W = W;
+    t.nbits = C.nbits;
+    t.null_bit = C.null_bit;
+    t.start = reinterpret_cast<const uint32_t*>(b + o_start);
+    t.B = reinterpret_cast<const uint32_t*>(b + o_B);
+    t.follow = reinterpret_cast<const uint32_t*>(b + o_fol);
+    t.gl_desc = reinterpret_cast<const uint2*>(b + o_desc);
+    t.gl_tt = reinterpret_cast<const uint32_t*>(b + o_tt);
+    t.gl_words = C.gl_ok ? (int32_t)C.gl_tt.size() : 0;
+    t.memo_K = C.memo_K;
+    t.memo_T = reinterpret_cast<const uint32_t*>(b + o_T);
+    t.memo_acc = b + o_acc;
+    t.memo_start = C.memo_start;
+    t.variants = C.variants;
+    t.nullable = C.nullable ? 1 : 0;
+    t.nn = (int32_t)C.nodes.size();
+    t.pnodes = reinterpret_cast<const int4*>(b + o_nd);
+    t.proot = 0;
+    return RX_OK;
+}
+
+static rx_status finish_compile(rx_regex* h, uint32_t flags) {
+    if (flags & RX_COMPILE_HOST_ONLY) {
+        h->host_only = true;
+        return RX_OK;
+    }
+    return upload(h);
+}
+
+int resolve_variant(const rx_regex* h, int v) {
+    if (v != RX_VARIANT_AUTO) return v;
+    uint32_t ok = h->host.variants;
+    if (ok & (1u << RX_VARIANT_MEMO)) return RX_VARIANT_MEMO;
+    if (ok & (1u << RX_VARIANT_THREAD)) return RX_VARIANT_THREAD;
+    if (ok & (1u << RX_VARIANT_SPARSE)) return RX_VARIANT_SPARSE;
+    return RX_VARIANT_WARP;
+}
+
+}  // namespace rx
+
+using namespace rx;
+
+#define RX_GUARD_BEGIN try {
+#define RX_GUARD_END                                  \
+    }                                                 \
+    catch (const std::bad_alloc&) {                   \
+        set_error("host allocation failed");          \
+        return RX_ERR_OOM;                            \
+    }                                                 \
+    catch (const std::exception& ex) {                \
+        set_error(std::string("internal: ") + ex.what()); \
+        return RX_ERR_INVALID_ARG;                    \
+    }                                                 \
+    catch (...) {                                     \
+        set_error("internal error");                  \
+        return RX_ERR_INVALID_ARG;                    \
+    }
+
+extern "C" {
+
+const char* rx_last_error(void) { return g_last_error.c_str(); }
+
+const char* rx_version(void) { return "rx-b300 0.1 (sm_103a)"; }
+
+rx_status rx_compile(const char* pat, size_t len, uint32_t flags, rx_handle* out, size_t* err_pos) {
+    RX_GUARD_BEGIN
+    if (!out || (!pat && len)) {
+        set_error("rx_compile: null argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    std::vector<rx_node> nodes;
+    size_t ep = 0;
+    std::string msg;
+    rx_status s = parse_pattern(pat ? pat : "", len, nodes, ep, msg);
+    if (s != RX_OK) {
+        if (err_pos) *err_pos = ep;
+        set_error(msg);
+        return s;
+    }
+    rx_regex* h = new rx_regex();
+    s = compile_tree(nodes.data(), nodes.size(), 0, flags, h->host, msg);
+    if (s == RX_OK) s = finish_compile(h, flags);
+    else set_error(msg);
+    if (s != RX_OK) {
+        rx_free(h);
+        return s;
+    }
+    *out = h;
+    return RX_OK;
+    RX_GUARD_END
+}
+
+rx_status rx_compile_ast(const rx_node* nodes, size_t n, int32_t root, uint32_t flags, rx_handle* out) {
+    RX_GUARD_BEGIN
+    if (!out || !nodes) {
+        set_error("rx_compile_ast: null argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    rx_regex* h = new rx_regex();
+    std::string msg;
+    rx_status s = compile_tree(nodes, n, root, flags, h->host, msg);
+    if (s == RX_OK) s = finish_compile(h, flags);
+    else set_error(msg);
+    if (s != RX_OK) {
+        rx_free(h);
+        return s;
+    }
+    *out = h;
+    return RX_OK;
+    RX_GUARD_END
+}
+
+rx_status rx_info(rx_handle h, rx_info_t* out) {
+    if (!h || !out) {
+        set_error("rx_info: null argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    out->nodes = (int32_t)h->host.nodes.size();
+    out->positions = h->host.m;
+    out->words = h->host.W;
+    out->nullable = h->host.nullable ? 1 : 0;
+    out->memo_states = h->host.memo_K;
+    out->variants = h->host.variants;
+    out->device_bytes = h->dev_bytes;
+    return RX_OK;
+}
+
+void rx_free(rx_handle h) {
+    if (!h) return;
+    if (h->dev_blob) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (h->device >= 0 && h->device != cur) cudaSetDevice(h->device);
+        cudaFree(h->dev_blob);
+        if (h->device >= 0 && h->device != cur && cur >= 0) cudaSetDevice(cur);
+    }
+    delete h;
+}
+
+rx_status rx_tables(rx_handle h, int32_t* cont, int32_t* pos_node, int32_t* pos_bit, int32_t* null_bit,
+                    uint32_t* start, uint32_t* follow) {
+    if (!h) {
+        set_error("rx_tables: null handle");
+        return RX_ERR_INVALID_ARG;
+    }
+    const Compiled& C = h->host;
+    if (cont) std::copy(C.cont.begin(), C.cont.end(), cont);
+    if (pos_node) std::copy(C.pos_node.begin(), C.pos_node.end(), pos_node);
+    if (pos_bit) std::copy(C.pos_bit.begin(), C.pos_bit.end(), pos_bit);
+    if (null_bit) *null_bit = C.null_bit;
+    if (start) std::copy(C.start.begin(), C.start.end(), start);
+    if (follow) std::copy(C.follow_pos.begin(), C.follow_pos.end(), follow);
+    return RX_OK;
+}
+
+rx_status rx_tree(rx_handle h, rx_node* out, size_t cap, size_t* n) {
+    if (!h || !n || (!out && cap)) {
+        set_error("rx_tree: null argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    *n = h->host.nodes.size();
+    size_t k = std::min(cap, h->host.nodes.size());
+    if (k) std::memcpy(out, h->host.nodes.data(), k * sizeof(rx_node));
+    return RX_OK;
+}
+
+rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                      void* stream, const rx_match_opts* opts) {
+    RX_GUARD_BEGIN
+    if (!h) {
+        set_error("rx_match: null handle");
+        return RX_ERR_INVALID_ARG;
+    }
+    if (h->host_only) {
+        set_error("rx_match: handle was compiled with RX_COMPILE_HOST_ONLY");
+        return RX_ERR_INVALID_ARG;
+    }
+    if (n == 0) return RX_OK;
+    if (!offsets || !out) {
+        set_error("rx_match: null offsets or out");
+        return RX_ERR_INVALID_ARG;
+    }
+    if (n > 0xffffffffull / 2) {
+        set_error("rx_match: more than 2^31 strings");
+        return RX_ERR_TOO_LARGE;
+    }
+    int variant = resolve_variant(h, opts ? opts->variant : RX_VARIANT_AUTO);
+    if (variant <= 0 || variant > RX_VARIANT_WARP || !((h->host.variants >> variant) & 1u)) {
+        set_error("rx_match: variant " + std::to_string(variant) + " cannot run this expression");
+        return RX_ERR_UNSUPPORTED;
+    }
+    bool sort = n >= 4096;
+    if (opts && opts->sort >= 0) sort = opts->sort != 0;
+    int block = opts ? opts->block : 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* ws = nullptr;
+    size_t need = match_workspace_bytes(n, sort);
+    rx_status s = get_workspace(st, need, &ws);
+    if (s != RX_OK) return s;
+    cudaError_t e = launch_match(h->dev, variant, n, strings, offsets, out, sort, block, ws, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match launch");
+    return RX_OK;
+    RX_GUARD_END
+}
+
+rx_status rx_match(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                   void* stream) {
+    return rx_match_ex(h, n, strings, offsets, out, stream, nullptr);
+}
+
+rx_status rx_trace(rx_handle h, const uint8_t* str, int64_t len, uint32_t* frontiers, void* stream) {
+    RX_GUARD_BEGIN
+    if (!h || h->host_only || !frontiers || len < 0 || (len > 0 && !str)) {
+        set_error("rx_trace: bad argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    cudaError_t e = launch_trace(h->dev, str, len, frontiers, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rx_trace launch");
+    return RX_OK;
+    RX_GUARD_END
+}
+
+}  // extern "C"
+
+namespace rx {
+rx_status get_workspace(cudaStream_t st, size_t bytes, void** out);
+}
+
+extern "C" {
+
+rx_status rx_match_pairs(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
+                         uint8_t* out, void* stream) {
+    RX_GUARD_BEGIN
+    if (n == 0) return RX_OK;
+    if (!handles || !offsets || !out) {
+        rx::set_error("rx_match_pairs: null argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    rx_match_opts o{RX_VARIANT_AUTO, 0, 0, 0};
+    for (size_t i = 0; i < n; i++) {
+        rx_status s = rx_match_ex(handles[i], 1, strings, offsets + i, out + i, stream, &o);
+        if (s != RX_OK) return s;
+    }
+    return RX_OK;
+    RX_GUARD_END
+}
+
+rx_status rx_match_seq(rx_handle h, const uint8_t* str, int64_t len, uint8_t* out, void* stream) {
+    RX_GUARD_BEGIN
+    if (!h || h->host_only || !out || len < 0 || (len > 0 && !str)) {
+        rx::set_error("rx_match_seq: bad argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int variant = rx::resolve_variant(h, RX_VARIANT_AUTO);
+    if (variant == RX_VARIANT_WARP) variant = RX_VARIANT_WARP;
+    size_t need = rx::match_workspace_bytes(1, false) + 256;
+    void* ws = nullptr;
+    rx_status s = rx::get_workspace(st, need, &ws);
+    if (s != RX_OK) return s;
+    int64_t* off = reinterpret_cast<int64_t*>(static_cast<uint8_t*>(ws) + rx::match_workspace_bytes(1, false));
+    cudaError_t e = rx::launch_fill_offsets(off, len, st);
+    if (e == cudaSuccess)
+        e = rx::launch_match(h->dev, variant, 1, str, off, out, false, 32, ws, rx::match_workspace_bytes(1, false), st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match_seq launch");
+    return RX_OK;
+    RX_GUARD_END
+}
+
+rx_status rx_profile_enable(int on) {
+    rx::prof_enable(on != 0);
+    return RX_OK;
+}
+
+rx_status rx_profile_read(int64_t* launches, int64_t* timed, double* kernel_ms) {
+    cudaError_t e = rx::prof_read(launches, timed, kernel_ms);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_profile_read");
+    return RX_OK;
+}
+
+rx_status rx_match_batch(const rx_handle*, size_t, const uint8_t*, const int64_t*, uint8_t*, void*) {
+    rx::set_error("rx_match_batch: not built yet");
+    return RX_ERR_UNSUPPORTED;
+}
+rx_status rx_match_long(rx_handle, const uint8_t*, int64_t, int64_t, uint8_t*, void*) {
+    rx::set_error("rx_match_long: not built yet");
+    return RX_ERR_UNSUPPORTED;
+}
+rx_status rx_serve_create(const rx_serve_cfg*, rx_server** out) {
+    if (out) *out = nullptr;
+    rx::set_error("serving: not built yet");
+    return RX_ERR_UNSUPPORTED;
+}
+rx_status rx_serve_submit(rx_server*, rx_handle, const uint8_t*, int64_t, uint64_t*) { return RX_ERR_UNSUPPORTED; }
+size_t rx_serve_poll(rx_server*, uint64_t*, uint8_t*, rx_status*, size_t) { return 0; }
+rx_status rx_serve_drain(rx_server*, int64_t) { return RX_ERR_UNSUPPORTED; }
+rx_status rx_serve_stats(rx_server*, rx_serve_stats_t*) { return RX_ERR_UNSUPPORTED; }
+rx_status rx_serve_destroy(rx_server*) { return RX_ERR_UNSUPPORTED; }
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// rx_internal.h -- shared declarations of the host compiler, the kernels and
+// the C ABI layer.  Not installed; include/rx.h is the public surface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rx.h"
+
+namespace rx {
+
+// Largest macro-step cache kept: rows of 256 x u32 must fit in shared memory.
+constexpr int kMemoMaxStates = 192;
+// Largest group of same-byte positions one thread-variant lookup covers.
+constexpr int kGroupMaxBits = 8;
+// Widest active set per thread for the sparse thread variant (32-bit words).
+constexpr int kSparseMaxWords = 8;
+// Widest active set per warp for the warp variant (lane-owned words).
+constexpr int kWarpMaxWords = 128;
+
+// Tables of one compiled expression as the kernels see them (device
+// pointers into one allocation).  Passed by value to kernels.
+struct DevTables {
+    int32_t m;         // positions (CHAR leaves)
+    int32_t W;         // 32-bit words per active set
+    int32_t nbits;     // bits used (positions + padding + null)
+    int32_t null_bit;  // bit index of null
+    const uint32_t* start;   // [W]        evolution of {root}
+    const uint32_t* B;       // [256*W]    positions labelled c
+    const uint32_t* follow;  // [nbits*W]  evolution of {cont p} by bit of p
+    // thread variant: one lookup per byte into a per-byte subset table
+    const uint2* gl_desc;    // [256] x = shift | word<<5 | mask<<8, y = word offset of the byte's table
+    const uint32_t* gl_tt;   // tables, W words per entry
+    int32_t gl_words;        // words in gl_tt (0: variant unavailable)
+    // macro-step cache
+    int32_t memo_K;          // states (0: unavailable); state 0 is the empty set
+    const uint32_t* memo_T;  // [K*256] next state * 256 (row start, in words)
+    const uint8_t* memo_acc; // [K] 1 iff the state's set holds null
+    uint32_t memo_start;     // start state * 256
+    uint32_t variants;       // bit v: rx_variant v can run
+    int32_t nullable;
+    // the paper's own machine (Section 8): node array + cont
+    int32_t nn;              // nodes in the flattened tree
+    const int4* pnodes;      // [nn] x = kind | byte<<8, y = l, z = r, w = cont (-1 = null)
+    int32_t proot;
+};
+
+// Host-side compiled expression.
+struct Compiled {
+    // tree (renumbered: preorder from the root, root = 0)
+    std::vector<rx_node> nodes;
+    std::vector<int32_t> orig_id;  // new id -> caller's id
+    std::vector<int32_t> cont;     // Def 4.4, -1 = null (new ids)
+    int m = 0;
+    std::vector<int32_t> pos_node;  // canonical position (left-to-right) -> new node id
+    std::vector<int32_t> pos_bit;   // canonical position -> bit index
+    int nbits = 0, W = 0, null_bit = 0;
+    bool nullable = false;
+    std::vector<uint32_t> start;       // W
+    std::vector<uint32_t> follow_pos;  // m*W, canonical position order
+    std::vector<uint32_t> follow_bit;  // nbits*W, by bit
+    std::vector<uint32_t> B;           // 256*W
+    // thread variant
+    bool gl_ok = false;
+    std::vector<uint2> gl_desc;  // 256
+    std::vector<uint32_t> gl_tt;
+    // cache of macro steps
+    int memo_K = 0;
+    std::vector<uint32_t> memo_T;  // K*256
+    std::vector<uint8_t> memo_acc;
+    uint32_t memo_start = 0;
+    uint32_t variants = 0;
+};
+
+// Compile a tree (caller ids).  Returns RX_OK or an error with msg set.
+rx_status compile_tree(const rx_node* nodes, size_t n, int32_t root, uint32_t flags, Compiled& out,
+                       std::string& msg);
+// Parse pattern text into a node array (root = 0).
+rx_status parse_pattern(const char* pat, size_t len, std::vector<rx_node>& nodes, size_t& err_pos,
+                        std::string& msg);
+
+void set_error(const std::string& msg);
+
+}  // namespace rx
+
+struct rx_regex {
+    rx::Compiled host;
+    rx::DevTables dev{};
+    void* dev_blob = nullptr;
+    int64_t dev_bytes = 0;
+    int device = -1;
+    bool host_only = false;
+};

@@ -1,0 +1,181 @@
+"""CPU-side checks of the library: the C ABI loads and exports every symbol
+include/rx.h declares, and the host compiler (a1-a4: parse, cont, evolutions,
+successor sets) agrees with the oracle.  No kernel runs here: handles are
+compiled with RX_COMPILE_HOST_ONLY."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1108_3126_b300 as rx
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1108_3126_b300 import build
+    build.build()
+
+
+def declared_symbols():
+    out = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(rx_\w+)\s*\(", text, flags=re.M):
+            out.add(m.group(1))
+    return out
+
+
+def test_exports_every_declared_symbol():
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    lib = ctypes.CDLL(rx.LIB_PATH)
+    missing = [s for s in sorted(syms) if not hasattr(lib, s)]
+    assert not missing, missing
+    # the binding covers the whole header
+    assert syms <= set(rx.SIGNATURES), syms - set(rx.SIGNATURES)
+
+
+def test_version_and_error_strings():
+    assert b"sm_103a" in rx.lib().rx_version()
+    assert rx.last_error()
+
+
+def host(pattern_or_nodes, flags=rx.COMPILE_HOST_ONLY):
+    if isinstance(pattern_or_nodes, (bytes, str)):
+        return rx.Regex.compile(pattern_or_nodes, flags)
+    return rx.Regex.from_nodes(pattern_or_nodes, 0, flags)
+
+
+def bits_to_set(words, pos_bit, null_bit):
+    s = set()
+    null_bit = int(null_bit)
+    for q, b in enumerate(pos_bit):
+        b = int(b)
+        if (int(words[b >> 5]) >> (b & 31)) & 1:
+            s.add(q)
+    has_null = bool((int(words[null_bit >> 5]) >> (null_bit & 31)) & 1)
+    return s, has_null
+
+
+def check_against_glushkov(nodes):
+    r = host(nodes)
+    tree = r.tree()
+    t = r.tables()
+    # the library numbers nodes in preorder; compare on its tree
+    pos = oracle.positions(tree)
+    assert t["pos_node"].tolist() == pos
+    assert t["cont"].tolist() == oracle.cont(tree).tolist()
+    nullable, first, last, follow = oracle.glushkov(tree)
+    idx = {p: q for q, p in enumerate(pos)}
+    st, st_null = bits_to_set(t["start"], t["pos_bit"], t["null_bit"])
+    assert st == {idx[p] for p in first} and st_null == nullable
+    for q, p in enumerate(pos):
+        f, fn = bits_to_set(t["follow"][q], t["pos_bit"], t["null_bit"])
+        assert f == {idx[x] for x in follow[p]}, (q, p)
+        assert fn == (p in last)
+    # bit layout: distinct bits, null separate, within the declared width
+    bits = t["pos_bit"].tolist()
+    assert len(set(bits)) == len(bits) and t["null_bit"] not in bits
+    assert max(bits + [t["null_bit"]]) < 32 * t["words"]
+    info = r.info()
+    assert info["positions"] == len(pos) and info["nullable"] == int(nullable)
+
+
+def test_fig41_tables():
+    # (a*)* b: Fig 4.1 numbering differs from preorder; compare through the tree
+    nodes = oracle.parse(b"(a*)*b")
+    check_against_glushkov(nodes)
+    r = host(b"(a*)*b")
+    t = r.tables()
+    tree = r.tree()
+    # preorder: 0 CAT, 1 STAR (p1), 2 STAR (p3), 3 a (p4), 4 b (p2)
+    assert tree["kind"].tolist() == [rx.CAT, rx.STAR, rx.STAR, rx.CHAR, rx.CHAR]
+    assert t["cont"].tolist() == [-1, 4, 1, 2, -1]  # = Fig 4.1: p1->p2, p3->p1, p4->p3
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tables_match_glushkov_random(seed):
+    for i in range(40):
+        size = 1 + (i * 7 + seed) % 90
+        alpha = [b"abc", synth.LOWER, synth.ALL_BYTES][i % 3]
+        e = synth.gen_regex(size, 10, alpha, synth.item_seed(0xC0 + seed, i), eps_loop_p=0.1)
+        check_against_glushkov(e)
+
+
+def test_wide_expression_tables():
+    # more than 64 and more than 1024 positions: sequential bit layout
+    e = synth.gen_regex(400, 14, synth.LOWER, synth.item_seed(0xC9, 1))
+    check_against_glushkov(e)
+    big = oracle.parse(b"(" + b"|".join(b"ab" for _ in range(700)) + b")*")
+    check_against_glushkov(big)
+
+
+def test_parse_matches_oracle_parser():
+    for i in range(150):
+        e = synth.gen_regex(1 + i % 60, 9, synth.ALL_BYTES, synth.item_seed(0xCA, i), eps_loop_p=0.05)
+        pat = synth.to_pattern(e)
+        assert (host(pat).tree() == oracle.parse(pat)).all()
+    for pat in [b"", b"()", b"a|", b"|", b"(|)*", b"\\x00\\xff", b"a**|\\e*b", b"\\(\\)\\|\\*\\\\"]:
+        assert (host(pat).tree() == oracle.parse(pat)).all(), pat
+
+
+@pytest.mark.parametrize("bad,pos", [(b"(", 1), (b")", 0), (b"*a", 0), (b"a(b", 3), (b"\\x4", 0), (b"ab)", 2)])
+def test_parse_errors(bad, pos):
+    with pytest.raises(rx.RxError) as ei:
+        host(bad)
+    assert ei.value.status == 1 and ei.value.err_pos == pos
+    with pytest.raises(ValueError):
+        oracle.parse(bad)
+
+
+def test_malformed_trees_rejected():
+    nd = rx.NODE_DTYPE
+    shared = np.array([(rx.CAT, 0, 0, 1, 1), (rx.CHAR, 97, 0, -1, -1)], nd)  # one child used twice
+    cyc = np.array([(rx.STAR, 0, 0, 1, -1), (rx.STAR, 0, 0, 0, -1)], nd)
+    oob = np.array([(rx.ALT, 0, 0, 1, 5), (rx.CHAR, 97, 0, -1, -1)], nd)
+    badkind = np.array([(9, 0, 0, -1, -1)], nd)
+    for t in (shared, cyc, oob, badkind):
+        with pytest.raises(rx.RxError) as ei:
+            rx.Regex.from_nodes(t, 0, rx.COMPILE_HOST_ONLY)
+        assert ei.value.status == 2
+    with pytest.raises(rx.RxError):
+        rx.Regex.from_nodes(shared, 7, rx.COMPILE_HOST_ONLY)
+
+
+def test_limits():
+    # more than RX_MAX_POSITIONS positions
+    pat = b"a" * 5000
+    with pytest.raises(rx.RxError) as ei:
+        host(pat)
+    assert ei.value.status == 3
+    deep = b"(" * 30000 + b"a" + b")" * 30000
+    with pytest.raises(rx.RxError) as ei:
+        host(deep)
+    assert ei.value.status == 3
+
+
+def test_memo_cache_is_a_cache_of_macro_steps():
+    # the cache covers every reachable set; its states are distinct sets
+    for i in range(20):
+        e = synth.gen_regex(64, 10, synth.LOWER, synth.item_seed(0xCB, i))
+        info = host(e, 0 | rx.COMPILE_HOST_ONLY).info()
+        assert info["memo_states"] >= 2
+        assert info["variants"] & (1 << rx.VARIANT_MEMO)
+    no = host(synth.gen_regex(64, 10, synth.LOWER, 5), rx.COMPILE_HOST_ONLY | rx.COMPILE_NO_MEMO).info()
+    assert no["memo_states"] == 0 and not (no["variants"] & (1 << rx.VARIANT_MEMO))
+
+
+def test_host_only_handle_cannot_match():
+    r = host(b"abc")
+    with pytest.raises(rx.RxError) as ei:
+        rx.match(r, 0, 0, 0, n=1, stream=0)
+    assert ei.value.status == 2
