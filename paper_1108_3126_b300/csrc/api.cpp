@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 
 #include "kernels.cuh"
 #include "rx_internal.h"
@@ -81,6 +82,10 @@ static rx_status upload(rx_regex* h) {
     size_t o_desc = take(256 * sizeof(uint2)), o_tt = take(std::max<size_t>(C.gl_tt.size(), 1) * 4);
     size_t o_T = take(std::max<size_t>(C.memo_T.size(), 1) * 4), o_acc = take(std::max<size_t>(C.memo_acc.size(), 1));
     size_t o_nd = take(C.nodes.size() * sizeof(int4));
+    const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
+    size_t o_sps = take(spW * 4 + 16), o_spB = take((size_t)256 * spW * 4 + 16),
+           o_spF = take((size_t)C.nbits * spW * 4 + 16);
+    size_t o_self = take(sizeof(DevTables));
     size_t total = off;
     std::vector<uint8_t> blob(total, 0);
     auto put = [&](size_t o, const void* p, size_t b) {
@@ -97,6 +102,17 @@ static rx_status upload(rx_regex* h) {
     for (size_t i = 0; i < C.nodes.size(); i++)
         pn[i] = make_int4((int)C.nodes[i].kind | ((int)C.nodes[i].byte << 8), C.nodes[i].l, C.nodes[i].r, C.cont[i]);
     put(o_nd, pn.data(), pn.size() * sizeof(int4));
+    if (spW) {
+        std::vector<uint32_t> ps(spW, 0u), pB((size_t)256 * spW, 0u), pF((size_t)C.nbits * spW, 0u);
+        for (int k = 0; k < W; k++) ps[k] = C.start[k];
+        for (int r = 0; r < 256; r++)
+            for (int k = 0; k < W; k++) pB[(size_t)r * spW + k] = C.B[(size_t)r * W + k];
+        for (int r = 0; r < C.nbits; r++)
+            for (int k = 0; k < W; k++) pF[(size_t)r * spW + k] = C.follow_bit[(size_t)r * W + k];
+        put(o_sps, ps.data(), ps.size() * 4);
+        put(o_spB, pB.data(), pB.size() * 4);
+        put(o_spF, pF.data(), pF.size() * 4);
+    }
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     e = cudaMalloc(&h->dev_blob, total);
@@ -121,6 +137,10 @@ static rx_status upload(rx_regex* h) {
     t.gl_desc = reinterpret_cast<const uint2*>(b + o_desc);
     t.gl_tt = reinterpret_cast<const uint32_t*>(b + o_tt);
     t.gl_words = C.gl_ok ? (int32_t)C.gl_tt.size() : 0;
+    t.sp_W = spW;
+    t.sp_start = reinterpret_cast<const uint32_t*>(b + o_sps);
+    t.sp_B = reinterpret_cast<const uint32_t*>(b + o_spB);
+    t.sp_follow = reinterpret_cast<const uint32_t*>(b + o_spF);
     t.memo_K = C.memo_K;
     t.memo_T = reinterpret_cast<const uint32_t*>(b + o_T);
     t.memo_acc = b + o_acc;
@@ -130,6 +150,9 @@ static rx_status upload(rx_regex* h) {
     t.nn = (int32_t)C.nodes.size();
     t.pnodes = reinterpret_cast<const int4*>(b + o_nd);
     t.proot = 0;
+    h->dev_self = reinterpret_cast<const DevTables*>(b + o_self);
+    e = cudaMemcpy(b + o_self, &t, sizeof(DevTables), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy table header");
     return RX_OK;
 }
 
@@ -305,8 +328,7 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
         set_error("rx_match: variant " + std::to_string(variant) + " cannot run this expression");
         return RX_ERR_UNSUPPORTED;
     }
-    bool sort = n >= 4096;
-    if (opts && opts->sort >= 0) sort = opts->sort != 0;
+    int sort = rx::resolve_sort(variant, opts ? opts->sort : -1, n);
     int block = opts ? opts->block : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* ws = nullptr;
@@ -370,14 +392,14 @@ rx_status rx_match_seq(rx_handle h, const uint8_t* str, int64_t len, uint8_t* ou
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int variant = rx::resolve_variant(h, RX_VARIANT_AUTO);
     if (variant == RX_VARIANT_WARP) variant = RX_VARIANT_WARP;
-    size_t need = rx::match_workspace_bytes(1, false) + 256;
+    size_t need = rx::match_workspace_bytes(1, 0) + 256;
     void* ws = nullptr;
     rx_status s = rx::get_workspace(st, need, &ws);
     if (s != RX_OK) return s;
-    int64_t* off = reinterpret_cast<int64_t*>(static_cast<uint8_t*>(ws) + rx::match_workspace_bytes(1, false));
+    int64_t* off = reinterpret_cast<int64_t*>(static_cast<uint8_t*>(ws) + rx::match_workspace_bytes(1, 0));
     cudaError_t e = rx::launch_fill_offsets(off, len, st);
     if (e == cudaSuccess)
-        e = rx::launch_match(h->dev, variant, 1, str, off, out, false, 32, ws, rx::match_workspace_bytes(1, false), st);
+        e = rx::launch_match(h->dev, variant, 1, str, off, out, 0, 32, ws, rx::match_workspace_bytes(1, 0), st);
     if (e != cudaSuccess) return cuda_fail(e, "rx_match_seq launch");
     return RX_OK;
     RX_GUARD_END
@@ -394,23 +416,90 @@ rx_status rx_profile_read(int64_t* launches, int64_t* timed, double* kernel_ms) 
     return RX_OK;
 }
 
-rx_status rx_match_batch(const rx_handle*, size_t, const uint8_t*, const int64_t*, uint8_t*, void*) {
-    rx::set_error("rx_match_batch: not built yet");
-    return RX_ERR_UNSUPPORTED;
+// class of a handle in the batched kernel (the variant it runs there)
+static int batch_class(const rx_regex* h) {
+    const Compiled& C = h->host;
+    if (C.memo_K > 0) return rx::kClsMemo;
+    if (C.gl_ok) return C.W == 1 ? rx::kClsThread1 : rx::kClsThread2;
+    if (C.W <= 4) return rx::kClsSparse4;
+    if (C.W <= 8) return rx::kClsSparse8;
+    return rx::kClsWarp;
 }
-rx_status rx_match_long(rx_handle, const uint8_t*, int64_t, int64_t, uint8_t*, void*) {
-    rx::set_error("rx_match_long: not built yet");
-    return RX_ERR_UNSUPPORTED;
+
+rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
+                         uint8_t* out, void* stream) {
+    RX_GUARD_BEGIN
+    if (n == 0) return RX_OK;
+    if (!handles || !offsets || !out) {
+        rx::set_error("rx_match_batch: null argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    if (n > 0x7fffffffull) {
+        rx::set_error("rx_match_batch: more than 2^31 pairs");
+        return RX_ERR_TOO_LARGE;
+    }
+    std::unordered_map<const rx_regex*, uint32_t> index;
+    std::vector<rx::BatchTab> tabs;
+    std::vector<uint32_t> pair_tab(n);
+    std::vector<uint8_t> cls(n);
+    std::vector<uint8_t> tab_cls;
+    const rx_regex* last = nullptr;
+    uint32_t last_i = 0;
+    for (size_t i = 0; i < n; i++) {
+        const rx_regex* h = handles[i];
+        if (h != last) {
+            if (!h || h->host_only) {
+                rx::set_error("rx_match_batch: null or host-only handle at pair " + std::to_string(i));
+                return RX_ERR_INVALID_ARG;
+            }
+            auto it = index.find(h);
+            if (it == index.end()) {
+                it = index.emplace(h, (uint32_t)tabs.size()).first;
+                rx::BatchTab bt;
+                bt.t = h->dev;
+                tabs.push_back(bt);
+                tab_cls.push_back((uint8_t)batch_class(h));
+            }
+            last = h;
+            last_i = it->second;
+        }
+        pair_tab[i] = last_i;
+        cls[i] = tab_cls[last_i];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    size_t need = rx::batch_workspace_bytes(n, tabs.size());
+    void* ws = nullptr;
+    rx_status s = rx::get_workspace(st, need, &ws);
+    if (s != RX_OK) return s;
+    cudaError_t e = rx::launch_batch(tabs.data(), tabs.size(), pair_tab.data(), cls.data(), n, strings, offsets, out,
+                                     ws, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match_batch launch");
+    return RX_OK;
+    RX_GUARD_END
 }
-rx_status rx_serve_create(const rx_serve_cfg*, rx_server** out) {
-    if (out) *out = nullptr;
-    rx::set_error("serving: not built yet");
-    return RX_ERR_UNSUPPORTED;
+
+rx_status rx_match_long(rx_handle h, const uint8_t* str, int64_t len, int64_t chunk_bytes, uint8_t* out,
+                        void* stream) {
+    RX_GUARD_BEGIN
+    if (!h || h->host_only || !out || len < 0 || (len > 0 && !str) || chunk_bytes < 0) {
+        rx::set_error("rx_match_long: bad argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!rx::long_supported(h->dev)) return rx_match_seq(h, str, len, out, stream);
+    int64_t C = chunk_bytes > 0 ? chunk_bytes : rx::long_chunk_auto(h->dev, len);
+    size_t need = rx::long_workspace_bytes(h->dev, len, C);
+    if (need > (size_t(16) << 30)) {
+        rx::set_error("rx_match_long: chunk size too small for this length (transfer tables exceed 16 GiB)");
+        return RX_ERR_TOO_LARGE;
+    }
+    void* ws = nullptr;
+    rx_status s = rx::get_workspace(st, need, &ws);
+    if (s != RX_OK) return s;
+    cudaError_t e = rx::launch_long(h->dev, str, len, C, out, ws, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match_long launch");
+    return RX_OK;
+    RX_GUARD_END
 }
-rx_status rx_serve_submit(rx_server*, rx_handle, const uint8_t*, int64_t, uint64_t*) { return RX_ERR_UNSUPPORTED; }
-size_t rx_serve_poll(rx_server*, uint64_t*, uint8_t*, rx_status*, size_t) { return 0; }
-rx_status rx_serve_drain(rx_server*, int64_t) { return RX_ERR_UNSUPPORTED; }
-rx_status rx_serve_stats(rx_server*, rx_serve_stats_t*) { return RX_ERR_UNSUPPORTED; }
-rx_status rx_serve_destroy(rx_server*) { return RX_ERR_UNSUPPORTED; }
 
 }  // extern "C"

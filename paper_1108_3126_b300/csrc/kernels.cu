@@ -15,6 +15,7 @@
 //   thread : F in registers (<= 64 bits), one subset-table load per byte
 //   sparse : F in registers (<= 256 bits), union of follow rows per active bit
 //   warp   : one warp per string, lane l owns bitset words l, l+32, ...
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <mutex>
@@ -22,187 +23,13 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "steppers.cuh"
 
 namespace rx {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ uint4 ld_stream(const uint8_t* p) {
-    return __ldcs(reinterpret_cast<const uint4*>(p));
-}
-
-__device__ __forceinline__ uint32_t byte_of(const uint4& v, int k) {
-    uint32_t w = (k < 4) ? v.x : (k < 8) ? v.y : (k < 12) ? v.z : v.w;
-    return (w >> (8 * (k & 3))) & 0xffu;
-}
-
-// cooperative copy global -> shared (16-byte granules; sizes rounded up)
-__device__ void copy_to_smem(void* dst, const void* src, size_t bytes) {
-    const uint4* s = reinterpret_cast<const uint4*>(src);
-    uint4* d = reinterpret_cast<uint4*>(dst);
-    size_t n = (bytes + 15) / 16;
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
-}
-
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-// ------------------------------------------------------------- steppers
-// Each stepper: smem_bytes(t), load(t, smem) [block-cooperative],
-// bind(t, smem), init(), step(c), dead(), accept(), kill().
-
-struct MemoStep {
-    const uint32_t* T;
-    const uint8_t* acc;
-    uint32_t st;
-    static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * 1024) + align16(t.memo_K); }
-    __device__ static void load(const DevTables& t, uint8_t* sm) {
-        copy_to_smem(sm, t.memo_T, (size_t)t.memo_K * 1024);
-        copy_to_smem(sm + align16((size_t)t.memo_K * 1024), t.memo_acc, t.memo_K);
-    }
-    __device__ void bind(const DevTables& t, uint8_t* sm) {
-        T = reinterpret_cast<const uint32_t*>(sm);
-        acc = sm + align16((size_t)t.memo_K * 1024);
-        st = t.memo_start;
-    }
-    __device__ __forceinline__ void step(uint32_t c) { st = T[st + c]; }
-    __device__ __forceinline__ bool dead() const { return st == 0; }
-    __device__ __forceinline__ bool accept() const { return acc[st >> 8] != 0; }
-    __device__ __forceinline__ void kill() { st = 0; }
-};
-
-struct Thread1Step {
-    const uint2* desc;
-    const uint32_t* tt;
-    uint32_t F, nb;
-    static size_t smem_bytes(const DevTables& t) { return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4); }
-    __device__ static void load(const DevTables& t, uint8_t* sm) {
-        copy_to_smem(sm, t.gl_desc, 256 * sizeof(uint2));
-        copy_to_smem(sm + 256 * sizeof(uint2), t.gl_tt, (size_t)t.gl_words * 4);
-    }
-    __device__ void bind(const DevTables& t, uint8_t* sm) {
-        desc = reinterpret_cast<const uint2*>(sm);
-        tt = reinterpret_cast<const uint32_t*>(sm + 256 * sizeof(uint2));
-        F = t.start[0];
-        nb = t.null_bit;
-    }
-    __device__ __forceinline__ void step(uint32_t c) {
-        uint2 d = desc[c];
-        uint32_t x = (F >> (d.x & 31u)) & (d.x >> 8);
-        F = tt[d.y + x];
-    }
-    __device__ __forceinline__ bool dead() const { return F == 0; }
-    __device__ __forceinline__ bool accept() const { return (F >> nb) & 1u; }
-    __device__ __forceinline__ void kill() { F = 0; }
-};
-
-struct Thread2Step {
-    const uint2* desc;
-    const uint2* tt;
-    uint32_t F0, F1, nb;
-    static size_t smem_bytes(const DevTables& t) { return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4); }
-    __device__ static void load(const DevTables& t, uint8_t* sm) {
-        copy_to_smem(sm, t.gl_desc, 256 * sizeof(uint2));
-        copy_to_smem(sm + 256 * sizeof(uint2), t.gl_tt, (size_t)t.gl_words * 4);
-    }
-    __device__ void bind(const DevTables& t, uint8_t* sm) {
-        desc = reinterpret_cast<const uint2*>(sm);
-        tt = reinterpret_cast<const uint2*>(sm + 256 * sizeof(uint2));
-        F0 = t.start[0];
-        F1 = t.start[1];
-        nb = t.null_bit;
-    }
-    __device__ __forceinline__ void step(uint32_t c) {
-        uint2 d = desc[c];
-        uint32_t w = (d.x & 32u) ? F1 : F0;
-        uint32_t x = (w >> (d.x & 31u)) & (d.x >> 8);
-        uint2 e = tt[(d.y >> 1) + x];
-        F0 = e.x;
-        F1 = e.y;
-    }
-    __device__ __forceinline__ bool dead() const { return (F0 | F1) == 0; }
-    __device__ __forceinline__ bool accept() const { return (((nb < 32) ? F0 : F1) >> (nb & 31)) & 1u; }
-    __device__ __forceinline__ void kill() { F0 = F1 = 0; }
-};
-
-template <int W>
-struct SparseStep {
-    static_assert(W % 4 == 0, "W must be a multiple of 4");
-    const uint32_t* B;
-    const uint32_t* follow;
-    uint32_t F[W];
-    uint32_t nb;
-    static size_t smem_bytes(const DevTables& t) { return (size_t)256 * W * 4 + (size_t)t.nbits * W * 4; }
-    __device__ static void load(const DevTables& t, uint8_t* sm) {
-        // tables are stored with t.W words per row; widen to W words
-        uint32_t* b = reinterpret_cast<uint32_t*>(sm);
-        uint32_t* f = b + 256 * W;
-        for (int i = threadIdx.x; i < 256 * W; i += blockDim.x) {
-            int r = i / W, k = i % W;
-            b[i] = (k < t.W) ? t.B[(size_t)r * t.W + k] : 0u;
-        }
-        for (int i = threadIdx.x; i < t.nbits * W; i += blockDim.x) {
-            int r = i / W, k = i % W;
-            f[i] = (k < t.W) ? t.follow[(size_t)r * t.W + k] : 0u;
-        }
-    }
-    __device__ void bind(const DevTables& t, uint8_t* sm) {
-        B = reinterpret_cast<const uint32_t*>(sm);
-        follow = B + 256 * W;
-#pragma unroll
-        for (int k = 0; k < W; k++) F[k] = (k < t.W) ? t.start[k] : 0u;
-        nb = t.null_bit;
-    }
-    __device__ __forceinline__ void step(uint32_t c) {
-        uint32_t S[W];
-        const uint4* b4 = reinterpret_cast<const uint4*>(B + c * W);
-#pragma unroll
-        for (int q = 0; q < W / 4; q++) {
-            uint4 v = b4[q];
-            S[4 * q] = F[4 * q] & v.x;
-            S[4 * q + 1] = F[4 * q + 1] & v.y;
-            S[4 * q + 2] = F[4 * q + 2] & v.z;
-            S[4 * q + 3] = F[4 * q + 3] & v.w;
-        }
-#pragma unroll
-        for (int k = 0; k < W; k++) F[k] = 0;
-#pragma unroll
-        for (int w = 0; w < W; w++) {
-            uint32_t s = S[w];
-            while (s) {
-                int b = __ffs(s) - 1;
-                s &= s - 1;
-                const uint4* r4 = reinterpret_cast<const uint4*>(follow + (size_t)(w * 32 + b) * W);
-#pragma unroll
-                for (int q = 0; q < W / 4; q++) {
-                    uint4 v = r4[q];
-                    F[4 * q] |= v.x;
-                    F[4 * q + 1] |= v.y;
-                    F[4 * q + 2] |= v.z;
-                    F[4 * q + 3] |= v.w;
-                }
-            }
-        }
-    }
-    __device__ __forceinline__ bool dead() const {
-        uint32_t o = 0;
-#pragma unroll
-        for (int k = 0; k < W; k++) o |= F[k];
-        return o == 0;
-    }
-    __device__ __forceinline__ bool accept() const {
-        uint32_t r = 0;
-#pragma unroll
-        for (int k = 0; k < W; k++)
-            if (k == (int)(nb >> 5)) r = (F[k] >> (nb & 31)) & 1u;
-        return r != 0;
-    }
-    __device__ __forceinline__ void kill() {
-#pragma unroll
-        for (int k = 0; k < W; k++) F[k] = 0;
-    }
-};
+using namespace rx::dev;
 
 // ------------------------------------------------ thread-per-string kernel
 // Persistent warps take tasks of 32 consecutive entries of the (length-
@@ -239,37 +66,7 @@ __global__ void __launch_bounds__(256) k_thread(const DevTables t, const uint8_t
             e += (uint64_t)off[id + 1];
         }
         S st = proto;
-        bool active = valid && s < e;
-        if (valid && !active) out[id] = st.accept();
-        if (!active) st.kill();
-        uint64_t blk = s & ~uint64_t(15);
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (active) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
-        while (__any_sync(FULL, active)) {
-            uint64_t nb = blk + 16;
-            uint4 vn = make_uint4(0, 0, 0, 0);
-            if (active && nb < e) vn = ld_stream(reinterpret_cast<const uint8_t*>(nb));
-            bool full = !active || (blk >= s && nb <= e);
-            if (__all_sync(FULL, full)) {
-#pragma unroll
-                for (int k = 0; k < 16; k++) st.step(byte_of(v, k));
-            } else {
-#pragma unroll
-                for (int k = 0; k < 16; k++) {
-                    S nx = st;
-                    nx.step(byte_of(v, k));
-                    bool ok = active && blk + k >= s && blk + k < e;
-                    if (ok) st = nx;
-                }
-            }
-            blk = nb;
-            v = vn;
-            if (active && (blk >= e || st.dead())) {
-                out[id] = st.accept();
-                st.kill();
-                active = false;
-            }
-        }
+        run_lane(st, s, e, valid, out + id);
     }
 }
 
@@ -296,7 +93,6 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
         follow = reinterpret_cast<const uint32_t*>(smem + align16(bw * 4));
     }
     const int lane = threadIdx.x & 31;
-    const int nbw = t.null_bit >> 5, nbb = t.null_bit & 31;
     for (;;) {
         unsigned task = 0;
         if (lane == 0) task = atomicAdd(queue, 1u);
@@ -305,77 +101,18 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
         long long id = perm ? (long long)perm[task] : (long long)task;
         const uint64_t base = reinterpret_cast<uint64_t>(str);
         const uint64_t s = base + (uint64_t)off[id], e = base + (uint64_t)off[id + 1];
-        uint32_t F[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            int w = k * 32 + lane;
-            F[k] = (w < W) ? t.start[w] : 0u;
-        }
-        bool dead = false;
-        for (uint64_t win = s & ~uint64_t(511); win < e && !dead; win += 512) {
-            uint4 v = make_uint4(0, 0, 0, 0);
-            uint64_t my = win + 16 * lane;
-            if (my < e && my + 16 > s) v = ld_stream(reinterpret_cast<const uint8_t*>(my));
-            for (int src = 0; src < 32 && !dead; src++) {
-                uint64_t blk = win + 16 * src;
-                if (blk >= e) break;
-                if (blk + 16 <= s) continue;
-                uint32_t words[4];
-                words[0] = __shfl_sync(FULL, v.x, src);
-                words[1] = __shfl_sync(FULL, v.y, src);
-                words[2] = __shfl_sync(FULL, v.z, src);
-                words[3] = __shfl_sync(FULL, v.w, src);
-#pragma unroll 1
-                for (int kb = 0; kb < 16; kb++) {
-                    uint64_t p = blk + kb;
-                    if (p < s || p >= e) continue;
-                    uint32_t c = (words[kb >> 2] >> (8 * (kb & 3))) & 0xffu;
-                    uint32_t Sx[K];
-#pragma unroll
-                    for (int k = 0; k < K; k++) {
-                        int w = k * 32 + lane;
-                        Sx[k] = (w < W) ? (F[k] & B[(size_t)c * W + w]) : 0u;
-                        F[k] = 0;
-                    }
-#pragma unroll
-                    for (int k = 0; k < K; k++) {
-                        unsigned act = __ballot_sync(FULL, Sx[k] != 0);
-                        while (act) {
-                            int srcl = __ffs(act) - 1;
-                            act &= act - 1;
-                            uint32_t bits = __shfl_sync(FULL, Sx[k], srcl);
-                            while (bits) {
-                                int b = __ffs(bits) - 1;
-                                bits &= bits - 1;
-                                const uint32_t* row = follow + (size_t)((k * 32 + srcl) * 32 + b) * W;
-#pragma unroll
-                                for (int kk = 0; kk < K; kk++) {
-                                    int w = kk * 32 + lane;
-                                    if (w < W) F[kk] |= row[w];
-                                }
-                            }
-                        }
-                    }
-                    uint32_t any = 0;
-#pragma unroll
-                    for (int k = 0; k < K; k++) any |= F[k];
-                    if (!__any_sync(FULL, any != 0)) {
-                        dead = true;
-                        break;
-                    }
-                }
-            }
-        }
-        uint32_t mine = 0;
-#pragma unroll
-        for (int k = 0; k < K; k++)
-            if (k == (nbw >> 5)) mine = F[k];
-        uint32_t nw = __shfl_sync(FULL, mine, nbw & 31);
-        if (lane == 0) out[id] = dead ? 0 : ((nw >> nbb) & 1u);
+        bool acc = warp_string<K>(t, B, follow, s, e);
+        if (lane == 0) out[id] = acc;
     }
 }
 
 // ---------------------------------------------------- length-sort planner
+// Stable-enough counting sort of the strings by (class, length bucket),
+// longest first within a class, in four contention-free passes:
+//   hist    : every block counts its contiguous range in shared memory
+//   colscan : per bucket, running sums over the blocks (block cursors)
+//   scan    : exclusive scan of the bucket totals
+//   scatter : every block places its range with shared-memory cursors
 __device__ __forceinline__ int len_bucket(int64_t len) {
     if (len < 2048) return (int)len;
     int lg = 63 - __clzll(len);  // >= 11
@@ -383,27 +120,43 @@ __device__ __forceinline__ int len_bucket(int64_t len) {
     return b < kLenBuckets ? b : kLenBuckets - 1;
 }
 
-__global__ void k_len_hist(const int64_t* __restrict__ off, long long n, unsigned* __restrict__ hist) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int b = len_bucket(off[i + 1] - off[i]);
-        unsigned peers = __match_any_sync(__activemask(), b);
-        int leader = __ffs(peers) - 1;
-        if ((threadIdx.x & 31) == leader) atomicAdd(&hist[b], __popc(peers));
-    }
+__device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, long long i) {
+    int lb = len_bucket(off[i + 1] - off[i]);
+    int c = cls ? (int)cls[i] : 0;
+    return c * kLenBuckets + (kLenBuckets - 1 - lb);
 }
 
-// exclusive scan with the LONGEST bucket first: cursor[b] = sum_{b' > b} hist[b']
-__global__ void k_len_scan(const unsigned* __restrict__ hist, unsigned* __restrict__ cursor) {
+__global__ void k_plan_hist(const int64_t* __restrict__ off, const uint8_t* __restrict__ cls, long long n,
+                            long long per, int nbk, unsigned* __restrict__ hist_blk) {
+    extern __shared__ unsigned sh[];
+    for (int b = threadIdx.x; b < nbk; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&sh[plan_key(off, cls, i)], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbk; b += blockDim.x) hist_blk[(size_t)blockIdx.x * nbk + b] = sh[b];
+}
+
+__global__ void k_plan_colscan(unsigned* __restrict__ hist_blk, int nblk, int nbk, unsigned* __restrict__ totals) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbk) return;
+    unsigned run = 0;
+    for (int g = 0; g < nblk; g++) {
+        unsigned h = hist_blk[(size_t)g * nbk + b];
+        hist_blk[(size_t)g * nbk + b] = run;
+        run += h;
+    }
+    totals[b] = run;
+}
+
+__global__ void k_plan_scan(unsigned* __restrict__ totals, int nbk) {
     __shared__ unsigned part[1024];
-    constexpr int PER = (kLenBuckets + 1023) / 1024;
     int t = threadIdx.x;
-    unsigned loc[PER];
+    int per = (nbk + 1023) / 1024;
     unsigned sum = 0;
-    for (int j = 0; j < PER; j++) {
-        int r = t * PER + j;  // position in descending order
-        int b = kLenBuckets - 1 - r;
-        loc[j] = (b >= 0) ? hist[b] : 0u;
-        sum += loc[j];
+    for (int j = 0; j < per; j++) {
+        int b = t * per + j;
+        if (b < nbk) sum += totals[b];
     }
     part[t] = sum;
     __syncthreads();
@@ -414,25 +167,26 @@ __global__ void k_len_scan(const unsigned* __restrict__ hist, unsigned* __restri
         __syncthreads();
     }
     unsigned run = part[t] - sum;
-    for (int j = 0; j < PER; j++) {
-        int r = t * PER + j;
-        int b = kLenBuckets - 1 - r;
-        if (b >= 0) cursor[b] = run;
-        run += loc[j];
+    for (int j = 0; j < per; j++) {
+        int b = t * per + j;
+        if (b < nbk) {
+            unsigned h = totals[b];
+            totals[b] = run;
+            run += h;
+        }
     }
 }
 
-__global__ void k_len_scatter(const int64_t* __restrict__ off, long long n, unsigned* __restrict__ cursor,
-                              uint32_t* __restrict__ perm) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int b = len_bucket(off[i + 1] - off[i]);
-        unsigned peers = __match_any_sync(__activemask(), b);
-        int leader = __ffs(peers) - 1;
-        unsigned base = 0;
-        if ((threadIdx.x & 31) == leader) base = atomicAdd(&cursor[b], __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        unsigned rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
-        perm[base + rank] = (uint32_t)i;
+__global__ void k_plan_scatter(const int64_t* __restrict__ off, const uint8_t* __restrict__ cls, long long n,
+                               long long per, int nbk, const unsigned* __restrict__ cur_blk,
+                               const unsigned* __restrict__ starts, uint32_t* __restrict__ perm) {
+    extern __shared__ unsigned sh[];
+    for (int b = threadIdx.x; b < nbk; b += blockDim.x) sh[b] = starts[b] + cur_blk[(size_t)blockIdx.x * nbk + b];
+    __syncthreads();
+    long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        unsigned pos = atomicAdd(&sh[plan_key(off, cls, i)], 1u);
+        perm[pos] = (uint32_t)i;
     }
 }
 
@@ -582,36 +336,70 @@ int sm_count() {
     return cached[dev];
 }
 
-size_t match_workspace_bytes(size_t n, bool sort) {
+int plan_blocks(size_t n) {
+    long long g = ((long long)n + 4095) / 4096;
+    return (int)std::max<long long>(1, std::min<long long>(g, (long long)sm_count() * 2));
+}
+
+size_t plan_workspace_bytes(size_t n, int nclasses) {
+    size_t nbk = (size_t)kLenBuckets * nclasses;
+    return align16((size_t)plan_blocks(n) * nbk * 4) + align16(nbk * 4) + align16(n * 4);
+}
+
+cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
+                        unsigned** starts, cudaStream_t st) {
+    const int nbk = kLenBuckets * nclasses;
+    const int G = plan_blocks(n);
+    const long long per = ((long long)n + G - 1) / G;
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    unsigned* hist_blk = reinterpret_cast<unsigned*>(w);
+    unsigned* totals = reinterpret_cast<unsigned*>(w + align16((size_t)G * nbk * 4));
+    *perm = reinterpret_cast<uint32_t*>(w + align16((size_t)G * nbk * 4) + align16((size_t)nbk * 4));
+    *starts = totals;
+    size_t shb = (size_t)nbk * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_plan_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_plan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+    if (e != cudaSuccess) return e;
+    k_plan_hist<<<G, 512, shb, st>>>(off, cls, (long long)n, per, nbk, hist_blk);
+    k_plan_colscan<<<(nbk + 255) / 256, 256, 0, st>>>(hist_blk, G, nbk, totals);
+    k_plan_scan<<<1, 1024, 0, st>>>(totals, nbk);
+    k_plan_scatter<<<G, 512, shb, st>>>(off, cls, (long long)n, per, nbk, hist_blk, totals, *perm);
+    prof_count(4);
+    return cudaGetLastError();
+}
+
+size_t match_workspace_bytes(size_t n, int sort) {
     size_t b = 256;  // queue counter
-    if (sort) b += align16((size_t)kLenBuckets * 4) * 2 + align16(n * 4);
+    if (sort >= 1) b += plan_workspace_bytes(n, 1);
     return b;
 }
 
+int resolve_sort(int variant, int sort, size_t n) {
+    const bool streams = variant == RX_VARIANT_MEMO || variant == RX_VARIANT_THREAD;
+    if (sort >= 0) {
+        if (sort >= 2 && !streams) return sort == 2 ? 1 : 0;
+        return sort;
+    }
+    if (variant == RX_VARIANT_MEMO || variant == RX_VARIANT_THREAD) return n >= 4096 ? 2 : 3;
+    return n >= 4096 ? 1 : 0;
+}
+
 cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_t* str, const int64_t* off,
-                         uint8_t* out, bool sort, int block, void* ws, size_t ws_bytes, cudaStream_t st) {
+                         uint8_t* out, int sort, int block, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     if (ws_bytes < match_workspace_bytes(n, sort)) return cudaErrorInvalidValue;
     uint8_t* w = static_cast<uint8_t*>(ws);
     unsigned* queue = reinterpret_cast<unsigned*>(w);
     uint32_t* perm = nullptr;
-    cudaError_t err;
-    if (sort) {
-        unsigned* hist = reinterpret_cast<unsigned*>(w + 256);
-        unsigned* cursor = reinterpret_cast<unsigned*>(w + 256 + align16((size_t)kLenBuckets * 4));
-        perm = reinterpret_cast<uint32_t*>(w + 256 + 2 * align16((size_t)kLenBuckets * 4));
-        err = cudaMemsetAsync(w, 0, 256 + align16((size_t)kLenBuckets * 4), st);
+    cudaError_t err = cudaMemsetAsync(w, 0, 256, st);
+    if (err != cudaSuccess) return err;
+    if (sort == 3) return launch_stream(t, variant, (long long)n, str, off, nullptr, out, queue, st);
+    if (sort >= 1) {
+        unsigned* starts = nullptr;
+        err = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st);
         if (err != cudaSuccess) return err;
-        int g = (int)std::min<long long>((long long)(n + 255) / 256, (long long)sm_count() * 8);
-        k_len_hist<<<g, 256, 0, st>>>(off, (long long)n, hist);
-        k_len_scan<<<1, 1024, 0, st>>>(hist, cursor);
-        k_len_scatter<<<g, 256, 0, st>>>(off, (long long)n, cursor, perm);
-        prof_count(3);
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
-    } else {
-        err = cudaMemsetAsync(w, 0, 256, st);
-        if (err != cudaSuccess) return err;
+        if (sort == 2) return launch_stream(t, variant, (long long)n, str, off, perm, out, queue, st);
     }
     if (block <= 0) block = 256;
     block = (block + 31) / 32 * 32;

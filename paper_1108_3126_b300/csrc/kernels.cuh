@@ -16,12 +16,46 @@ struct Workspace {
     int device = -1;
 };
 
-// Bytes of scratch rx_match needs for n strings.
-size_t match_workspace_bytes(size_t n, bool sort);
+// Work order of rx_match: 0 = input order, 1 = global sort by length
+// (planner kernels) + the per-variant kernel, 2 = global sort + the
+// streaming kernel (memo and thread variants).
+int resolve_sort(int variant, int sort, size_t n);
 
-// Single expression, n strings.  variant is resolved (not AUTO).
+// Bytes of scratch rx_match needs for n strings.
+size_t match_workspace_bytes(size_t n, int sort);
+
+// Single expression, n strings.  variant and sort are resolved.
 cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_t* str, const int64_t* off,
-                         uint8_t* out, bool sort, int block, void* ws, size_t ws_bytes, cudaStream_t stream);
+                         uint8_t* out, int sort, int block, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+// Streaming kernel (memo and thread variants); perm may be NULL.
+cudaError_t launch_stream(const DevTables& t, int variant, long long n, const uint8_t* str, const int64_t* off,
+                          const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st);
+
+// Planner: order n strings by (class, length), longest first per class.
+// cls (device, n bytes) may be NULL (one class).  Writes *perm (n u32) and
+// *starts (first slot of every bucket) inside ws.
+size_t plan_workspace_bytes(size_t n, int nclasses);
+cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
+                        unsigned** starts, cudaStream_t st);
+
+// Batched pairs (batch.cu).  Variant classes, in task order.
+struct BatchTab {
+    DevTables t;
+};
+constexpr int kBatchClasses = 6;
+enum { kClsWarp = 0, kClsSparse8 = 1, kClsSparse4 = 2, kClsThread2 = 3, kClsThread1 = 4, kClsMemo = 5 };
+size_t batch_workspace_bytes(size_t n, size_t ntabs);
+cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
+                         size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
+                         cudaStream_t st);
+
+// Chunked single-string mode (long.cu).
+bool long_supported(const DevTables& t);
+int64_t long_chunk_auto(const DevTables& t, int64_t len);
+size_t long_workspace_bytes(const DevTables& t, int64_t len, int64_t C);
+cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, uint8_t* out, void* ws,
+                        size_t ws_bytes, cudaStream_t st);
 
 // Frontier after every byte of one string.
 cudaError_t launch_trace(const DevTables& t, const uint8_t* str, int64_t len, uint32_t* rows, cudaStream_t stream);

@@ -35,6 +35,11 @@ struct DevTables {
     const uint2* gl_desc;    // [256] x = shift | word<<5 | mask<<8, y = word offset of the byte's table
     const uint32_t* gl_tt;   // tables, W words per entry
     int32_t gl_words;        // words in gl_tt (0: variant unavailable)
+    // sparse variant: the same tables with rows padded to sp_W (4 or 8) words
+    int32_t sp_W;            // 0: W > 8
+    const uint32_t* sp_start;
+    const uint32_t* sp_B;
+    const uint32_t* sp_follow;
     // macro-step cache
     int32_t memo_K;          // states (0: unavailable); state 0 is the empty set
     const uint32_t* memo_T;  // [K*256] next state * 256 (row start, in words)
@@ -89,6 +94,7 @@ void set_error(const std::string& msg);
 struct rx_regex {
     rx::Compiled host;
     rx::DevTables dev{};
+    const rx::DevTables* dev_self = nullptr;  // device copy of `dev` (inside dev_blob)
     void* dev_blob = nullptr;
     int64_t dev_bytes = 0;
     int device = -1;

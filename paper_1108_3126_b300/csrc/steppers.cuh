@@ -1,0 +1,560 @@
+// steppers.cuh -- device-side building blocks shared by the kernels: input
+// loads and the steppers, each of which holds one active set and advances
+// it by one macro step of the lockstep machine (Rathnayake & Thielecke,
+// SOS 2011, Def 5.2) per input byte.
+#pragma once
+
+#include <cstdint>
+
+#include "rx_internal.h"
+
+namespace rx {
+namespace dev {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint4 ld_stream(const uint8_t* p) {
+    return __ldcs(reinterpret_cast<const uint4*>(p));
+}
+
+__device__ __forceinline__ uint32_t byte_of(const uint4& v, int k) {
+    uint32_t w = (k < 4) ? v.x : (k < 8) ? v.y : (k < 12) ? v.z : v.w;
+    return (w >> (8 * (k & 3))) & 0xffu;
+}
+
+// cooperative copy global -> shared (16-byte granules; sizes rounded up)
+__device__ inline void copy_to_smem(void* dst, const void* src, size_t bytes) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    size_t n = (bytes + 15) / 16;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// ------------------------------------------------------------- steppers
+// A stepper holds one active set and advances it by one byte.  Interface:
+//   smem_bytes(t) / load(t, smem) / bind(t, smem)   tables in shared memory
+//   bind_global(t)                                  tables read from global
+//   step(c)  dead()  accept()  kill()
+//   set_unit(b)       the set {bit b} (start of a chunk transfer row)
+//   store(dst)        write the set (ROW_WORDS words; memo writes the state id)
+
+struct MemoStep {
+    static constexpr int ROW_WORDS = 1;
+    const uint32_t* T;
+    const uint8_t* acc;
+    uint32_t st;
+    static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * 1024) + align16(t.memo_K); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        copy_to_smem(sm, t.memo_T, (size_t)t.memo_K * 1024);
+        copy_to_smem(sm + align16((size_t)t.memo_K * 1024), t.memo_acc, t.memo_K);
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        T = reinterpret_cast<const uint32_t*>(sm);
+        acc = sm + align16((size_t)t.memo_K * 1024);
+        st = t.memo_start;
+    }
+    __device__ void bind_global(const DevTables& t) {
+        T = t.memo_T;
+        acc = t.memo_acc;
+        st = t.memo_start;
+    }
+    __device__ __forceinline__ void step(uint32_t c) { st = T[st + c]; }
+    __device__ __forceinline__ bool dead() const { return st == 0; }
+    __device__ __forceinline__ bool accept() const { return acc[st >> 8] != 0; }
+    __device__ __forceinline__ void kill() { st = 0; }
+    __device__ __forceinline__ void set_state(uint32_t s) { st = s * 256u; }
+    __device__ __forceinline__ void save(uint32_t* p) const { p[0] = st; }
+    __device__ __forceinline__ void restore(const uint32_t* p) { st = p[0]; }
+};
+
+struct Thread1Step {
+    static constexpr int ROW_WORDS = 1;
+    const uint2* desc;
+    const uint32_t* tt;
+    uint32_t F, nb;
+    static size_t smem_bytes(const DevTables& t) { return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        copy_to_smem(sm, t.gl_desc, 256 * sizeof(uint2));
+        copy_to_smem(sm + 256 * sizeof(uint2), t.gl_tt, (size_t)t.gl_words * 4);
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        desc = reinterpret_cast<const uint2*>(sm);
+        tt = reinterpret_cast<const uint32_t*>(sm + 256 * sizeof(uint2));
+        F = t.start[0];
+        nb = t.null_bit;
+    }
+    __device__ void bind_global(const DevTables& t) {
+        desc = t.gl_desc;
+        tt = t.gl_tt;
+        F = t.start[0];
+        nb = t.null_bit;
+    }
+    __device__ __forceinline__ void step(uint32_t c) {
+        uint2 d = desc[c];
+        uint32_t x = (F >> (d.x & 31u)) & (d.x >> 8);
+        F = tt[d.y + x];
+    }
+    __device__ __forceinline__ bool dead() const { return F == 0; }
+    __device__ __forceinline__ bool accept() const { return (F >> nb) & 1u; }
+    __device__ __forceinline__ void kill() { F = 0; }
+    __device__ __forceinline__ void set_unit(int b) { F = (b < 32) ? (1u << b) : 0u; }
+    __device__ __forceinline__ void store(uint32_t* d) const { d[0] = F; }
+    __device__ __forceinline__ void save(uint32_t* p) const { p[0] = F; }
+    __device__ __forceinline__ void restore(const uint32_t* p) { F = p[0]; }
+};
+
+struct Thread2Step {
+    static constexpr int ROW_WORDS = 2;
+    const uint2* desc;
+    const uint2* tt;
+    uint32_t F0, F1, nb;
+    static size_t smem_bytes(const DevTables& t) { return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        copy_to_smem(sm, t.gl_desc, 256 * sizeof(uint2));
+        copy_to_smem(sm + 256 * sizeof(uint2), t.gl_tt, (size_t)t.gl_words * 4);
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        desc = reinterpret_cast<const uint2*>(sm);
+        tt = reinterpret_cast<const uint2*>(sm + 256 * sizeof(uint2));
+        F0 = t.start[0];
+        F1 = t.start[1];
+        nb = t.null_bit;
+    }
+    __device__ void bind_global(const DevTables& t) {
+        desc = t.gl_desc;
+        tt = reinterpret_cast<const uint2*>(t.gl_tt);
+        F0 = t.start[0];
+        F1 = t.start[1];
+        nb = t.null_bit;
+    }
+    __device__ __forceinline__ void step(uint32_t c) {
+        uint2 d = desc[c];
+        uint32_t w = (d.x & 32u) ? F1 : F0;
+        uint32_t x = (w >> (d.x & 31u)) & (d.x >> 8);
+        uint2 e = tt[(d.y >> 1) + x];
+        F0 = e.x;
+        F1 = e.y;
+    }
+    __device__ __forceinline__ bool dead() const { return (F0 | F1) == 0; }
+    __device__ __forceinline__ bool accept() const { return (((nb < 32) ? F0 : F1) >> (nb & 31)) & 1u; }
+    __device__ __forceinline__ void kill() { F0 = F1 = 0; }
+    __device__ __forceinline__ void set_unit(int b) {
+        F0 = (b < 32) ? (1u << b) : 0u;
+        F1 = (b >= 32 && b < 64) ? (1u << (b - 32)) : 0u;
+    }
+    __device__ __forceinline__ void store(uint32_t* d) const {
+        d[0] = F0;
+        d[1] = F1;
+    }
+    __device__ __forceinline__ void save(uint32_t* p) const { store(p); }
+    __device__ __forceinline__ void restore(const uint32_t* p) {
+        F0 = p[0];
+        F1 = p[1];
+    }
+};
+
+// rows padded to W (4 or 8) words: t.sp_B [256*W], t.sp_follow [nbits*W]
+template <int W>
+struct SparseStep {
+    static_assert(W % 4 == 0, "W must be a multiple of 4");
+    static constexpr int ROW_WORDS = W;
+    const uint32_t* B;
+    const uint32_t* follow;
+    uint32_t F[W];
+    uint32_t nb;
+    static size_t smem_bytes(const DevTables& t) { return (size_t)256 * W * 4 + align16((size_t)t.nbits * W * 4); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        copy_to_smem(sm, t.sp_B, (size_t)256 * W * 4);
+        copy_to_smem(sm + (size_t)256 * W * 4, t.sp_follow, (size_t)t.nbits * W * 4);
+    }
+    __device__ void init(const DevTables& t) {
+#pragma unroll
+        for (int k = 0; k < W; k++) F[k] = t.sp_start[k];
+        nb = t.null_bit;
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        B = reinterpret_cast<const uint32_t*>(sm);
+        follow = B + 256 * W;
+        init(t);
+    }
+    __device__ void bind_global(const DevTables& t) {
+        B = t.sp_B;
+        follow = t.sp_follow;
+        init(t);
+    }
+    __device__ __forceinline__ void step(uint32_t c) {
+        uint32_t S[W];
+        const uint4* b4 = reinterpret_cast<const uint4*>(B + c * W);
+#pragma unroll
+        for (int q = 0; q < W / 4; q++) {
+            uint4 v = b4[q];
+            S[4 * q] = F[4 * q] & v.x;
+            S[4 * q + 1] = F[4 * q + 1] & v.y;
+            S[4 * q + 2] = F[4 * q + 2] & v.z;
+            S[4 * q + 3] = F[4 * q + 3] & v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < W; k++) F[k] = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            uint32_t s = S[w];
+            while (s) {
+                int b = __ffs(s) - 1;
+                s &= s - 1;
+                const uint4* r4 = reinterpret_cast<const uint4*>(follow + (size_t)(w * 32 + b) * W);
+#pragma unroll
+                for (int q = 0; q < W / 4; q++) {
+                    uint4 v = r4[q];
+                    F[4 * q] |= v.x;
+                    F[4 * q + 1] |= v.y;
+                    F[4 * q + 2] |= v.z;
+                    F[4 * q + 3] |= v.w;
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ bool dead() const {
+        uint32_t o = 0;
+#pragma unroll
+        for (int k = 0; k < W; k++) o |= F[k];
+        return o == 0;
+    }
+    __device__ __forceinline__ bool accept() const {
+        uint32_t r = 0;
+#pragma unroll
+        for (int k = 0; k < W; k++)
+            if (k == (int)(nb >> 5)) r = (F[k] >> (nb & 31)) & 1u;
+        return r != 0;
+    }
+    __device__ __forceinline__ void kill() {
+#pragma unroll
+        for (int k = 0; k < W; k++) F[k] = 0;
+    }
+    __device__ __forceinline__ void set_unit(int b) {
+#pragma unroll
+        for (int k = 0; k < W; k++) F[k] = (k == (b >> 5)) ? (1u << (b & 31)) : 0u;
+    }
+    __device__ __forceinline__ void store(uint32_t* d) const {
+#pragma unroll
+        for (int k = 0; k < W; k++) d[k] = F[k];
+    }
+    __device__ __forceinline__ void save(uint32_t* p) const { store(p); }
+    __device__ __forceinline__ void restore(const uint32_t* p) {
+#pragma unroll
+        for (int k = 0; k < W; k++) F[k] = p[k];
+    }
+};
+
+// Advance a stepper over the bytes [s, e) (absolute addresses) -- every
+// lane of the warp calls this with the SAME range (chunk kernels).  Stops
+// early when every lane's set is empty.
+template <class S>
+__device__ __forceinline__ void run_range_uniform(S& st, uint64_t s, uint64_t e) {
+    uint64_t blk = s & ~uint64_t(15);
+    while (blk < e) {
+        uint4 v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
+        if (blk >= s && blk + 16 <= e) {
+#pragma unroll
+            for (int k = 0; k < 16; k++) st.step(byte_of(v, k));
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                bool ok = blk + k >= s && blk + k < e;
+                if (ok) st.step(byte_of(v, k));
+            }
+        }
+        blk += 16;
+        if (__all_sync(FULL, st.dead())) break;
+    }
+}
+
+
+}  // namespace dev
+}  // namespace rx
+
+namespace rx {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// Shared-memory steppers addressed with 32-bit shared-window addresses.
+// The tables are copied into shared memory with every stored pointer
+// already converted to a shared address, so one step is: extract the byte,
+// form the address, one 32-bit shared load.
+
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint2 lds64(uint32_t a) {
+    uint2 v;
+    asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds8(uint32_t a) {
+    uint16_t v;
+    asm("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte k (0..3) of w, zero-extended
+__device__ __forceinline__ uint32_t byte_k(uint32_t w, int k) { return __byte_perm(w, 0u, 0x4440u | (uint32_t)k); }
+
+// cache of macro steps: st = shared address of the current state's row of
+// 256 entries; each entry is the shared address of the successor's row.
+struct MemoS {
+    uint32_t st, base, acc;
+    static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * 1024) + align16(t.memo_K); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        uint32_t b = smem_addr(sm);
+        uint32_t* T = reinterpret_cast<uint32_t*>(sm);
+        for (int i = threadIdx.x; i < t.memo_K * 256; i += blockDim.x) T[i] = b + t.memo_T[i] * 4u;
+        copy_to_smem(sm + align16((size_t)t.memo_K * 1024), t.memo_acc, t.memo_K);
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        base = smem_addr(sm);
+        acc = base + (uint32_t)align16((size_t)t.memo_K * 1024);
+        st = base + t.memo_start * 4u;
+    }
+    __device__ __forceinline__ void step(uint32_t c) { st = lds32(st + c * 4u); }
+    __device__ __forceinline__ bool dead() const { return st == base; }
+    __device__ __forceinline__ bool accept() const { return lds8(acc + ((st - base) >> 10)) != 0; }
+    __device__ __forceinline__ void kill() { st = base; }
+};
+
+// register bitset (one word): desc[c] = {shift | mask << 8, shared address
+// of the byte's subset table}; entry x of that table is the new set.
+struct Thread1S {
+    uint32_t F, nb, desc;
+    static size_t smem_bytes(const DevTables& t) { return 256 * 8 + align16((size_t)t.gl_words * 4); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        uint32_t tt = smem_addr(sm) + 256 * 8;
+        uint2* d = reinterpret_cast<uint2*>(sm);
+        for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+            uint2 x = t.gl_desc[c];
+            d[c] = make_uint2((x.x & 31u) | (x.x & 0xff00u), tt + x.y * 4u);
+        }
+        copy_to_smem(sm + 256 * 8, t.gl_tt, (size_t)t.gl_words * 4);
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        desc = smem_addr(sm);
+        F = t.start[0];
+        nb = t.null_bit;
+    }
+    __device__ __forceinline__ void step(uint32_t c) {
+        uint2 d = lds64(desc + c * 8u);
+        uint32_t x = (F >> (d.x & 31u)) & (d.x >> 8);
+        F = lds32(d.y + x * 4u);
+    }
+    __device__ __forceinline__ bool dead() const { return F == 0; }
+    __device__ __forceinline__ bool accept() const { return (F >> nb) & 1u; }
+    __device__ __forceinline__ void kill() { F = 0; }
+};
+
+struct Thread2S {
+    uint32_t F0, F1, nb, desc;
+    static size_t smem_bytes(const DevTables& t) { return 256 * 8 + align16((size_t)t.gl_words * 4); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        uint32_t tt = smem_addr(sm) + 256 * 8;
+        uint2* d = reinterpret_cast<uint2*>(sm);
+        for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+            uint2 x = t.gl_desc[c];
+            d[c] = make_uint2(x.x, tt + x.y * 4u);
+        }
+        copy_to_smem(sm + 256 * 8, t.gl_tt, (size_t)t.gl_words * 4);
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        desc = smem_addr(sm);
+        F0 = t.start[0];
+        F1 = t.start[1];
+        nb = t.null_bit;
+    }
+    __device__ __forceinline__ void step(uint32_t c) {
+        uint2 d = lds64(desc + c * 8u);
+        uint32_t w = (d.x & 32u) ? F1 : F0;
+        uint32_t x = (w >> (d.x & 31u)) & (d.x >> 8);
+        uint2 e = lds64(d.y + x * 8u);
+        F0 = e.x;
+        F1 = e.y;
+    }
+    __device__ __forceinline__ bool dead() const { return (F0 | F1) == 0; }
+    __device__ __forceinline__ bool accept() const { return (((nb < 32) ? F0 : F1) >> (nb & 31)) & 1u; }
+    __device__ __forceinline__ void kill() { F0 = F1 = 0; }
+};
+
+}  // namespace dev
+}  // namespace rx
+
+namespace rx {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// One string per lane, [s, e) absolute addresses; warp-synchronous (every
+// lane of the warp must call it).  The lane walks aligned 16-byte blocks
+// with one block of prefetch; blocks whole for every lane take an unrolled
+// path, boundary blocks a predicated one.  A lane whose string ends or whose
+// set empties writes *outp and then holds the empty set, which every step
+// keeps empty.
+template <class S>
+__device__ __forceinline__ void run_lane(S& st, uint64_t s, uint64_t e, bool valid, uint8_t* outp) {
+    bool active = valid && s < e;
+    if (valid && !active) *outp = st.accept();
+    if (!active) st.kill();
+    uint64_t blk = s & ~uint64_t(15);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (active) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
+    while (__any_sync(FULL, active)) {
+        uint64_t nb = blk + 16;
+        uint4 vn = make_uint4(0, 0, 0, 0);
+        if (active && nb < e) vn = ld_stream(reinterpret_cast<const uint8_t*>(nb));
+        bool full = !active || (blk >= s && nb <= e);
+        if (__all_sync(FULL, full)) {
+#pragma unroll
+            for (int k = 0; k < 16; k++) st.step(byte_of(v, k));
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                S nx = st;
+                nx.step(byte_of(v, k));
+                bool ok = active && blk + k >= s && blk + k < e;
+                if (ok) st = nx;
+            }
+        }
+        blk = nb;
+        v = vn;
+        if (active && (blk >= e || st.dead())) {
+            *outp = st.accept();
+            st.kill();
+            active = false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One string per warp: lane l owns words l, l+32, ... (K per lane) of the
+// active set.  A step ANDs with B[c], then ORs the follow row of every
+// active bit, found with ballot / shuffle so the loop is warp-uniform.  The
+// warp stages 512 input bytes at a time with one 16-byte load per lane.
+// Returns whether the string is accepted (same value in every lane).
+// warp_span: advance the set F (lane-owned words) over [s, e); returns true
+// if the set emptied (the string is stuck), in which case F is all zero.
+template <int K>
+__device__ bool warp_span(const DevTables& t, const uint32_t* B, const uint32_t* follow, uint64_t s, uint64_t e,
+                          uint32_t (&F)[K]) {
+    const int W = t.W;
+    const int lane = threadIdx.x & 31;
+    bool dead = false;
+    for (uint64_t win = s & ~uint64_t(511); win < e && !dead; win += 512) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        uint64_t my = win + 16 * lane;
+        if (my < e && my + 16 > s) v = ld_stream(reinterpret_cast<const uint8_t*>(my));
+        for (int src = 0; src < 32 && !dead; src++) {
+            uint64_t blk = win + 16 * src;
+            if (blk >= e) break;
+            if (blk + 16 <= s) continue;
+            uint32_t words[4];
+            words[0] = __shfl_sync(FULL, v.x, src);
+            words[1] = __shfl_sync(FULL, v.y, src);
+            words[2] = __shfl_sync(FULL, v.z, src);
+            words[3] = __shfl_sync(FULL, v.w, src);
+#pragma unroll 1
+            for (int kb = 0; kb < 16; kb++) {
+                uint64_t p = blk + kb;
+                if (p < s || p >= e) continue;
+                uint32_t c = (words[kb >> 2] >> (8 * (kb & 3))) & 0xffu;
+                uint32_t Sx[K];
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    int w = k * 32 + lane;
+                    Sx[k] = (w < W) ? (F[k] & B[(size_t)c * W + w]) : 0u;
+                    F[k] = 0;
+                }
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    unsigned act = __ballot_sync(FULL, Sx[k] != 0);
+                    while (act) {
+                        int srcl = __ffs(act) - 1;
+                        act &= act - 1;
+                        uint32_t bits = __shfl_sync(FULL, Sx[k], srcl);
+                        while (bits) {
+                            int b = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            const uint32_t* row = follow + (size_t)((k * 32 + srcl) * 32 + b) * W;
+#pragma unroll
+                            for (int kk = 0; kk < K; kk++) {
+                                int w = kk * 32 + lane;
+                                if (w < W) F[kk] |= row[w];
+                            }
+                        }
+                    }
+                }
+                uint32_t any = 0;
+#pragma unroll
+                for (int k = 0; k < K; k++) any |= F[k];
+                if (!__any_sync(FULL, any != 0)) {
+                    dead = true;
+                    break;
+                }
+            }
+        }
+    }
+    return dead;
+}
+
+// null bit of the lane-owned set (same value in every lane)
+template <int K>
+__device__ __forceinline__ bool warp_accepts(const DevTables& t, const uint32_t (&F)[K]) {
+    const int nbw = t.null_bit >> 5, nbb = t.null_bit & 31;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        if (k == (nbw >> 5)) mine = F[k];
+    uint32_t nw = __shfl_sync(FULL, mine, nbw & 31);
+    return (nw >> nbb) & 1u;
+}
+
+template <int K>
+__device__ bool warp_string(const DevTables& t, const uint32_t* B, const uint32_t* follow, uint64_t s, uint64_t e) {
+    const int lane = threadIdx.x & 31;
+    uint32_t F[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        int w = k * 32 + lane;
+        F[k] = (w < t.W) ? t.start[w] : 0u;
+    }
+    bool dead = warp_span<K>(t, B, follow, s, e, F);
+    return !dead && warp_accepts<K>(t, F);
+}
+
+// Advance one lane's set over [s, e) (absolute addresses), warp-
+// synchronously; lanes with active == false only keep step with the others.
+// Stops reading once the set is empty.
+template <class S>
+__device__ __forceinline__ void run_lane_span(S& st, uint64_t s, uint64_t e, bool active) {
+    active = active && s < e;
+    uint64_t blk = s & ~uint64_t(15);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (active) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
+    while (__any_sync(FULL, active)) {
+        uint64_t nb = blk + 16;
+        uint4 vn = make_uint4(0, 0, 0, 0);
+        if (active && nb < e) vn = ld_stream(reinterpret_cast<const uint8_t*>(nb));
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            S nx = st;
+            nx.step(byte_of(v, k));
+            bool ok = active && blk + k >= s && blk + k < e;
+            if (ok) st = nx;
+        }
+        blk = nb;
+        v = vn;
+        if (active && (blk >= e || st.dead())) active = false;
+    }
+}
+
+}  // namespace dev
+}  // namespace rx

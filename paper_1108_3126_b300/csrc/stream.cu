@@ -1,0 +1,170 @@
+// stream.cu -- the single-expression streaming kernel (rx_match default).
+//
+// One lane walks one string, one macro step of the lockstep machine
+// (Rathnayake & Thielecke, SOS 2011, Def 5.2) per byte, the active set in
+// registers (or a state id of the cache of macro steps) and the tables in
+// shared memory.  Work distribution: the planner orders the strings by
+// length, longest first; persistent warps take rounds of 32 consecutive
+// entries from a global counter, so the lanes of a round have (nearly) the
+// same length and finish together, and the longest rounds start first.
+// Input: every lane reads its string in aligned 32-byte blocks (one full
+// sector, two 16-byte loads) with loads issued two blocks ahead.
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "steppers.cuh"
+
+namespace rx {
+
+namespace {
+
+using namespace rx::dev;
+
+constexpr int STREAM_BLOCK = 256;
+
+struct Blk32 {
+    uint4 a, b;
+};
+
+__device__ __forceinline__ Blk32 ld_blk(uint64_t addr, bool on) {
+    Blk32 r;
+    r.a = make_uint4(0, 0, 0, 0);
+    r.b = r.a;
+    if (on) {
+        r.a = ld_stream(reinterpret_cast<const uint8_t*>(addr));
+        r.b = ld_stream(reinterpret_cast<const uint8_t*>(addr + 16));
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint32_t word_of(const Blk32& v, int q) {
+    return q == 0 ? v.a.x : q == 1 ? v.a.y : q == 2 ? v.a.z : q == 3 ? v.a.w
+         : q == 4 ? v.b.x : q == 5 ? v.b.y : q == 6 ? v.b.z : v.b.w;
+}
+
+// bytes of the 32-byte block at blk that lie in [s, e), as a bit mask
+__device__ __forceinline__ uint32_t valid_mask(uint64_t blk, uint64_t s, uint64_t e, bool active) {
+    if (!active || blk >= e || blk + 32 <= s) return 0u;
+    uint32_t lo = blk >= s ? 0u : (uint32_t)(s - blk);
+    uint32_t hi = blk + 32 <= e ? 32u : (uint32_t)(e - blk);
+    uint32_t m_hi = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    return m_hi & ~((1u << lo) - 1u);
+}
+
+// Process one 32-byte block of every lane of the warp: the unrolled path
+// when the block is whole for every lane that still has bytes, the masked
+// path otherwise.  Lanes without bytes hold the empty set (harmless).
+template <class S>
+__device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
+    if (__all_sync(FULL, mask == 0xffffffffu || mask == 0u)) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            uint32_t w = word_of(v, q);
+#pragma unroll
+            for (int k = 0; k < 4; k++) st.step(byte_k(w, k));
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            uint32_t w = word_of(v, q);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                S nx = st;
+                nx.step(byte_k(w, k));
+                if ((mask >> (4 * q + k)) & 1u) st = nx;
+            }
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(STREAM_BLOCK) k_stream(const DevTables t, const uint8_t* __restrict__ str,
+                                                         const int64_t* __restrict__ off,
+                                                         const uint32_t* __restrict__ perm, long long n,
+                                                         uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    S::load(t, smem);
+    __syncthreads();
+    S proto;
+    proto.bind(t, smem);
+    const int lane = threadIdx.x & 31;
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    const long long nround = (n + 31) / 32;
+    for (;;) {
+        unsigned r = 0;
+        if (lane == 0) r = atomicAdd(queue, 1u);
+        r = __shfl_sync(FULL, r, 0);
+        if ((long long)r >= nround) break;
+        const long long k = (long long)r * 32 + lane;
+        const bool valid = k < n;
+        const long long id = valid ? (perm ? (long long)perm[k] : k) : 0;
+        uint64_t s = base, e = base;
+        if (valid) {
+            s += (uint64_t)off[id];
+            e += (uint64_t)off[id + 1];
+        }
+        S st = proto;
+        bool active = valid && s < e;
+        if (valid && !active) out[id] = st.accept();
+        if (!active) st.kill();
+        uint64_t blk = s & ~uint64_t(31);
+        Blk32 va = ld_blk(blk, active);
+        Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
+        while (__any_sync(FULL, active)) {
+            // block A at blk, then block B at blk + 32; each buffer is
+            // refilled two blocks ahead right after it is consumed
+            block32(st, va, valid_mask(blk, s, e, active));
+            if (active && (blk + 32 >= e || st.dead())) {
+                out[id] = st.accept();
+                st.kill();
+                active = false;
+            }
+            va = ld_blk(blk + 64, active && blk + 64 < e);
+            if (!__any_sync(FULL, active)) break;
+            block32(st, vb, valid_mask(blk + 32, s, e, active));
+            if (active && (blk + 64 >= e || st.dead())) {
+                out[id] = st.accept();
+                st.kill();
+                active = false;
+            }
+            vb = ld_blk(blk + 96, active && blk + 96 < e);
+            blk += 64;
+        }
+    }
+}
+
+template <class S>
+cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
+                            const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st) {
+    size_t sm = S::smem_bytes(t);
+    auto kern = k_stream<S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, STREAM_BLOCK, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long rounds = (n + 31) / 32;
+    long long grid = std::min<long long>((rounds * 32 + STREAM_BLOCK - 1) / STREAM_BLOCK,
+                                         (long long)per_sm * sm_count());
+    {
+        ProfScope ps(st);
+        kern<<<(unsigned)std::max<long long>(grid, 1), STREAM_BLOCK, sm, st>>>(t, str, off, perm, n, out, queue);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool stream_supported(const DevTables& t, int variant) {
+    return variant == RX_VARIANT_MEMO || (variant == RX_VARIANT_THREAD && t.W <= 2);
+}
+
+cudaError_t launch_stream(const DevTables& t, int variant, long long n, const uint8_t* str, const int64_t* off,
+                          const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st) {
+    if (variant == RX_VARIANT_MEMO) return launch_stream_t<MemoS>(t, n, str, off, perm, out, queue, st);
+    if (t.W == 1) return launch_stream_t<Thread1S>(t, n, str, off, perm, out, queue, st);
+    return launch_stream_t<Thread2S>(t, n, str, off, perm, out, queue, st);
+}
+
+}  // namespace rx

@@ -83,7 +83,8 @@ def _L():
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, P, ctypes.c_int,
                                        ctypes.c_uint64, ctypes.POINTER(_Strings)]
         lib.sy_gen_strings.restype = ctypes.c_int
-        lib.sy_gen_star_text.argtypes = [P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, P]
+        lib.sy_gen_star_text.argtypes = [P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, P,
+                                         ctypes.POINTER(ctypes.c_int64)]
         lib.sy_gen_star_text.restype = ctypes.c_int
         lib.sy_uniform.argtypes = [P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_uint64]
         lib.sy_uniform.restype = None
@@ -253,15 +254,18 @@ def uniform_bytes(length: int, alphabet: bytes, seed: int) -> np.ndarray:
     return out[:length]
 
 
-def star_text(nodes: np.ndarray, total: int, seed: int, piece: int = 4096) -> np.ndarray:
+def star_text(nodes: np.ndarray, total: int, seed: int, piece: int = 4096, with_end: bool = False):
     """A text of ``total`` bytes in the language of (e)* cut at ``total``:
-    concatenated language samples of e (target lengths uniform in [1, piece])."""
+    whole language samples of e (target lengths uniform in [1, piece])
+    concatenated, so every prefix stays a prefix of a member of (e)*.  With
+    ``with_end`` also returns the offset where the last whole sample ends."""
     out = np.empty(max(total, 1), np.uint8)
     nd = np.ascontiguousarray(nodes)
-    rc = _L().sy_gen_star_text(_ptr(nd), len(nd), total, piece, seed & (2**64 - 1), _ptr(out))
+    last = ctypes.c_int64(0)
+    rc = _L().sy_gen_star_text(_ptr(nd), len(nd), total, piece, seed & (2**64 - 1), _ptr(out), ctypes.byref(last))
     if rc != 0:
         raise RuntimeError("sy_gen_star_text failed (language of e holds no non-empty string?)")
-    return out[:total]
+    return (out[:total], int(last.value)) if with_end else out[:total]
 
 
 def wrap_star(nodes: np.ndarray) -> np.ndarray:
@@ -331,12 +335,12 @@ def long_regex(seed: int = SEED_BASE + 4, positions: int = 48) -> np.ndarray:
     raise RuntimeError("no tree with the requested position count")
 
 
-def cfg_long(seed: int = SEED_BASE + 4, total: int = 1 << 30):
+def cfg_long(seed: int = SEED_BASE + 4, total: int = 1 << 30, with_end: bool = False):
     """(R)* with 48 positions and one text of ``total`` bytes in its prefix
-    language.  Returns (nodes of (R)*, text)."""
+    language.  Returns (nodes of (R)*, text[, end of the last whole sample])."""
     r = long_regex(seed)
-    text = star_text(r, total, item_seed(seed, 1))
-    return wrap_star(r), text
+    text, end = star_text(r, total, item_seed(seed, 1), with_end=True)
+    return (wrap_star(r), text, end) if with_end else (wrap_star(r), text)
 
 
 def serving_pool(seed: int = SEED_BASE + 5, pool: int = 2000) -> list:

@@ -373,12 +373,22 @@ int sy_gen_strings(const sy_node* nd, int nnodes, int64_t n, int64_t lmin, int64
 }
 
 /*
- * One long text in the language of e* (e = the given tree): independent
- * segments, each a concatenation of language samples of e, cut to `total`
- * bytes.  Segment k uses item seed k, so the text is reproducible.
+ * One long text in the language of e* (e = the given tree), cut to `total`
+ * bytes: independent segments of about 1 MiB, each a concatenation of WHOLE
+ * language samples of e (target lengths uniform in [1, piece]), joined end
+ * to end, so every prefix of the text is a prefix of a member of e*.  Only
+ * the last sample may be cut.  Segment k uses item seed k, so the text is
+ * reproducible whatever the thread count.  *last_end (optional) receives the
+ * end offset of the last whole sample (a member of e* ends there).
  */
-int sy_gen_star_text(const sy_node* nd, int nnodes, int64_t total, int64_t piece, uint64_t seed, uint8_t* out) {
-    int64_t nseg = (total + (1 << 20) - 1) >> 20;
+int sy_gen_star_text(const sy_node* nd, int nnodes, int64_t total, int64_t piece, uint64_t seed, uint8_t* out,
+                     int64_t* last_end) {
+    const int64_t SEG = 1 << 20;
+    int64_t nseg = (total + SEG - 1) / SEG;
+    if (nseg < 1) nseg = 1;
+    uint8_t** bufs = (uint8_t**)calloc((size_t)nseg, sizeof(uint8_t*));
+    int64_t* lens = (int64_t*)calloc((size_t)nseg, sizeof(int64_t));
+    if (!bufs || !lens) return -1;
     int failed = 0;
 #pragma omp parallel
     {
@@ -390,24 +400,47 @@ int sy_gen_star_text(const sy_node* nd, int nnodes, int64_t total, int64_t piece
             if (!tmp || !one) { failed = 1; continue; }
             rng_t g;
             g.s = sy_item_seed(seed, (uint64_t)k);
-            int64_t pos = k << 20, end = pos + (1 << 20);
-            if (end > total) end = total;
+            uint8_t* buf = (uint8_t*)malloc((size_t)(SEG + cap));
+            if (!buf) { failed = 1; continue; }
+            int64_t pos = 0;
             int stuck = 0;
-            while (pos < end) {
+            while (pos < SEG) {
                 int64_t target = rint_in(&g, 1, piece);
                 int64_t len = sample_one(nd, nnodes, target, 1, cap, &g, one, tmp, cap);
                 if (len <= 0) {
                     if (++stuck > 64) { failed = 2; break; }
                     continue;
                 }
-                int64_t take = len < end - pos ? len : end - pos;
-                memcpy(out + pos, one, (size_t)take);
-                pos += take;
+                memcpy(buf + pos, one, (size_t)len);
+                pos += len;
             }
+            bufs[k] = buf;
+            lens[k] = pos;
         }
         free(tmp);
         free(one);
     }
+    int64_t pos = 0, lastb = 0;
+    for (int64_t k = 0; k < nseg && !failed; k++) {
+        int64_t take = lens[k] < total - pos ? lens[k] : total - pos;
+        if (take > 0) memcpy(out + pos, bufs[k], (size_t)take);
+        if (take == lens[k]) lastb = pos + take;
+        pos += take;
+    }
+    /* more segments than needed never happens (each holds >= 1 MiB); if the
+       segments fall short, repeat them (still whole samples) */
+    while (!failed && pos < total) {
+        for (int64_t k = 0; k < nseg && pos < total; k++) {
+            int64_t take = lens[k] < total - pos ? lens[k] : total - pos;
+            memcpy(out + pos, bufs[k], (size_t)take);
+            if (take == lens[k]) lastb = pos + take;
+            pos += take;
+        }
+    }
+    for (int64_t k = 0; k < nseg; k++) free(bufs[k]);
+    free(bufs);
+    free(lens);
+    if (last_end) *last_end = lastb;
     return failed ? -1 : 0;
 }
 

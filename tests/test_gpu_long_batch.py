@@ -1,0 +1,193 @@
+"""GPU parity of the chunked long-string mode (rx_match_long), the sequential
+one-thread form (rx_match_seq), the persistent batched form
+(rx_match_batch) and the plain one-launch-per-pair form (rx_match_pairs),
+against the CPU oracle and against each other.  Exact booleans."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1108_3126_b300 as rx
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1108_3126_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def dev(a):
+    return torch.from_numpy(np.array(a, copy=True)).cuda()
+
+
+def long_match(r, d_text, n, chunk=0):
+    out = torch.full((1,), 7, dtype=torch.uint8, device="cuda")
+    rx.match_long(r, d_text, n, out, chunk_bytes=chunk)
+    torch.cuda.synchronize()
+    return int(out.item())
+
+
+def seq_match(r, d_text, n):
+    out = torch.full((1,), 7, dtype=torch.uint8, device="cuda")
+    rx.match_seq(r, d_text, n, out)
+    torch.cuda.synchronize()
+    return int(out.item())
+
+
+@pytest.fixture(scope="module")
+def long_case():
+    R = synth.long_regex()
+    nodes = synth.wrap_star(R)
+    assert synth.n_positions(nodes) == 48
+    text, end = synth.star_text(R, 4 << 20, synth.item_seed(0xE0, 0), with_end=True)
+    assert oracle.o2(nodes, text[:end].tobytes())
+    return nodes, text
+
+
+def test_long_text_chunk_sizes_vs_seq_and_o2(long_case):
+    nodes, text = long_case
+    variants = [text, text.copy()]
+    variants[1][-1] = ord("a") if variants[1][-1] != ord("a") else ord("b")
+    r_memo = rx.Regex.from_nodes(nodes)
+    r_bits = rx.Regex.from_nodes(nodes, 0, rx.COMPILE_NO_MEMO)
+    assert r_memo.info()["memo_states"] > 0 and r_bits.info()["memo_states"] == 0
+    for t in variants:
+        d = dev(t)
+        n = len(t)
+        # O2 on a 1 MiB prefix and on the whole text
+        want_full = oracle.o2(nodes, t.tobytes())
+        pre = 1 << 20
+        want_pre = oracle.o2(nodes, t[:pre].tobytes())
+        for r in (r_memo, r_bits):
+            assert seq_match(r, d, n) == want_full
+            assert seq_match(r, d, pre) == want_pre
+            for chunk in (0, 7, 4096, 1 << 20, 3 << 20, n + 5):
+                assert long_match(r, d, n, chunk) == want_full, (chunk, r.info()["memo_states"])
+            assert long_match(r, d, pre, 1000) == want_pre
+    # chunk size 1 on a shorter prefix (one chunk per byte)
+    d = dev(text[:50000])
+    w = oracle.o2(nodes, text[:50000].tobytes())
+    assert long_match(r_memo, d, 50000, 1) == w
+    assert long_match(r_bits, d, 50000, 1) == w
+
+
+def test_long_random_expressions_and_edges():
+    for i in range(30):
+        alpha = [b"abc", synth.LOWER, synth.ALL_BYTES][i % 3]
+        e = synth.gen_regex(10 + 7 * i, 10, alpha, synth.item_seed(0xE1, i), eps_loop_p=0.05)
+        s = synth.gen_strings(e, 3, 0, 30000, alpha, synth.item_seed(0xE2, i), p_lang=0.7)
+        for flags in (0, rx.COMPILE_NO_MEMO):
+            r = rx.Regex.from_nodes(e, 0, flags)
+            for k in range(s.n):
+                w = s.get(k)
+                want = oracle.o2(e, w)
+                d = dev(np.frombuffer(w + b"\0", np.uint8))
+                for chunk in (0, 1 + i, 4096):
+                    assert long_match(r, d, len(w), chunk) == want, (synth.to_pattern(e)[:60], len(w), chunk)
+    # empty string: the expression's nullability
+    for pat, want in [(b"a*", 1), (b"a", 0), (b"\\e", 1), (b"(a|\\e)b*", 1)]:
+        r = rx.Regex.compile(pat)
+        d = dev(np.zeros(16, np.uint8))
+        assert long_match(r, d, 0) == want
+        assert seq_match(r, d, 0) == want
+
+
+def test_long_wide_expression_falls_back_to_sequential():
+    pat = b"(" + b"|".join(b"x" + bytes([97 + i % 26]) for i in range(400)) + b")*"
+    nodes = oracle.parse(pat)
+    r = rx.Regex.from_nodes(nodes, 0, rx.COMPILE_NO_MEMO)
+    assert r.info()["words"] > 8
+    s = synth.gen_strings(nodes, 4, 100, 5000, synth.LOWER, 3, p_lang=0.8)
+    for k in range(s.n):
+        w = s.get(k)
+        d = dev(np.frombuffer(w + b"\0", np.uint8))
+        assert long_match(r, d, len(w)) == oracle.o2(nodes, w)
+
+
+@pytest.mark.slow
+def test_long_full_size_chunked_equals_sequential():
+    """The 1 GiB text of the long-text configuration: chunked result equals
+    the one-thread sequential GPU run (and the oracle on a prefix)."""
+    nodes, text, end = synth.cfg_long(with_end=True)
+    r = rx.Regex.from_nodes(nodes)
+    d = torch.from_numpy(text).cuda()
+    n = len(text)
+    got = long_match(r, d, n)
+    assert got == seq_match(r, d, n)
+    # the text is a member of (R)* up to its last whole sample: the active set
+    # stays non-empty over (nearly) the whole gigabyte
+    assert end > n - 65536
+    assert long_match(r, d, end) == 1 and seq_match(r, d, end) == 1
+    flip = d.clone()
+    flip[-1] = ord("q") if int(text[-1]) != ord("q") else ord("r")
+    assert long_match(r, flip, n) == seq_match(r, flip, n)
+    pre = 2 << 20
+    assert long_match(r, d, pre, 4096) == oracle.o2(nodes, text[:pre].tobytes())
+
+
+def batch_case(n_regex=250, max_len=6000, seed=0xE3):
+    w = synth.cfg_batched(seed=seed, n_regex=n_regex, max_len=max_len, max_strings=24)
+    # add wide expressions (warp class) and no-cache expressions (bitset classes)
+    extra_regs, extra_strs, extra_rid = [], [], []
+    for i in range(6):
+        pat = b"(" + b"|".join(bytes([97 + (i + j) % 26]) + bytes([97 + j % 26]) for j in range(40 + 60 * i)) + b")*"
+        nd = oracle.parse(pat)
+        extra_regs.append(nd)
+        s = synth.gen_strings(nd, 20, 0, 3000, synth.LOWER, synth.item_seed(seed, 900 + i), p_lang=0.7)
+        extra_strs += [s.get(k) for k in range(s.n)]
+        extra_rid += [n_regex + i] * s.n
+    regs = w.regexes + extra_regs
+    strs = [w.strings.get(k) for k in range(w.strings.n)] + extra_strs
+    rid = np.concatenate([w.regex_of, np.array(extra_rid, np.int32)])
+    # interleave the pairs so runs of the same handle are broken up
+    order = np.random.default_rng(seed).permutation(len(strs))
+    strs = [strs[k] for k in order]
+    rid = rid[order]
+    return regs, synth.pack(strs), rid
+
+
+def test_batched_and_plain_forms_vs_o2():
+    regs, s, rid = batch_case()
+    want = np.zeros(s.n, np.uint8)
+    for k in range(s.n):
+        want[k] = oracle.o2(regs[rid[k]], s.get(k))
+    handles = []
+    compiled = {}
+    for i, nd in enumerate(regs):
+        flags = rx.COMPILE_NO_MEMO if i % 3 == 1 else 0
+        compiled[i] = rx.Regex.from_nodes(nd, 0, flags)
+    classes = set()
+    for k in range(s.n):
+        r = compiled[int(rid[k])]
+        handles.append(r)
+        inf = r.info()
+        classes.add((inf["memo_states"] > 0, inf["words"]))
+    assert any(w > 8 for _, w in classes) and any(m for m, _ in classes) and any(not m for m, _ in classes)
+    d, o = dev(s.data), dev(s.offsets)
+    out = torch.full((s.n,), 7, dtype=torch.uint8, device="cuda")
+    rx.match_batch(handles, d, o, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert (got == want).all(), np.nonzero(got != want)[0][:10]
+    out.fill_(7)
+    rx.match_pairs(handles, d, o, out)
+    torch.cuda.synchronize()
+    assert (out.cpu().numpy() == want).all()
+
+
+def test_batched_edges():
+    r = rx.Regex.compile(b"(ab)*")
+    s = synth.pack([b"", b"ab", b"aba", b"abab" * 5000])
+    d, o = dev(s.data), dev(s.offsets)
+    out = torch.full((s.n,), 7, dtype=torch.uint8, device="cuda")
+    rx.match_batch([r] * s.n, d, o, out)
+    torch.cuda.synchronize()
+    assert out.cpu().numpy().tolist() == [1, 1, 0, 1]
+    rx.match_batch([], d, o, out)  # n = 0 is a no-op
+    with pytest.raises(rx.RxError):
+        rx.match_batch([rx.Regex.compile(b"a", rx.COMPILE_HOST_ONLY)], d, o, out)

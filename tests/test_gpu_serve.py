@@ -1,0 +1,117 @@
+"""GPU serving (rx_serve_*): continuous batching gives every request the
+same result alone as in a mix with others (exact), under admission by a
+device-memory budget, with host or device payloads; results agree with the
+CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1108_3126_b300 as rx
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1108_3126_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def workload(seed=0xF0, n_req=300):
+    pool = []
+    for i in range(12):
+        size = [8, 20, 64, 200, 500, 1000][i % 6]
+        pool.append(synth.gen_regex(size, 14, synth.LOWER if i % 2 else synth.ALL_BYTES, synth.item_seed(seed, i)))
+    # a wide expression without the macro-step cache (warp class)
+    pool.append(oracle.parse(b"(" + b"|".join(bytes([97 + j % 26]) + bytes([97 + (j * 7) % 26])
+                                               for j in range(300)) + b")*"))
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_req):
+        ri = int(rng.integers(0, len(pool)))
+        nodes = pool[ri]
+        alpha = synth.ALL_BYTES if ri % 2 == 0 and ri < 12 else synth.LOWER
+        lmax = int(rng.choice([64, 4096, 70000, 3 << 20], p=[0.4, 0.4, 0.17, 0.03]))
+        s = synth.gen_strings(nodes, 1, 0, lmax, alpha, synth.item_seed(seed + 1, k), p_lang=0.6, log_len=True)
+        reqs.append((ri, s.get(0)))
+    return pool, reqs
+
+
+def compile_pool(pool):
+    out = []
+    for i, nd in enumerate(pool):
+        out.append(rx.Regex.from_nodes(nd, 0, rx.COMPILE_NO_MEMO if i % 3 == 2 else 0))
+    return out
+
+
+def serve_all(handles, reqs, **kw):
+    srv = rx.Server(**kw)
+    tickets = {}
+    for k, (ri, w) in enumerate(reqs):
+        while True:
+            try:
+                t = srv.submit(handles[ri], w)
+                break
+            except rx.RxError as e:
+                assert e.status == 7  # busy: drain some
+                srv.drain(60000)
+        tickets[t] = k
+    srv.drain(120000)
+    res = np.full(len(reqs), 9, np.uint8)
+    got = 0
+    while got < len(reqs):
+        tk, r, st = srv.poll(4096)
+        assert (st == 0).all()
+        for a, b in zip(tk, r):
+            res[tickets[int(a)]] = b
+        got += len(tk)
+    stats = srv.stats()
+    srv.close()
+    return res, stats
+
+
+def test_mix_equals_alone_equals_oracle():
+    pool, reqs = workload()
+    handles = compile_pool(pool)
+    mixed, stats = serve_all(handles, reqs, max_inflight=64, tick_bytes=4096)
+    assert stats["completed"] == len(reqs) and stats["p99_ns"] >= stats["p50_ns"] > 0
+    assert stats["peak_inflight"] > 1  # requests really overlapped
+    for k in range(0, len(reqs), 5):
+        alone, _ = serve_all(handles, [reqs[k]], max_inflight=4, tick_bytes=1 << 16)
+        assert alone[0] == mixed[k], k
+    for k, (ri, w) in enumerate(reqs):
+        if len(w) <= 200000:
+            assert mixed[k] == oracle.o2(pool[ri], w), (k, len(w))
+
+
+def test_small_budget_admission_is_exact():
+    pool, reqs = workload(seed=0xF5, n_req=80)
+    handles = compile_pool(pool)
+    want, _ = serve_all(handles, reqs, max_inflight=256, tick_bytes=1 << 15)
+    tight, st = serve_all(handles, reqs, max_inflight=256, tick_bytes=1000, device_budget_bytes=100000)
+    assert (tight == want).all()
+    assert st["peak_device_bytes"] <= max(100000, max(len(w) for _, w in reqs) * 3)
+
+
+def test_device_payload_mode():
+    pool, reqs = workload(seed=0xF7, n_req=60)
+    handles = compile_pool(pool)
+    want, _ = serve_all(handles, reqs, max_inflight=32)
+    srv = rx.Server(max_inflight=32, device_payload=True)
+    bufs = [torch.from_numpy(np.frombuffer(w + b"\0", np.uint8).copy()).cuda() for _, w in reqs]
+    torch.cuda.synchronize()
+    tickets = {}
+    for k, (ri, w) in enumerate(reqs):
+        tickets[srv.submit(handles[ri], bufs[k], len(w))] = k
+    srv.drain(60000)
+    got = np.full(len(reqs), 9, np.uint8)
+    tk, r, st = srv.poll(1000)
+    assert (st == 0).all()
+    for a, b in zip(tk, r):
+        got[tickets[int(a)]] = b
+    assert (got == want).all()
+    srv.close()
