@@ -294,7 +294,7 @@ def run_streaming(args, world, rank, local):
 
     if rank != 0:
         return
-    kname = {1: "k_thread<MemoStep>", 2: "k_thread<Thread1Step|Thread2Step>", 3: "k_thread<SparseStep>",
+    kname = {1: "k_stream<MemoS>", 2: "k_stream<Thread1S|Thread2S>", 3: "k_thread<SparseStep>",
              4: "k_warp"}[variant if variant else (1 if info["variants"] & 2 else 2)]
     src_hash = kernel_source_hash()
     traffic = TRAFFIC.get((kname, src_hash))
@@ -327,13 +327,224 @@ def run_streaming(args, world, rank, local):
     print(json.dumps(line))
 
 
+def _dev_setup(local):
+    import torch
+    from paper_1108_3126_b300 import build as rxbuild
+    rxbuild.build()
+    torch.cuda.set_device(local)
+    return torch.device("cuda", local)
+
+
+def _time(fn, reps, stream, dev):
+    import torch
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / reps
+
+
+def run_batched(args, world, rank, local):
+    """10,000 expressions x 1-64 strings each, one persistent launch
+    (rx_match_batch) against one launch per pair (rx_match_pairs)."""
+    import torch
+    import paper_1108_3126_b300 as rx
+    import synth
+    dev = _dev_setup(local)
+    t0 = time.perf_counter()
+    w = synth.cfg_batched(n_regex=args.regexes)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    handles = [rx.Regex.from_nodes(nd) for nd in w.regexes]
+    compile_s = time.perf_counter() - t0
+    hs = rx.handle_array([handles[i] for i in w.regex_of])
+    s = w.strings
+    n, total = s.n, int(s.offsets[-1])
+    d_str = torch.from_numpy(s.data).to(dev)
+    d_off = torch.from_numpy(s.offsets).to(dev)
+    out = torch.zeros(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        rx.match_batch(hs, d_str, d_off, out, stream=stream)
+    rx.profile_read()
+    rx.profile_enable(True)
+    ms = _time(lambda: rx.match_batch(hs, d_str, d_off, out, stream=stream), args.steps, stream, dev)
+    rx.profile_enable(False)
+    launches, timed, kms = rx.profile_read()
+    res_batch = out.cpu().numpy().copy()
+    out.fill_(7)
+    rx.match_pairs(hs, d_str, d_off, out, stream=stream)  # warm
+    plain_ms = _time(lambda: rx.match_pairs(hs, d_str, d_off, out, stream=stream), 1, stream, dev)
+    assert (out.cpu().numpy() == res_batch).all(), "batched and plain forms disagree"
+    infos = [h.info() for h in handles]
+    line = {"metric": METRIC, "workload": "batched", "value": round(total / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"batched uneven: {len(handles)} regexes 8-512 AST nodes (log-uniform, depth<=12, "
+                                   "5% (eps*|e)* loops) over 256 bytes; 1-64 strings each, L log-uniform 1 B-64 KiB",
+                       "pairs": n, "total_bytes": total, "positions_max": max(i["positions"] for i in infos),
+                       "memo_share": sum(1 for i in infos if i["memo_states"]) / len(infos),
+                       "gen_s": round(gen_s, 1), "compile_s": round(compile_s, 2)},
+            "plain_per_pair": {"ms": round(plain_ms, 2), "GB/s": round(total / (plain_ms * 1e-3) / 1e9, 3),
+                               "launches": n},
+            "batched_over_plain": round(plain_ms / ms, 1),
+            "kernel_ms": round(kms / max(timed, 1), 4), "gpu_launches_per_step": launches / args.steps}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_long(args, world, rank, local):
+    """One 1 GiB text against (R)* with 48 positions: exact chunked mode
+    (rx_match_long) against the one-thread sequential run (rx_match_seq)."""
+    import torch
+    import paper_1108_3126_b300 as rx
+    import synth
+    dev = _dev_setup(local)
+    nodes, text, end = synth.cfg_long(total=args.long_bytes, with_end=True)
+    r = rx.Regex.from_nodes(nodes)
+    d = torch.from_numpy(text).to(dev)
+    n = len(text)
+    out = torch.zeros(1, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        rx.match_long(r, d, n, out, stream=stream)
+    rx.profile_read()
+    rx.profile_enable(True)
+    ms = _time(lambda: rx.match_long(r, d, n, out, stream=stream), args.steps, stream, dev)
+    rx.profile_enable(False)
+    launches, timed, kms = rx.profile_read()
+    chunked = int(out.item())
+    pre = min(n, args.seq_bytes)
+    seq_ms = _time(lambda: rx.match_seq(r, d, pre, out, stream=stream), 1, stream, dev)
+    rx.match_long(r, d, pre, out, stream=stream)
+    torch.cuda.synchronize(dev)
+    agree_prefix = int(out.item())
+    rx.match_seq(r, d, pre, out, stream=stream)
+    torch.cuda.synchronize(dev)
+    assert int(out.item()) == agree_prefix
+    peak, _ = peaks()
+    kernel_ms = kms / max(timed, 1)
+    line = {"metric": METRIC, "workload": "long", "value": round(n / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "long text: (R)* with 48 positions over a..z, one text of concatenated language "
+                                   "samples of R", "bytes": n, "memo_states": r.info()["memo_states"],
+                       "accepted": chunked, "last_whole_sample_end": end},
+            "sequential_gpu": {"bytes": pre, "ms": round(seq_ms, 2), "GB/s": round(pre / (seq_ms * 1e-3) / 1e9, 4)},
+            "chunked_over_sequential": round((n / ms) / (pre / seq_ms), 1),
+            "roofline": {"bound": "hbm", "kernel": "k_chunk_memo", "kernel_ms": round(kernel_ms, 4),
+                         "achieved": round(n / (kernel_ms * 1e-3) / 1e9, 1), "peak": peak,
+                         "frac": round(n / (kernel_ms * 1e-3) / 1e9 / peak, 4)},
+            "gpu_launches_per_step": launches / args.steps}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_serving(args, world, rank, local):
+    """Poisson arrivals of (regex, string) requests over a pool of 2000
+    compiled expressions (80% reuse; 20% compiled on arrival), payloads
+    resident on the device, swept over arrival rates; p50/p99 latency and
+    throughput, against the plain per-request form."""
+    import torch
+    import paper_1108_3126_b300 as rx
+    import synth
+    dev = _dev_setup(local)
+    pool_nodes = synth.serving_pool(pool=args.pool)
+    pool = [rx.Regex.from_nodes(nd) for nd in pool_nodes]
+    rng = np.random.default_rng(0x5EED0005)
+    # payloads: log-uniform 16 B - 16 MiB, half from a pool expression's language
+    npay = args.payloads
+    lens = np.exp(rng.uniform(np.log(16), np.log(16 << 20), npay)).astype(np.int64)
+    owners = rng.integers(0, len(pool), npay)
+    datas = []
+    for k in range(npay):
+        s = synth.gen_strings(pool_nodes[owners[k]], 1, int(lens[k]), int(lens[k]), synth.ALL_BYTES,
+                              synth.item_seed(0x5EED0005, 10 + k), p_lang=0.5)
+        datas.append(s.data)
+    dbufs = [torch.from_numpy(np.concatenate([x, np.zeros(16, np.uint8)])).to(dev) for x in datas]
+    torch.cuda.synchronize(dev)
+    fresh_nodes = [synth.gen_regex(int(np.exp(rng.uniform(np.log(8), np.log(1025)))), 14, synth.ALL_BYTES,
+                                   synth.item_seed(0x5EED0005, 100000 + k)) for k in range(256)]
+    points = []
+    for rate in args.rates:
+        nreq = int(min(args.max_requests, max(200, rate * args.seconds)))
+        gaps = rng.exponential(1.0 / rate, nreq)
+        arrive = np.cumsum(gaps)
+        pick = rng.integers(0, npay, nreq)
+        reuse = rng.random(nreq) < 0.8
+        srv = rx.Server(max_inflight=8192, tick_bytes=1 << 16, device_payload=True)
+        fresh = []
+        t0 = time.perf_counter()
+        for k in range(nreq):
+            while time.perf_counter() - t0 < arrive[k]:
+                pass
+            p = int(pick[k])
+            if reuse[k]:
+                h = pool[int(owners[p])]
+            else:
+                h = rx.Regex.from_nodes(fresh_nodes[k % len(fresh_nodes)])
+                fresh.append(h)
+            srv.submit(h, dbufs[p], len(datas[p]))
+        offered = nreq / max(time.perf_counter() - t0, 1e-9)
+        srv.drain(600000)
+        st = srv.stats()
+        srv.close()
+        points.append({"rate_target": rate, "rate_offered": round(offered, 1), "requests": nreq,
+                       "req_per_s": round(st["req_per_s"], 1), "GB/s": round(st["gb_per_s"], 2),
+                       "p50_ms": round(st["p50_ns"] / 1e6, 3), "p99_ms": round(st["p99_ns"] / 1e6, 3),
+                       "ticks": st["ticks"], "peak_inflight": st["peak_inflight"]})
+        del fresh
+    # plain per-request form: one synchronous call per request
+    out = torch.zeros(1, dtype=torch.uint8, device=dev)
+    off = torch.zeros(2, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lat = []
+    nb = 0
+    t0 = time.perf_counter()
+    for k in range(args.plain_requests):
+        p = int(rng.integers(0, npay))
+        ts = time.perf_counter()
+        rx.match_long(pool[int(owners[p])], dbufs[p], len(datas[p]), out, stream=stream) \
+            if len(datas[p]) > (1 << 20) else rx.match_seq(pool[int(owners[p])], dbufs[p], len(datas[p]), out,
+                                                           stream=stream)
+        torch.cuda.synchronize(dev)
+        lat.append(time.perf_counter() - ts)
+        nb += len(datas[p])
+    el = time.perf_counter() - t0
+    best = max(points, key=lambda q: q["req_per_s"])
+    line = {"metric": METRIC, "workload": "serving", "value": best["GB/s"], "unit": "GB/s", "n_gpus": world,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"serving: Poisson arrivals, pool of {len(pool)} regexes 8-1024 nodes, 80% reuse, "
+                                   f"payloads log-uniform 16 B-16 MiB ({npay} device-resident payloads)"},
+            "sweep": points,
+            "plain_per_request": {"requests": args.plain_requests, "req_per_s": round(args.plain_requests / el, 1),
+                                  "GB/s": round(nb / el / 1e9, 3),
+                                  "p50_ms": round(1e3 * float(np.median(lat)), 3),
+                                  "p99_ms": round(1e3 * float(np.quantile(lat, 0.99)), 3)},
+            "served_over_plain_req_per_s": round(best["req_per_s"] / (args.plain_requests / el), 1)}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="streaming", choices=["streaming"])
+    ap.add_argument("--workload", default="streaming", choices=["streaming", "batched", "long", "serving"])
+    ap.add_argument("--regexes", type=int, default=10000, help="batched: number of expressions")
+    ap.add_argument("--long-bytes", type=int, default=1 << 30, help="long: text length")
+    ap.add_argument("--seq-bytes", type=int, default=64 << 20, help="long: prefix timed sequentially")
+    ap.add_argument("--pool", type=int, default=2000, help="serving: compiled expressions")
+    ap.add_argument("--payloads", type=int, default=768, help="serving: device-resident payloads")
+    ap.add_argument("--rates", type=float, nargs="+", default=[1000, 10000, 50000, 200000])
+    ap.add_argument("--seconds", type=float, default=0.5, help="serving: arrival window per rate")
+    ap.add_argument("--max-requests", type=int, default=20000)
+    ap.add_argument("--plain-requests", type=int, default=300)
     ap.add_argument("--variant", default="auto", choices=["auto", "memo", "thread", "sparse", "warp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--strings", type=int, default=1 << 20, help="batch size (default: the full workload)")
@@ -349,7 +560,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        run_streaming(args, world, rank, local)
+        {"streaming": run_streaming, "batched": run_batched, "long": run_long,
+         "serving": run_serving}[args.workload](args, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -219,7 +219,15 @@ def match(rx: Regex, strings, offsets, out, n: int | None = None, stream=None, v
 
 
 def _handles(regexes) -> np.ndarray:
+    if isinstance(regexes, np.ndarray):
+        return np.ascontiguousarray(regexes, np.uint64)
     return np.array([r.handle for r in regexes], np.uint64)
+
+
+def handle_array(regexes) -> np.ndarray:
+    """Host array of raw handles (pass to match_batch / match_pairs to avoid
+    rebuilding it on every call)."""
+    return _handles(regexes)
 
 
 def match_batch(regexes, strings, offsets, out, stream=None):

@@ -177,6 +177,33 @@ int resolve_variant(const rx_regex* h, int v) {
 
 using namespace rx;
 
+// Section 8's machine, one string after another (prior-art comparison; every
+// micro-iteration is a launch followed by a flag read-back).
+static rx_status match_paper(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                             void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<int64_t> off(n + 1);
+    cudaError_t e = cudaMemcpyAsync(off.data(), offsets, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match (paper): offsets read-back");
+    size_t need = (2 * (size_t)(h->dev.nn + 1) + 4) * sizeof(int);
+    void* ws = nullptr;
+    rx_status s = get_workspace(st, need, &ws);
+    if (s != RX_OK) return s;
+    int* hflags = nullptr;
+    e = cudaMallocHost(&hflags, 4 * sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match (paper): pinned flags");
+    std::vector<uint8_t> res(n);
+    for (size_t i = 0; i < n && e == cudaSuccess; i++)
+        e = paper_match_one(h->dev, strings + off[i], off[i + 1] - off[i], static_cast<int*>(ws), hflags, &res[i], st);
+    cudaFreeHost(hflags);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match (paper) launch");
+    e = cudaMemcpyAsync(out, res.data(), n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match (paper): results");
+    return RX_OK;
+}
+
 #define RX_GUARD_BEGIN try {
 #define RX_GUARD_END                                  \
     }                                                 \
@@ -324,6 +351,7 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
         return RX_ERR_TOO_LARGE;
     }
     int variant = resolve_variant(h, opts ? opts->variant : RX_VARIANT_AUTO);
+    if (variant == RX_VARIANT_PAPER) return match_paper(h, n, strings, offsets, out, stream);
     if (variant <= 0 || variant > RX_VARIANT_WARP || !((h->host.variants >> variant) & 1u)) {
         set_error("rx_match: variant " + std::to_string(variant) + " cannot run this expression");
         return RX_ERR_UNSUPPORTED;

@@ -74,6 +74,10 @@ struct ProfScope {
 cudaError_t prof_read(int64_t* launches, int64_t* timed, double* ms);
 void prof_enable(bool on);
 
+// Section 8's machine on one string (paper_machine.cu); host-driven.
+cudaError_t paper_match_one(const DevTables& t, const uint8_t* str, int64_t len, int* scratch, int* hflags,
+                            uint8_t* out_host, cudaStream_t st);
+
 // Device properties cached per device.
 int sm_count();
 

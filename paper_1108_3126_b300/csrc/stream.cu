@@ -26,14 +26,17 @@ struct Blk32 {
     uint4 a, b;
 };
 
+// one 256-bit load of an aligned 32-byte block (a whole sector): one L1
+// wavefront per lane instead of two for a pair of 128-bit loads
 __device__ __forceinline__ Blk32 ld_blk(uint64_t addr, bool on) {
     Blk32 r;
     r.a = make_uint4(0, 0, 0, 0);
     r.b = r.a;
-    if (on) {
-        r.a = ld_stream(reinterpret_cast<const uint8_t*>(addr));
-        r.b = ld_stream(reinterpret_cast<const uint8_t*>(addr + 16));
-    }
+    if (on)
+        asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r.a.x), "=r"(r.a.y), "=r"(r.a.z), "=r"(r.a.w), "=r"(r.b.x), "=r"(r.b.y), "=r"(r.b.z),
+                       "=r"(r.b.w)
+                     : "l"(addr));
     return r;
 }
 

@@ -258,7 +258,8 @@ def star_text(nodes: np.ndarray, total: int, seed: int, piece: int = 4096, with_
     """A text of ``total`` bytes in the language of (e)* cut at ``total``:
     whole language samples of e (target lengths uniform in [1, piece])
     concatenated, so every prefix stays a prefix of a member of (e)*.  With
-    ``with_end`` also returns the offset where the last whole sample ends."""
+    ``with_end`` also returns an offset where a member of (e)* ends (the end
+    of the last whole ~1 MiB segment of samples)."""
     out = np.empty(max(total, 1), np.uint8)
     nd = np.ascontiguousarray(nodes)
     last = ctypes.c_int64(0)
@@ -337,7 +338,7 @@ def long_regex(seed: int = SEED_BASE + 4, positions: int = 48) -> np.ndarray:
 
 def cfg_long(seed: int = SEED_BASE + 4, total: int = 1 << 30, with_end: bool = False):
     """(R)* with 48 positions and one text of ``total`` bytes in its prefix
-    language.  Returns (nodes of (R)*, text[, end of the last whole sample])."""
+    language.  Returns (nodes of (R)*, text[, an offset where a member ends])."""
     r = long_regex(seed)
     text, end = star_text(r, total, item_seed(seed, 1), with_end=True)
     return (wrap_star(r), text, end) if with_end else (wrap_star(r), text)

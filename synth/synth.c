@@ -379,7 +379,7 @@ int sy_gen_strings(const sy_node* nd, int nnodes, int64_t n, int64_t lmin, int64
  * to end, so every prefix of the text is a prefix of a member of e*.  Only
  * the last sample may be cut.  Segment k uses item seed k, so the text is
  * reproducible whatever the thread count.  *last_end (optional) receives the
- * end offset of the last whole sample (a member of e* ends there).
+ * end offset of the last whole segment (a member of e* ends there).
  */
 int sy_gen_star_text(const sy_node* nd, int nnodes, int64_t total, int64_t piece, uint64_t seed, uint8_t* out,
                      int64_t* last_end) {

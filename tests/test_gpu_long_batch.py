@@ -119,9 +119,9 @@ def test_long_full_size_chunked_equals_sequential():
     n = len(text)
     got = long_match(r, d, n)
     assert got == seq_match(r, d, n)
-    # the text is a member of (R)* up to its last whole sample: the active set
-    # stays non-empty over (nearly) the whole gigabyte
-    assert end > n - 65536
+    # the text is a member of (R)* up to the end of its last whole 1 MiB
+    # segment: the active set stays non-empty over (nearly) the whole gigabyte
+    assert end > n - (2 << 20)
     assert long_match(r, d, end) == 1 and seq_match(r, d, end) == 1
     flip = d.clone()
     flip[-1] = ord("q") if int(text[-1]) != ord("q") else ord("r")
