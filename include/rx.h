@@ -188,6 +188,31 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
                       void* stream, const rx_match_opts* opts);
 
 /*
+ * rx_match_static -- rx_match for callers that cannot let the library
+ * allocate device memory.  (The paper has no counterpart: this concerns
+ * only how scratch space is obtained.)  rx_match grows a per-stream scratch
+ * buffer with cudaMalloc, after synchronising the stream and freeing the old
+ * buffer, whenever it meets a larger batch; a caller that must not block on
+ * the device, or whose device-memory budget is fixed in advance, cannot
+ * accept that.  rx_match_static runs the same planner and kernels with its
+ * scratch in one fixed 4 MiB array compiled into the library: every GPU that
+ * loads the library holds that array until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   Arguments, layout and result: as rx_match (async on `stream`).
+ *   Limit: at most 262,144 strings per call; larger n returns
+ *   RX_ERR_TOO_LARGE with nothing launched.
+ *   The first call on a device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ *   Every call shares the one array (the work counter is cleared by each
+ *   call; the rest keeps the last call's contents): calls that overlap on
+ *   the GPU -- on different streams, or from different threads -- race and
+ *   must be serialised by the caller.
+ * Errors: RX_ERR_INVALID_ARG, RX_ERR_TOO_LARGE, RX_ERR_CUDA.
+ */
+rx_status rx_match_static(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                          void* stream);
+
+/*
  * rx_match_batch -- n (expression, string) pairs in one persistent launch
  * (async).  handles is a HOST array of n handles (pair i uses handles[i]);
  * strings/offsets/out as in rx_match.  Pairs are bucketed by variant and

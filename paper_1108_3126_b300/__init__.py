@@ -75,6 +75,7 @@ SIGNATURES = {
     "rx_tree": ([P, P, SZ, ctypes.POINTER(SZ)], I32),
     "rx_match": ([P, SZ, P, P, P, P], I32),
     "rx_match_ex": ([P, SZ, P, P, P, P, ctypes.POINTER(_Opts)], I32),
+    "rx_match_static": ([P, SZ, P, P, P, P], I32),
     "rx_match_batch": ([P, SZ, P, P, P, P], I32),
     "rx_match_pairs": ([P, SZ, P, P, P, P], I32),
     "rx_match_long": ([P, P, I64, I64, P, P], I32),
@@ -216,6 +217,15 @@ def match(rx: Regex, strings, offsets, out, n: int | None = None, stream=None, v
     o = _Opts(variant, block, sort, 0)
     _check(lib().rx_match_ex(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream),
                              ctypes.byref(o)))
+
+
+def match_static(rx: Regex, strings, offsets, out, n: int | None = None, stream=None):
+    """As match(), with no device allocation by the library: scratch is a
+    fixed array inside librx.so (at most 262,144 strings per call; calls
+    that overlap on the GPU race on it)."""
+    if n is None:
+        n = len(offsets) - 1
+    _check(lib().rx_match_static(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream)))
 
 
 def _handles(regexes) -> np.ndarray:
