@@ -196,6 +196,10 @@ def run_streaming(args, world, rank, local):
     info = r.info()
     stream = torch.cuda.current_stream(dev)
     variant = {"auto": 0, "memo": 1, "thread": 2, "sparse": 3, "warp": 4}[args.variant]
+    # the autotuner measures every variant / block choice on this batch once
+    # (before the timed region) and rx_match's automatic choice uses it
+    rx.tune_reset()
+    tuned = rx.autotune(r, d_str, d_off, d_out, n=n, stream=stream) if variant == 0 else None
 
     def step():
         rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=variant)
@@ -236,21 +240,22 @@ def run_streaming(args, world, rank, local):
 
     # the other kernel variants on the same batch (informational)
     variants = {}
-    for v in (1, 2, 3, 4) if not args.quick else ():
+    for name, v, blk in ((("memo_pair", 1, 0), ("memo_single", 1, 257), ("thread", 2, 0), ("sparse", 3, 0),
+                          ("warp", 4, 0)) if not args.quick else ()):
         if not (info["variants"] >> v) & 1:
             continue
         reps = max(3, min(50, args.steps // 20))
         for _ in range(2):
-            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v)
+            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v, block=blk)
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(reps):
-            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v)
+            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v, block=blk)
         b.record(stream)
         torch.cuda.synchronize(dev)
         vms = a.elapsed_time(b) / reps
-        variants[rx.VARIANT_NAMES[v]] = {"GB/s": round(total_bytes / (vms * 1e-3) / 1e9, 1), "ms": round(vms, 4)}
+        variants[name] = {"GB/s": round(total_bytes / (vms * 1e-3) / 1e9, 1), "ms": round(vms, 4)}
 
     # end to end through the public API with host buffers: compile the
     # expression, copy strings + offsets from pinned host memory, match, read
@@ -294,8 +299,10 @@ def run_streaming(args, world, rank, local):
 
     if rank != 0:
         return
-    kname = {1: "k_stream<MemoS>", 2: "k_stream<Thread1S|Thread2S>", 3: "k_thread<SparseStep>",
-             4: "k_warp"}[variant if variant else (1 if info["variants"] & 2 else 2)]
+    chosen_v = tuned["variant"] if tuned else (variant or 1)
+    chosen_b = tuned["block"] if tuned else 0
+    kname = {1: "k_stream<MemoPair>" if (info.get("pair", True) and not (chosen_b & 1)) else "k_stream<MemoS>",
+             2: "k_stream<Thread1S|Thread2S>", 3: "k_thread<SparseStep>", 4: "k_warp"}[chosen_v]
     src_hash = kernel_source_hash()
     traffic = TRAFFIC.get((kname, src_hash))
     line = {
@@ -320,6 +327,7 @@ def run_streaming(args, world, rank, local):
         "clocks": clk,
         "cpu_baseline": cpu,
         "variants": variants,
+        "autotune": tuned,
         "compile_us": round(compile_us, 1),
         "accepted": accepted,
         "kernel_src": src_hash,

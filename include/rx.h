@@ -175,10 +175,15 @@ rx_status rx_match(rx_handle h, size_t n, const uint8_t* strings, const int64_t*
                    void* stream);
 
 typedef struct {
-    int32_t variant;    /* rx_variant; AUTO = library choice                 */
-    int32_t block;      /* threads per block, 0 = default                    */
-    int32_t sort;       /* -1 = auto, 0 = no length sort, 1 = sort by length */
-    int32_t reserved;
+    int32_t variant;    /* rx_variant; AUTO = tuned or library choice        */
+    int32_t block;      /* threads per block, 0 = tuned or default; for the
+                           cache of macro steps an odd value selects the
+                           one-byte-per-lookup kernel (block - 1 threads)    */
+    int32_t sort;       /* -1 = auto, 0 = input order, 1 = length order +
+                           per-variant kernel, 2 = length order + streaming
+                           kernel, 3 = streaming kernel in input order       */
+    int32_t len_hint;   /* mean string length if known (selects the tuned
+                           entry of that length bucket), 0 = unknown         */
 } rx_match_opts;
 
 /* rx_match_ex -- rx_match with an explicit variant / launch shape.
@@ -310,6 +315,43 @@ rx_status rx_serve_stats(rx_server* s, rx_serve_stats_t* out);
 /* rx_serve_destroy -- stop the server thread, free its device memory.
  * Outstanding requests are cancelled. */
 rx_status rx_serve_destroy(rx_server* s);
+
+/* ---------------------------------------------------------------- autotune */
+/*
+ * The library's choice of kernel variant and block size per (position-count
+ * bucket, mean-length bucket, cache present) is kept in a process-wide table
+ * filled by measurement.  rx_match / rx_match_ex with variant AUTO use the
+ * entry for the handle's position count and, when opts->len_hint is given,
+ * its length bucket (else the bucket-independent entry); without an entry
+ * they fall back to memo > thread > sparse > warp.
+ */
+typedef struct {
+    int32_t pos_bucket;  /* floor(log2(positions + 1))                       */
+    int32_t len_bucket;  /* floor(log2(mean length + 1)); -1 = any length    */
+    int32_t memo;        /* 1: entry for handles with a macro-step cache     */
+    int32_t variant;     /* chosen rx_variant                                */
+    int32_t block;       /* chosen threads per block                         */
+    float gb_per_s;      /* input GB/s of the choice on the tuning sample    */
+} rx_tune_entry;
+
+/*
+ * rx_autotune -- time every variant that can run h, at 128/256/512 threads
+ * per block (and, for the cache of macro steps, the one- and two-byte
+ * lookups), on the caller's sample batch (device strings/offsets as in
+ * rx_match; `out` device scratch of n bytes), and record the fastest in the
+ * table (for the sample's length bucket and as the bucket-independent
+ * entry).  Synchronises `stream`.  *chosen (optional) receives the entry.
+ * Errors: as rx_match.
+ */
+rx_status rx_autotune(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                      void* stream, rx_tune_entry* chosen);
+
+/* rx_autotune_table -- copy up to cap entries of the table; returns the
+ * number of entries in the table. */
+size_t rx_autotune_table(rx_tune_entry* out, size_t cap);
+
+/* rx_autotune_reset -- empty the table. */
+void rx_autotune_reset(void);
 
 /* -------------------------------------------------------------- profiling */
 /*

@@ -48,7 +48,12 @@ class _Info(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block", ctypes.c_int32), ("sort", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("len_hint", ctypes.c_int32)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("pos_bucket", ctypes.c_int32), ("len_bucket", ctypes.c_int32), ("memo", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("block", ctypes.c_int32), ("gb_per_s", ctypes.c_float)]
 
 
 class ServeCfg(ctypes.Structure):
@@ -87,6 +92,9 @@ SIGNATURES = {
     "rx_serve_drain": ([P, I64], I32),
     "rx_serve_stats": ([P, ctypes.POINTER(ServeStats)], I32),
     "rx_serve_destroy": ([P], I32),
+    "rx_autotune": ([P, SZ, P, P, P, P, ctypes.POINTER(TuneEntry)], I32),
+    "rx_autotune_table": ([P, SZ], SZ),
+    "rx_autotune_reset": ([], None),
     "rx_profile_enable": ([I32], I32),
     "rx_profile_read": ([ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double)], I32),
     "rx_last_error": ([], ctypes.c_char_p),
@@ -210,11 +218,11 @@ class Regex:
 
 
 def match(rx: Regex, strings, offsets, out, n: int | None = None, stream=None, variant: int = 0,
-          block: int = 0, sort: int = -1):
+          block: int = 0, sort: int = -1, len_hint: int = 0):
     """out[i] = 1 iff the expression matches strings[offsets[i]:offsets[i+1]] (async)."""
     if n is None:
         n = len(offsets) - 1
-    o = _Opts(variant, block, sort, 0)
+    o = _Opts(variant, block, sort, min(int(len_hint), 2**31 - 1))
     _check(lib().rx_match_ex(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream),
                              ctypes.byref(o)))
 
@@ -264,6 +272,32 @@ def match_seq(rx: Regex, text, length: int, out, stream=None):
 
 def trace(rx: Regex, text, length: int, frontiers, stream=None):
     _check(lib().rx_trace(rx.handle, _ptr(text), length, _ptr(frontiers), _stream(stream)))
+
+
+def _tune_dict(e: TuneEntry) -> dict:
+    return {f: getattr(e, f) for f, _ in TuneEntry._fields_}
+
+
+def autotune(rx: Regex, strings, offsets, out, n: int | None = None, stream=None) -> dict:
+    """Time every variant/block choice on this sample batch and record the
+    fastest for the expression's bucket (synchronises the stream)."""
+    if n is None:
+        n = len(offsets) - 1
+    e = TuneEntry()
+    _check(lib().rx_autotune(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream),
+                             ctypes.byref(e)))
+    return _tune_dict(e)
+
+
+def tune_table() -> list:
+    k = lib().rx_autotune_table(None, 0)
+    arr = (TuneEntry * max(k, 1))()
+    k = lib().rx_autotune_table(arr, k)
+    return [_tune_dict(arr[i]) for i in range(k)]
+
+
+def tune_reset():
+    lib().rx_autotune_reset()
 
 
 def profile_enable(on: bool = True):

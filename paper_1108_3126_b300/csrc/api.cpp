@@ -85,6 +85,7 @@ static rx_status upload(rx_regex* h) {
     const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
     size_t o_sps = take(spW * 4 + 16), o_spB = take((size_t)256 * spW * 4 + 16),
            o_spF = take((size_t)C.nbits * spW * 4 + 16);
+    size_t o_bg = take(std::max<size_t>(C.bg_T.size(), 1) * 2);
     size_t o_self = take(sizeof(DevTables));
     size_t total = off;
     std::vector<uint8_t> blob(total, 0);
@@ -102,6 +103,7 @@ static rx_status upload(rx_regex* h) {
     for (size_t i = 0; i < C.nodes.size(); i++)
         pn[i] = make_int4((int)C.nodes[i].kind | ((int)C.nodes[i].byte << 8), C.nodes[i].l, C.nodes[i].r, C.cont[i]);
     put(o_nd, pn.data(), pn.size() * sizeof(int4));
+    put(o_bg, C.bg_T.data(), C.bg_T.size() * 2);
     if (spW) {
         std::vector<uint32_t> ps(spW, 0u), pB((size_t)256 * spW, 0u), pF((size_t)C.nbits * spW, 0u);
         for (int k = 0; k < W; k++) ps[k] = C.start[k];
@@ -145,6 +147,8 @@ static rx_status upload(rx_regex* h) {
     t.memo_T = reinterpret_cast<const uint32_t*>(b + o_T);
     t.memo_acc = b + o_acc;
     t.memo_start = C.memo_start;
+    t.bg_T = C.bg_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bg);
+    t.bg_lo = C.bg_lo;
     t.variants = C.variants;
     t.nullable = C.nullable ? 1 : 0;
     t.nn = (int32_t)C.nodes.size();
@@ -163,6 +167,8 @@ static rx_status finish_compile(rx_regex* h, uint32_t flags) {
     }
     return upload(h);
 }
+
+bool tuned_choice(const rx_regex* h, int64_t len_hint, int* variant, int* block);
 
 int resolve_variant(const rx_regex* h, int v) {
     if (v != RX_VARIANT_AUTO) return v;
@@ -350,14 +356,23 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
         set_error("rx_match: more than 2^31 strings");
         return RX_ERR_TOO_LARGE;
     }
-    int variant = resolve_variant(h, opts ? opts->variant : RX_VARIANT_AUTO);
+    int req = opts ? opts->variant : RX_VARIANT_AUTO;
+    int block = opts ? opts->block : 0;
+    int variant = RX_VARIANT_AUTO;
+    if (req == RX_VARIANT_AUTO) {
+        int tv = 0, tb = 0;
+        if (tuned_choice(h, opts ? opts->len_hint : 0, &tv, &tb)) {
+            variant = tv;
+            if (block == 0) block = tb;
+        }
+    }
+    if (variant == RX_VARIANT_AUTO) variant = resolve_variant(h, req);
     if (variant == RX_VARIANT_PAPER) return match_paper(h, n, strings, offsets, out, stream);
     if (variant <= 0 || variant > RX_VARIANT_WARP || !((h->host.variants >> variant) & 1u)) {
         set_error("rx_match: variant " + std::to_string(variant) + " cannot run this expression");
         return RX_ERR_UNSUPPORTED;
     }
     int sort = rx::resolve_sort(variant, opts ? opts->sort : -1, n);
-    int block = opts ? opts->block : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* ws = nullptr;
     size_t need = match_workspace_bytes(n, sort);

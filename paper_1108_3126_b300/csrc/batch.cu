@@ -130,7 +130,7 @@ cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h
     if (e != cudaSuccess) return e;
     uint32_t* perm = nullptr;
     unsigned* starts = nullptr;
-    e = launch_plan(off, cls, kBatchClasses, n, plan_ws, &perm, &starts, st);
+    e = launch_plan(off, cls, kBatchClasses, n, plan_ws, &perm, &starts, st, nullptr);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, 0);

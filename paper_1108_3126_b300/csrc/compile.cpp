@@ -469,6 +469,34 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
             C.memo_start = (uint32_t)s0 * 256u;
         }
     }
+    // ---- 8b. two macro steps per lookup: when every label lies in one
+    // aligned window of 32 byte values, entry 32*j + i of a state's pair row
+    // is the state after reading byte lo+i then byte lo+j (two steps of the
+    // cache above); bytes outside the window use the single-byte row.
+    C.bg_T.clear();
+    C.bg_lo = -1;
+    if (C.memo_K > 0 && C.memo_K <= kPairMaxStates && m > 0) {
+        int lo = 256, hi = -1;
+        for (int c = 0; c < 256; c++)
+            if (!groups[c].empty()) {
+                lo = std::min(lo, c);
+                hi = std::max(hi, c);
+            }
+        int w0 = lo & ~31;
+        if (hi < w0 + 32) {
+            const int K = C.memo_K;
+            C.bg_lo = w0;
+            C.bg_T.assign((size_t)K * 1280, 0);
+            for (int k = 0; k < K; k++) {
+                uint16_t* row = &C.bg_T[(size_t)k * 1280];
+                for (int i = 0; i < 32; i++) {
+                    uint32_t mid = C.memo_T[(size_t)k * 256 + w0 + i] / 256u;
+                    for (int j = 0; j < 32; j++) row[j * 32 + i] = (uint16_t)(C.memo_T[(size_t)mid * 256 + w0 + j] / 256u);
+                }
+                for (int c = 0; c < 256; c++) row[1024 + c] = (uint16_t)(C.memo_T[(size_t)k * 256 + c] / 256u);
+            }
+        }
+    }
     // ---- 9. which kernel variants can run this expression
     C.variants = 0;
     if (C.memo_K > 0) C.variants |= 1u << RX_VARIANT_MEMO;

@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
 //   scan    : exclusive scan of the bucket totals
 //   scatter : every block places its range with shared-memory cursors
 __device__ __forceinline__ int len_bucket(int64_t len) {
-    if (len < 2048) return (int)len;
+    if (len < 2048) return (int)(len >> 4);
     int lg = 63 - __clzll(len);  // >= 11
-    int b = 2048 + 4 * (lg - 11) + (int)((len >> (lg - 2)) & 3);
+    int b = 128 + 4 * (lg - 11) + (int)((len >> (lg - 2)) & 3);
     return b < kLenBuckets ? b : kLenBuckets - 1;
 }
 
@@ -141,7 +141,18 @@ __global__ void k_plan_colscan(unsigned* __restrict__ hist_blk, int nblk, int nb
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbk) return;
     unsigned run = 0;
-    for (int g = 0; g < nblk; g++) {
+    int g = 0;
+    for (; g + 8 <= nblk; g += 8) {
+        unsigned h[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) h[k] = hist_blk[(size_t)(g + k) * nbk + b];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            hist_blk[(size_t)(g + k) * nbk + b] = run;
+            run += h[k];
+        }
+    }
+    for (; g < nblk; g++) {
         unsigned h = hist_blk[(size_t)g * nbk + b];
         hist_blk[(size_t)g * nbk + b] = run;
         run += h;
@@ -149,9 +160,10 @@ __global__ void k_plan_colscan(unsigned* __restrict__ hist_blk, int nblk, int nb
     totals[b] = run;
 }
 
-__global__ void k_plan_scan(unsigned* __restrict__ totals, int nbk) {
+__global__ void k_plan_scan(unsigned* __restrict__ totals, int nbk, unsigned* __restrict__ queue) {
     __shared__ unsigned part[1024];
     int t = threadIdx.x;
+    if (t == 0 && queue) *queue = 0;  // the work counter of the kernel that follows
     int per = (nbk + 1023) / 1024;
     unsigned sum = 0;
     for (int j = 0; j < per; j++) {
@@ -337,8 +349,8 @@ int sm_count() {
 }
 
 int plan_blocks(size_t n) {
-    long long g = ((long long)n + 4095) / 4096;
-    return (int)std::max<long long>(1, std::min<long long>(g, (long long)sm_count() * 2));
+    long long g = ((long long)n + 8191) / 8192;
+    return (int)std::max<long long>(1, std::min<long long>(g, (long long)sm_count()));
 }
 
 size_t plan_workspace_bytes(size_t n, int nclasses) {
@@ -347,7 +359,7 @@ size_t plan_workspace_bytes(size_t n, int nclasses) {
 }
 
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
-                        unsigned** starts, cudaStream_t st) {
+                        unsigned** starts, cudaStream_t st, unsigned* queue) {
     const int nbk = kLenBuckets * nclasses;
     const int G = plan_blocks(n);
     const long long per = ((long long)n + G - 1) / G;
@@ -363,7 +375,7 @@ cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, si
     if (e != cudaSuccess) return e;
     k_plan_hist<<<G, 512, shb, st>>>(off, cls, (long long)n, per, nbk, hist_blk);
     k_plan_colscan<<<(nbk + 255) / 256, 256, 0, st>>>(hist_blk, G, nbk, totals);
-    k_plan_scan<<<1, 1024, 0, st>>>(totals, nbk);
+    k_plan_scan<<<1, 1024, 0, st>>>(totals, nbk, queue);
     k_plan_scatter<<<G, 512, shb, st>>>(off, cls, (long long)n, per, nbk, hist_blk, totals, *perm);
     prof_count(4);
     return cudaGetLastError();
@@ -392,14 +404,19 @@ cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_
     uint8_t* w = static_cast<uint8_t*>(ws);
     unsigned* queue = reinterpret_cast<unsigned*>(w);
     uint32_t* perm = nullptr;
-    cudaError_t err = cudaMemsetAsync(w, 0, 256, st);
-    if (err != cudaSuccess) return err;
-    if (sort == 3) return launch_stream(t, variant, (long long)n, str, off, nullptr, out, queue, st);
+    cudaError_t err = cudaSuccess;
+    if (sort < 1) {  // with the planner, its scan kernel clears the counter
+        err = cudaMemsetAsync(w, 0, 256, st);
+        if (err != cudaSuccess) return err;
+    }
+    if (sort == 3) return launch_stream(t, variant, (long long)n, str, off, nullptr, out, queue, block, st);
+    // the remaining kernels take 32..256 threads per block
+    const int req_block = block;
     if (sort >= 1) {
         unsigned* starts = nullptr;
-        err = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st);
+        err = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st, queue);
         if (err != cudaSuccess) return err;
-        if (sort == 2) return launch_stream(t, variant, (long long)n, str, off, perm, out, queue, st);
+        if (sort == 2) return launch_stream(t, variant, (long long)n, str, off, perm, out, queue, req_block, st);
     }
     if (block <= 0) block = 256;
     block = (block + 31) / 32 * 32;

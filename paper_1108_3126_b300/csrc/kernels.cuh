@@ -6,8 +6,10 @@
 
 namespace rx {
 
-// Length buckets used to order strings longest first.
-constexpr int kLenBuckets = 2048 + 256;
+// Length buckets used to order strings longest first: 16-byte-wide buckets
+// below 2 KiB (the lanes of a round then end within one 32-byte block of each
+// other), quarter-octave buckets above.
+constexpr int kLenBuckets = 384;
 
 struct Workspace {
     void* base = nullptr;
@@ -30,14 +32,14 @@ cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_
 
 // Streaming kernel (memo and thread variants); perm may be NULL.
 cudaError_t launch_stream(const DevTables& t, int variant, long long n, const uint8_t* str, const int64_t* off,
-                          const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st);
+                          const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st);
 
 // Planner: order n strings by (class, length), longest first per class.
 // cls (device, n bytes) may be NULL (one class).  Writes *perm (n u32) and
 // *starts (first slot of every bucket) inside ws.
 size_t plan_workspace_bytes(size_t n, int nclasses);
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
-                        unsigned** starts, cudaStream_t st);
+                        unsigned** starts, cudaStream_t st, unsigned* queue = nullptr);
 
 // Batched pairs (batch.cu).  Variant classes, in task order.
 struct BatchTab {

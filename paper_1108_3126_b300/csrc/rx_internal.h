@@ -16,6 +16,8 @@ namespace rx {
 constexpr int kMemoMaxStates = 192;
 // Largest group of same-byte positions one thread-variant lookup covers.
 constexpr int kGroupMaxBits = 8;
+// Largest cache for which the two-byte rows are built (2.5 KB per state).
+constexpr int kPairMaxStates = 64;
 // Widest active set per thread for the sparse thread variant (32-bit words).
 constexpr int kSparseMaxWords = 8;
 // Widest active set per warp for the warp variant (lane-owned words).
@@ -45,6 +47,10 @@ struct DevTables {
     const uint32_t* memo_T;  // [K*256] next state * 256 (row start, in words)
     const uint8_t* memo_acc; // [K] 1 iff the state's set holds null
     uint32_t memo_start;     // start state * 256
+    // two-byte cache: for labels inside one 32-value window [bg_lo, bg_lo+32),
+    // per state a row of 1024 pair successors then 256 byte successors (u16 ids)
+    const uint16_t* bg_T;    // [K * 1280], 0 = unavailable
+    int32_t bg_lo;
     uint32_t variants;       // bit v: rx_variant v can run
     int32_t nullable;
     // the paper's own machine (Section 8): node array + cont
@@ -77,6 +83,9 @@ struct Compiled {
     std::vector<uint32_t> memo_T;  // K*256
     std::vector<uint8_t> memo_acc;
     uint32_t memo_start = 0;
+    // two-byte cache (see DevTables::bg_T)
+    std::vector<uint16_t> bg_T;
+    int bg_lo = -1;
     uint32_t variants = 0;
 };
 

@@ -326,6 +326,45 @@ struct MemoS {
     __device__ __forceinline__ void kill() { st = base; }
 };
 
+__device__ __forceinline__ uint32_t lds16(uint32_t a) {
+    uint16_t v;
+    asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+
+// two macro steps per lookup (see DevTables::bg_T): st = shared address of
+// the current state's row; the row holds 1024 pair successors (index
+// 32*second + first, bytes relative to the window) then 256 byte successors,
+// as u16 state ids; a row is 2560 bytes.
+struct MemoPair {
+    static constexpr bool kPairs = true;
+    static constexpr uint32_t ROW = 2560;
+    uint32_t st, base, acc, win;
+    static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * ROW) + align16(t.memo_K); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        copy_to_smem(sm, t.bg_T, (size_t)t.memo_K * ROW);
+        copy_to_smem(sm + align16((size_t)t.memo_K * ROW), t.memo_acc, t.memo_K);
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        base = smem_addr(sm);
+        acc = base + (uint32_t)align16((size_t)t.memo_K * ROW);
+        st = base + (t.memo_start >> 8) * ROW;
+        win = (uint32_t)t.bg_lo * 0x01010101u;
+    }
+    __device__ __forceinline__ void step(uint32_t c) { st = base + lds16(st + 2048u + c * 2u) * ROW; }
+    // x: first byte in bits 0-7, second in bits 8-15 (both inside the window)
+    __device__ __forceinline__ void step2(uint32_t x) {
+        uint32_t t = x & 0x1F1Fu;
+        uint32_t idx = ((t >> 3) & 0xFFE0u) | (t & ~0xFFE0u);
+        st = base + lds16(st + idx * 2u) * ROW;
+    }
+    // every byte of w inside the window
+    __device__ __forceinline__ uint32_t out_of_window(uint32_t w) const { return (w ^ win) & 0xE0E0E0E0u; }
+    __device__ __forceinline__ bool dead() const { return st == base; }
+    __device__ __forceinline__ bool accept() const { return lds8(acc + (st - base) / ROW) != 0; }
+    __device__ __forceinline__ void kill() { st = base; }
+};
+
 // register bitset (one word): desc[c] = {shift | mask << 8, shared address
 // of the byte's subset table}; entry x of that table is the new set.
 struct Thread1S {

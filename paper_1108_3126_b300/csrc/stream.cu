@@ -21,6 +21,7 @@ namespace {
 using namespace rx::dev;
 
 constexpr int STREAM_BLOCK = 256;
+constexpr int STREAM_MAX_BLOCK = 512;
 
 struct Blk32 {
     uint4 a, b;
@@ -57,8 +58,34 @@ __device__ __forceinline__ uint32_t valid_mask(uint64_t blk, uint64_t s, uint64_
 // Process one 32-byte block of every lane of the warp: the unrolled path
 // when the block is whole for every lane that still has bytes, the masked
 // path otherwise.  Lanes without bytes hold the empty set (harmless).
+template <class S, class = void>
+struct has_pairs {
+    static constexpr bool value = false;
+};
+template <class S>
+struct has_pairs<S, decltype(void(S::kPairs))> {
+    static constexpr bool value = S::kPairs;
+};
+
 template <class S>
 __device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
+    if constexpr (has_pairs<S>::value) {
+        // two bytes per lookup when the block is whole and inside the window
+        // for every lane that still has bytes
+        uint32_t out = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) out |= st.out_of_window(word_of(v, q));
+        bool pair_ok = mask == 0u || (mask == 0xffffffffu && out == 0u);
+        if (__all_sync(FULL, pair_ok)) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                uint32_t w = word_of(v, q);
+                st.step2(w);
+                st.step2(w >> 16);
+            }
+            return;
+        }
+    }
     if (__all_sync(FULL, mask == 0xffffffffu || mask == 0u)) {
 #pragma unroll
         for (int q = 0; q < 8; q++) {
@@ -81,7 +108,7 @@ __device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(STREAM_BLOCK) k_stream(const DevTables t, const uint8_t* __restrict__ str,
+__global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_stream(const DevTables t, const uint8_t* __restrict__ str,
                                                          const int64_t* __restrict__ off,
                                                          const uint32_t* __restrict__ perm, long long n,
                                                          uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
@@ -138,36 +165,45 @@ __global__ void __launch_bounds__(STREAM_BLOCK) k_stream(const DevTables t, cons
 
 template <class S>
 cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
-                            const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st) {
+                            const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
     size_t sm = S::smem_bytes(t);
     auto kern = k_stream<S>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, STREAM_BLOCK, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long rounds = (n + 31) / 32;
-    long long grid = std::min<long long>((rounds * 32 + STREAM_BLOCK - 1) / STREAM_BLOCK,
-                                         (long long)per_sm * sm_count());
+    long long grid = std::min<long long>((rounds * 32 + block - 1) / block, (long long)per_sm * sm_count());
     {
         ProfScope ps(st);
-        kern<<<(unsigned)std::max<long long>(grid, 1), STREAM_BLOCK, sm, st>>>(t, str, off, perm, n, out, queue);
+        kern<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, off, perm, n, out, queue);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
+bool stream_pairs(const DevTables& t) { return t.bg_T != nullptr; }
+
 bool stream_supported(const DevTables& t, int variant) {
     return variant == RX_VARIANT_MEMO || (variant == RX_VARIANT_THREAD && t.W <= 2);
 }
 
 cudaError_t launch_stream(const DevTables& t, int variant, long long n, const uint8_t* str, const int64_t* off,
-                          const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st) {
-    if (variant == RX_VARIANT_MEMO) return launch_stream_t<MemoS>(t, n, str, off, perm, out, queue, st);
-    if (t.W == 1) return launch_stream_t<Thread1S>(t, n, str, off, perm, out, queue, st);
-    return launch_stream_t<Thread2S>(t, n, str, off, perm, out, queue, st);
+                          const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
+    // an odd block request (e.g. 257) asks for the single-byte memo kernel
+    const int single = block & 1;
+    block &= ~1;
+    block = (block == 128 || block == 64 || block == 512) ? block : STREAM_BLOCK;
+    block |= single;
+    if (variant == RX_VARIANT_MEMO) {
+        if (t.bg_T && !(block & 1)) return launch_stream_t<MemoPair>(t, n, str, off, perm, out, queue, block, st);
+        return launch_stream_t<MemoS>(t, n, str, off, perm, out, queue, block & ~1, st);
+    }
+    if (t.W == 1) return launch_stream_t<Thread1S>(t, n, str, off, perm, out, queue, block & ~1, st);
+    return launch_stream_t<Thread2S>(t, n, str, off, perm, out, queue, block & ~1, st);
 }
 
 }  // namespace rx

@@ -48,9 +48,10 @@ def test_small_config_all_variants_vs_o1_o2():
     vs = variants_of(r)
     assert rx.VARIANT_MEMO in vs and rx.VARIANT_WARP in vs
     for v in [0] + vs:
-        for sort in (0, 1):
-            got = run(r, w.strings, v, sort)
-            assert (got == want2).all(), (v, sort, np.nonzero(got != want2)[0][:10])
+        for sort in (0, 1, 2, 3):
+            for block in ((0, 257, 128, 512) if v == rx.VARIANT_MEMO else (0,)):
+                got = run(r, w.strings, v, sort, block)
+                assert (got == want2).all(), (v, sort, block, np.nonzero(got != want2)[0][:10])
 
 
 @pytest.mark.parametrize("seed", range(4))
@@ -60,8 +61,9 @@ def test_streaming_config_reduced_vs_o2(seed):
     want = oracle.o2_batch(nodes, w.strings.data, w.strings.offsets)
     r = rx.Regex.from_nodes(nodes)
     for v in [0] + variants_of(r):
-        got = run(r, w.strings, v)
-        assert (got == want).all(), (v, np.nonzero(got != want)[0][:10])
+        for block in ((0, 257) if v == rx.VARIANT_MEMO else (0,)):
+            got = run(r, w.strings, v, block=block)
+            assert (got == want).all(), (v, block, np.nonzero(got != want)[0][:10])
     # a share of both verdicts, and language samples accepted
     assert 0.2 < want.mean() < 0.9
     assert want[w.strings.kind == 1].all()
@@ -201,6 +203,27 @@ def test_seq_and_pairs_forms():
         rx.match_seq(r, d[a:] if b > a else d, b - a, one)
         torch.cuda.synchronize()
         assert int(one.item()) == want[i]
+
+
+def test_autotune_records_and_is_used():
+    w = synth.cfg_streaming(seed=synth.SEED_BASE + 77, n=20000)
+    nodes = w.regexes[0]
+    r = rx.Regex.from_nodes(nodes)
+    d, o = dev(w.strings.data), dev(w.strings.offsets)
+    out = torch.zeros(w.strings.n, dtype=torch.uint8, device="cuda")
+    rx.tune_reset()
+    e = rx.autotune(r, d, o, out)
+    assert e["gb_per_s"] > 0 and (r.info()["variants"] >> e["variant"]) & 1
+    table = rx.tune_table()
+    assert len(table) == 2 and {t["len_bucket"] for t in table} == {-1, e["len_bucket"]}
+    want = oracle.o2_batch(nodes, w.strings.data, w.strings.offsets)
+    for hint in (0, 512, 10 ** 6):
+        out.fill_(7)
+        rx.match(r, d, o, out, len_hint=hint)
+        torch.cuda.synchronize()
+        assert (out.cpu().numpy() == want).all()
+    rx.tune_reset()
+    assert rx.tune_table() == []
 
 
 def test_errors_do_not_poison_the_context():
