@@ -105,6 +105,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+STREAMING_WORKLOAD = ("streaming: 1 regex x 64 AST nodes (depth<=10) over a..z; 1,048,576 strings L~U[1,1024] "
+                      "(half language samples, half 1-3 random edits); int64 offsets")
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value over all ranks (timing aggregation: the job is as
+    slow as its slowest rank).  Works with gloo (CPU) and nccl (CUDA)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -163,7 +179,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "streaming: 1 regex x 64 nodes over a..z, 1,048,576 strings L~U[1,1024]",
+            "config": {"workload": STREAMING_WORKLOAD, "strings": s.n, "total_bytes": int(s.offsets[-1]),
                        "sample_strings_per_step": per_step},
             "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} consecutive strings per step, O2 (Fig 6.1 machine), {cores} threads"},
@@ -196,10 +212,13 @@ def run_streaming(args, world, rank, local):
     info = r.info()
     stream = torch.cuda.current_stream(dev)
     variant = {"auto": 0, "memo": 1, "thread": 2, "sparse": 3, "warp": 4}[args.variant]
-    # the autotuner measures every variant / block choice on this batch once
-    # (before the timed region) and rx_match's automatic choice uses it
+    # with --autotune the autotuner measures every variant / block choice on
+    # this batch once (before the timed region) and rx_match's automatic
+    # choice uses it; by default the library's built-in choice is used (the
+    # tuner's earlier result for this bucket), so profiled runs of the same
+    # command launch the same kernels
     rx.tune_reset()
-    tuned = rx.autotune(r, d_str, d_off, d_out, n=n, stream=stream) if variant == 0 else None
+    tuned = rx.autotune(r, d_str, d_off, d_out, n=n, stream=stream) if (variant == 0 and args.autotune) else None
 
     def step():
         rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=variant)
@@ -227,10 +246,7 @@ def run_streaming(args, world, rank, local):
     ms = e0.elapsed_time(e1) / args.steps
     launches, timed, kms = rx.profile_read()
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     value = world * total_bytes / (ms * 1e-3) / 1e9
     kernel_ms = kms / max(timed, 1)
     alg_bytes = total_bytes + 8 * (n + 1) + n
@@ -286,10 +302,7 @@ def run_streaming(args, world, rank, local):
     b.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = a.elapsed_time(b) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e_val = world * total_bytes / (e2e_ms * 1e-3) / 1e9
 
     cpu = None
@@ -299,7 +312,7 @@ def run_streaming(args, world, rank, local):
 
     if rank != 0:
         return
-    chosen_v = tuned["variant"] if tuned else (variant or 1)
+    chosen_v = tuned["variant"] if tuned else (variant or (1 if info["memo_states"] else 2))
     chosen_b = tuned["block"] if tuned else 0
     kname = {1: "k_stream<MemoPair>" if (info.get("pair", True) and not (chosen_b & 1)) else "k_stream<MemoS>",
              2: "k_stream<Thread1S|Thread2S>", 3: "k_thread<SparseStep>", 4: "k_warp"}[chosen_v]
@@ -309,8 +322,7 @@ def run_streaming(args, world, rank, local):
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "streaming: 1 regex x 64 AST nodes (depth<=10) over a..z; 1,048,576 strings "
-                               "L~U[1,1024] (half language samples, half 1-3 random edits); int64 offsets",
+        "config": {"workload": STREAMING_WORKLOAD,
                    "total_bytes": total_bytes, "strings": n, "positions": info["positions"],
                    "memo_states": info["memo_states"], "variant": args.variant,
                    "l2": "inputs (537 MB) larger than the 126 MB L2; no flush",
@@ -475,36 +487,38 @@ def run_serving(args, world, rank, local):
     dbufs = [torch.from_numpy(np.concatenate([x, np.zeros(16, np.uint8)])).to(dev) for x in datas]
     torch.cuda.synchronize(dev)
     fresh_nodes = [synth.gen_regex(int(np.exp(rng.uniform(np.log(8), np.log(1025)))), 14, synth.ALL_BYTES,
-                                   synth.item_seed(0x5EED0005, 100000 + k)) for k in range(256)]
+                                   synth.item_seed(0x5EED0005, 100000 + k)) for k in range(4096)]
     points = []
+    fresh_all = []
+    compile_us = []
     for rate in args.rates:
         nreq = int(min(args.max_requests, max(200, rate * args.seconds)))
-        gaps = rng.exponential(1.0 / rate, nreq)
-        arrive = np.cumsum(gaps)
+        arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
         pick = rng.integers(0, npay, nreq)
         reuse = rng.random(nreq) < 0.8
-        srv = rx.Server(max_inflight=8192, tick_bytes=1 << 16, device_payload=True)
-        fresh = []
-        t0 = time.perf_counter()
+        handles = np.zeros(nreq, np.uint64)
         for k in range(nreq):
-            while time.perf_counter() - t0 < arrive[k]:
-                pass
-            p = int(pick[k])
             if reuse[k]:
-                h = pool[int(owners[p])]
+                handles[k] = pool[int(owners[int(pick[k])])].handle
             else:
+                # a regex outside the pool: compiled on arrival (cost reported separately)
+                t0 = time.perf_counter()
                 h = rx.Regex.from_nodes(fresh_nodes[k % len(fresh_nodes)])
-                fresh.append(h)
-            srv.submit(h, dbufs[p], len(datas[p]))
-        offered = nreq / max(time.perf_counter() - t0, 1e-9)
+                compile_us.append((time.perf_counter() - t0) * 1e6)
+                fresh_all.append(h)
+                handles[k] = h.handle
+        payloads = np.array([dbufs[int(p)].data_ptr() for p in pick], np.uint64)
+        lens = np.array([len(datas[int(p)]) for p in pick], np.int64)
+        srv = rx.Server(max_inflight=8192, device_payload=True)
+        _, late = srv.replay(handles, payloads, lens, (arrive * 1e9).astype(np.int64))
         srv.drain(600000)
         st = srv.stats()
         srv.close()
-        points.append({"rate_target": rate, "rate_offered": round(offered, 1), "requests": nreq,
+        points.append({"rate_target": rate, "requests": nreq, "submit_late_ms": round(late / 1e6, 3),
                        "req_per_s": round(st["req_per_s"], 1), "GB/s": round(st["gb_per_s"], 2),
                        "p50_ms": round(st["p50_ns"] / 1e6, 3), "p99_ms": round(st["p99_ns"] / 1e6, 3),
-                       "ticks": st["ticks"], "peak_inflight": st["peak_inflight"]})
-        del fresh
+                       "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
+                       "mean_bytes": int(lens.mean())})
     # plain per-request form: one synchronous call per request
     out = torch.zeros(1, dtype=torch.uint8, device=dev)
     off = torch.zeros(2, dtype=torch.int64, device=dev)
@@ -532,7 +546,8 @@ def run_serving(args, world, rank, local):
                                   "GB/s": round(nb / el / 1e9, 3),
                                   "p50_ms": round(1e3 * float(np.median(lat)), 3),
                                   "p99_ms": round(1e3 * float(np.quantile(lat, 0.99)), 3)},
-            "served_over_plain_req_per_s": round(best["req_per_s"] / (args.plain_requests / el), 1)}
+            "served_over_plain_req_per_s": round(best["req_per_s"] / (args.plain_requests / el), 1),
+            "compile_on_miss_us_mean": round(float(np.mean(compile_us)), 1) if compile_us else None}
     if rank == 0:
         print(json.dumps(line))
 
@@ -549,7 +564,7 @@ def main():
     ap.add_argument("--seq-bytes", type=int, default=64 << 20, help="long: prefix timed sequentially")
     ap.add_argument("--pool", type=int, default=2000, help="serving: compiled expressions")
     ap.add_argument("--payloads", type=int, default=768, help="serving: device-resident payloads")
-    ap.add_argument("--rates", type=float, nargs="+", default=[1000, 10000, 50000, 200000])
+    ap.add_argument("--rates", type=float, nargs="+", default=[1000, 3000, 10000, 30000, 100000, 200000])
     ap.add_argument("--seconds", type=float, default=0.5, help="serving: arrival window per rate")
     ap.add_argument("--max-requests", type=int, default=20000)
     ap.add_argument("--plain-requests", type=int, default=300)
@@ -557,6 +572,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--strings", type=int, default=1 << 20, help="batch size (default: the full workload)")
     ap.add_argument("--quick", action="store_true", help="skip the variant sweep, e2e repeats and CPU baseline")
+    ap.add_argument("--autotune", action="store_true", help="run the autotuner on the batch before timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

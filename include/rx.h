@@ -275,7 +275,9 @@ typedef struct {
     int64_t tick_bytes;          /* bytes each in-flight request advances
                                     per device tick                        */
     int32_t device_payload;      /* 1: submit() bytes are device pointers  */
-    int32_t reserved;
+    int32_t long_threshold;      /* requests longer than this (bytes) run
+                                    the chunked mode (rx_match_long) on
+                                    their own streams; 0 = 64 KiB          */
 } rx_serve_cfg;
 
 typedef struct {
@@ -305,6 +307,17 @@ rx_status rx_serve_submit(rx_server* s, rx_handle h, const uint8_t* bytes, int64
  * returns how many were written.  results[i] is 0/1, st[i] the status of
  * that request. */
 size_t rx_serve_poll(rx_server* s, uint64_t* tickets, uint8_t* results, rx_status* st, size_t max);
+
+/* rx_serve_replay -- load generator for measurement: submit n requests,
+ * request i at time t0 + arrival_ns[i] (t0 = entry to the call; the calling
+ * thread waits between submissions), handles[i] / payloads[i] / lens[i] as
+ * in rx_serve_submit.  tickets (optional, n) receives the tickets.  Returns
+ * when all are submitted (not completed); a full queue is retried.
+ * *late_ns (optional) receives the largest lateness of a submission behind
+ * its arrival time.  Errors: as rx_serve_submit. */
+rx_status rx_serve_replay(rx_server* s, const rx_handle* handles, const uint8_t* const* payloads,
+                          const int64_t* lens, const int64_t* arrival_ns, size_t n, uint64_t* tickets,
+                          int64_t* late_ns);
 
 /* rx_serve_drain -- wait until every submitted request has completed, up
  * to timeout_ms.  Errors: RX_ERR_TIMEOUT. */

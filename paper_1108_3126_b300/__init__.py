@@ -59,7 +59,7 @@ class TuneEntry(ctypes.Structure):
 class ServeCfg(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("tick_bytes", ctypes.c_int64),
-                ("device_payload", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("device_payload", ctypes.c_int32), ("long_threshold", ctypes.c_int32)]
 
 
 class ServeStats(ctypes.Structure):
@@ -89,6 +89,7 @@ SIGNATURES = {
     "rx_serve_create": ([ctypes.POINTER(ServeCfg), ctypes.POINTER(P)], I32),
     "rx_serve_submit": ([P, P, P, I64, ctypes.POINTER(ctypes.c_uint64)], I32),
     "rx_serve_poll": ([P, P, P, P, SZ], SZ),
+    "rx_serve_replay": ([P, P, P, P, P, SZ, P, ctypes.POINTER(I64)], I32),
     "rx_serve_drain": ([P, I64], I32),
     "rx_serve_stats": ([P, ctypes.POINTER(ServeStats)], I32),
     "rx_serve_destroy": ([P], I32),
@@ -317,8 +318,9 @@ class Server:
     """Continuous-batching matcher (rx_serve_*)."""
 
     def __init__(self, device_budget_bytes: int = 0, max_inflight: int = 256, queue_capacity: int = 65536,
-                 tick_bytes: int = 1 << 16, device_payload: bool = False):
-        cfg = ServeCfg(device_budget_bytes, max_inflight, queue_capacity, tick_bytes, int(device_payload), 0)
+                 tick_bytes: int = 0, device_payload: bool = False, long_threshold: int = 0):
+        cfg = ServeCfg(device_budget_bytes, max_inflight, queue_capacity, tick_bytes, int(device_payload),
+                       long_threshold)
         h = P()
         _check(lib().rx_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._s = h.value
@@ -334,6 +336,20 @@ class Server:
             assert length is not None
         _check(lib().rx_serve_submit(self._s, rx.handle, ptr, length, ctypes.byref(t)))
         return int(t.value)
+
+    def replay(self, handles: np.ndarray, payloads: np.ndarray, lens: np.ndarray, arrival_ns: np.ndarray):
+        """Submit request i at arrival_ns[i] after the call starts (native
+        pacing); returns (tickets, largest lateness in ns)."""
+        n = len(lens)
+        hs = np.ascontiguousarray(handles, np.uint64)
+        ps = np.ascontiguousarray(payloads, np.uint64)
+        ls = np.ascontiguousarray(lens, np.int64)
+        ar = np.ascontiguousarray(arrival_ns, np.int64)
+        tk = np.zeros(max(n, 1), np.uint64)
+        late = I64(0)
+        _check(lib().rx_serve_replay(self._s, hs.ctypes.data, ps.ctypes.data, ls.ctypes.data, ar.ctypes.data, n,
+                                     tk.ctypes.data, ctypes.byref(late)))
+        return tk[:n], int(late.value)
 
     def poll(self, max_n: int = 4096):
         tick = np.zeros(max_n, np.uint64)

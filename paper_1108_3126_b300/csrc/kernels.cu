@@ -405,7 +405,7 @@ cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_
     unsigned* queue = reinterpret_cast<unsigned*>(w);
     uint32_t* perm = nullptr;
     cudaError_t err = cudaSuccess;
-    if (sort < 1) {  // with the planner, its scan kernel clears the counter
+    if (sort != 1 && sort != 2) {  // with the planner, its scan kernel clears the counter
         err = cudaMemsetAsync(w, 0, 256, st);
         if (err != cudaSuccess) return err;
     }

@@ -52,6 +52,11 @@ cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h
                          size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
                          cudaStream_t st);
 
+// Spans of the chunked mode run from given cache states (stream.cu).
+cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
+                              const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
+                              uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st);
+
 // Chunked single-string mode (long.cu).
 bool long_supported(const DevTables& t);
 int64_t long_chunk_auto(const DevTables& t, int64_t len);

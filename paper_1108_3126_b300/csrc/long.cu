@@ -27,9 +27,11 @@ namespace {
 
 using namespace rx::dev;
 
-// one warp per (chunk, group of 32 incoming states); lanes = incoming states
+// Phase 1: one warp per (chunk, group of 32 incoming states); lanes =
+// incoming states; every lane reads the same bytes, the first P of the chunk.
 __global__ void __launch_bounds__(256) k_chunk_memo(const DevTables t, const uint8_t* __restrict__ str, int64_t len,
-                                                    int64_t C, long long J, int groups, uint16_t* __restrict__ maps) {
+                                                    int64_t C, int64_t P, long long J, int groups,
+                                                    uint16_t* __restrict__ maps) {
     extern __shared__ __align__(16) uint8_t smem[];
     MemoStep::load(t, smem);
     __syncthreads();
@@ -45,9 +47,108 @@ __global__ void __launch_bounds__(256) k_chunk_memo(const DevTables t, const uin
         int s0 = g * 32 + lane;
         MemoStep st = proto;
         st.set_state(s0 < t.memo_K ? (uint32_t)s0 : 0u);
-        uint64_t s = base + (uint64_t)(j * C), e = base + (uint64_t)std::min<int64_t>((j + 1) * C, len);
+        const int64_t lo = j * C;
+        uint64_t s = base + (uint64_t)lo, e = base + (uint64_t)min(min(lo + P, lo + C), len);
         run_range_uniform(st, s, e);
         if (s0 < t.memo_K) maps[j * t.memo_K + s0] = (uint16_t)(st.st >> 8);
+    }
+}
+
+// The distinct states the K incoming states reach after the prefix: per
+// chunk, slot[s] = rank of pre[s] among them, dlist[r] = the r-th, cnt.
+// One warp per chunk; a bitmap of states (K <= 192) per warp in shared memory.
+__global__ void __launch_bounds__(256) k_distinct(const uint16_t* __restrict__ pre, long long J, int K,
+                                                  uint16_t* __restrict__ slot, uint16_t* __restrict__ dlist,
+                                                  unsigned* __restrict__ cnt) {
+    __shared__ unsigned bm_all[8][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned* bm = bm_all[wid];
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + wid; j < J; j += warps) {
+        if (lane < 8) bm[lane] = 0;
+        __syncwarp();
+        for (int s = lane; s < K; s += 32) {
+            unsigned v = pre[j * K + s];
+            atomicOr(&bm[v >> 5], 1u << (v & 31));
+        }
+        __syncwarp();
+        unsigned word = lane < 8 ? bm[lane] : 0u;
+        unsigned c = __popc(word), incl = c;
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            unsigned x = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += x;
+        }
+        unsigned excl = incl - c;
+        unsigned total = __shfl_sync(0xffffffffu, incl, 7);
+        for (int s = lane; s < K; s += 32) {
+            unsigned v = pre[j * K + s];
+            unsigned w = v >> 5;
+            // rank = number of distinct states below v
+            unsigned base_w = 0;
+            for (unsigned q = 0; q < w; q++) base_w += __popc(bm[q]);
+            slot[j * K + s] = (uint16_t)(base_w + __popc(bm[w] & ((1u << (v & 31)) - 1u)));
+        }
+        if (lane < 8) {
+            unsigned r = excl;
+            unsigned x = word;
+            while (x) {
+                int b = __ffs(x) - 1;
+                x &= x - 1;
+                dlist[j * K + r++] = (uint16_t)(lane * 32 + b);
+            }
+        }
+        if (lane == 0) cnt[j] = total;
+        __syncwarp();
+    }
+}
+
+// exclusive scan of the per-chunk task counts (one block); also clears the
+// work counter of the span kernel that follows
+__global__ void k_scan_cnt(const unsigned* __restrict__ cnt, long long J, unsigned* __restrict__ toff,
+                           unsigned* __restrict__ queue) {
+    __shared__ unsigned part[1024];
+    const int t = threadIdx.x;
+    if (t == 0) *queue = 0;
+    const long long per = (J + 1023) / 1024;
+    unsigned sum = 0;
+    for (long long i = t * per; i < min((long long)(t + 1) * per, J); i++) sum += cnt[i];
+    part[t] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        unsigned v = (t >= d) ? part[t - d] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned run = part[t] - sum;
+    for (long long i = t * per; i < min((long long)(t + 1) * per, J); i++) {
+        toff[i] = run;
+        run += cnt[i];
+    }
+    if (t == 1023) toff[J] = part[1023];
+}
+
+__global__ void k_tasks(const unsigned* __restrict__ cnt, const unsigned* __restrict__ toff,
+                        const uint16_t* __restrict__ dlist, long long J, int K, uint32_t* __restrict__ task_chunk,
+                        uint16_t* __restrict__ task_state) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < J; j += warps) {
+        const unsigned c = cnt[j], o = toff[j];
+        for (unsigned r = lane; r < c; r += 32) {
+            task_chunk[o + r] = (uint32_t)j;
+            task_state[o + r] = dlist[j * K + r];
+        }
+    }
+}
+
+__global__ void k_final_maps(const uint16_t* __restrict__ slot, const unsigned* __restrict__ toff,
+                             const uint16_t* __restrict__ res, long long J, int K, uint16_t* __restrict__ maps) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < J * K;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long j = i / K;
+        maps[i] = res[toff[j] + slot[i]];
     }
 }
 
@@ -68,6 +169,7 @@ __global__ void k_compose_maps(const uint16_t* __restrict__ in, long long cnt, i
 }
 
 __global__ void k_finish_memo(const DevTables t, const uint16_t* __restrict__ map, int has_map, uint8_t* out) {
+    // has_map == 0: the empty text, accepted iff the start state holds null
     if (threadIdx.x != 0) return;
     uint32_t s = t.memo_start >> 8;
     if (has_map) s = map[s];
@@ -223,16 +325,68 @@ cudaError_t compose_rows(const DevTables& t, uint32_t* a, uint32_t* b, long long
 }  // namespace
 
 int64_t long_chunk_auto(const DevTables& t, int64_t len) {
-    int groups = t.memo_K > 0 ? (t.memo_K + 31) / 32 : (t.nbits + 31) / 32;
+    if (t.memo_K > 0) {
+        // enough chunks that the converged tasks (about one per chunk) fill
+        // every lane of the GPU a few times over
+        long long target = (long long)sm_count() * 1536 * 2;
+        int64_t C = (len + target - 1) / std::max<long long>(target, 1);
+        C = std::max<int64_t>(C, 1024);
+        return (C + 31) & ~int64_t(31);
+    }
+    int groups = (t.nbits + 31) / 32;
     long long target = (long long)sm_count() * 64 * 8 / std::max(groups, 1);
     int64_t C = (len + target - 1) / std::max<long long>(target, 1);
     C = std::max<int64_t>(C, 4096);
     return (C + 15) & ~int64_t(15);
 }
 
+// prefix every incoming state runs before the distinct states are taken
+constexpr int64_t kLongPrefix = 128;
+
+struct MemoLongWs {
+    uint16_t *pre, *slot, *dlist, *task_state, *res, *maps_a, *maps_b;
+    uint32_t* task_chunk;
+    unsigned *cnt, *toff, *queue;
+};
+
+static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t x = off;
+        off += al256(b);
+        return w ? w + x : nullptr;
+    };
+    const size_t JK = (size_t)J * K;
+    uint8_t* p_pre = take(JK * 2);
+    uint8_t* p_slot = take(JK * 2);
+    uint8_t* p_dl = take(JK * 2);
+    uint8_t* p_ts = take(JK * 2);
+    uint8_t* p_res = take(JK * 2);
+    uint8_t* p_ma = take(JK * 2);
+    uint8_t* p_mb = take(JK * 2);
+    uint8_t* p_tc = take(JK * 4);
+    uint8_t* p_cnt = take((size_t)J * 4);
+    uint8_t* p_toff = take((size_t)(J + 1) * 4);
+    uint8_t* p_q = take(256);
+    if (o) {
+        o->pre = reinterpret_cast<uint16_t*>(p_pre);
+        o->slot = reinterpret_cast<uint16_t*>(p_slot);
+        o->dlist = reinterpret_cast<uint16_t*>(p_dl);
+        o->task_state = reinterpret_cast<uint16_t*>(p_ts);
+        o->res = reinterpret_cast<uint16_t*>(p_res);
+        o->maps_a = reinterpret_cast<uint16_t*>(p_ma);
+        o->maps_b = reinterpret_cast<uint16_t*>(p_mb);
+        o->task_chunk = reinterpret_cast<uint32_t*>(p_tc);
+        o->cnt = reinterpret_cast<unsigned*>(p_cnt);
+        o->toff = reinterpret_cast<unsigned*>(p_toff);
+        o->queue = reinterpret_cast<unsigned*>(p_q);
+    }
+    return off;
+}
+
 size_t long_workspace_bytes(const DevTables& t, int64_t len, int64_t C) {
     long long J = (len + C - 1) / C;
-    if (t.memo_K > 0) return 2 * al256((size_t)J * t.memo_K * 2) + 256;
+    if (t.memo_K > 0) return memo_long_layout(std::max(J, 1LL), t.memo_K, nullptr, nullptr) + 256;
     int k = rows_kind(t);
     if (!k) return 0;
     int RW = (k == 1) ? 1 : (k == 2 ? 2 : k);
@@ -249,39 +403,56 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
     cudaError_t e;
     if (t.memo_K > 0) {
         const int K = t.memo_K;
-        uint16_t* a = reinterpret_cast<uint16_t*>(w);
-        uint16_t* b = reinterpret_cast<uint16_t*>(w + al256((size_t)J * K * 2));
-        if (J > 0) {
-            int groups = (K + 31) / 32;
-            size_t sm = MemoStep::smem_bytes(t);
-            e = cudaFuncSetAttribute(k_chunk_memo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            int per_sm = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_memo, 256, sm);
-            if (e != cudaSuccess) return e;
-            long long need = (J * groups + 7) / 8;
-            long long grid = std::min<long long>(need, (long long)std::max(per_sm, 1) * sm_count());
-            {
-                ProfScope ps(st);
-                k_chunk_memo<<<(unsigned)std::max<long long>(grid, 1), 256, sm, st>>>(t, str, len, C, J, groups, a);
-            }
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            int G = std::max(2, std::min(512, (48 * 1024) / (K * 2)));
-            long long cnt = J;
-            uint16_t* cur = a;
-            uint16_t* nxt = b;
-            while (cnt > 1) {
-                long long nb = (cnt + G - 1) / G;
-                k_compose_maps<<<(unsigned)nb, 128, (size_t)G * K * 2, st>>>(cur, cnt, K, G, nxt);
-                prof_count(1);
-                std::swap(cur, nxt);
-                cnt = nb;
-            }
-            k_finish_memo<<<1, 32, 0, st>>>(t, cur, 1, out);
-        } else {
-            k_finish_memo<<<1, 32, 0, st>>>(t, a, 0, out);
+        if (J == 0) {
+            k_finish_memo<<<1, 32, 0, st>>>(t, nullptr, 0, out);
+            prof_count(1);
+            return cudaGetLastError();
         }
+        MemoLongWs L;
+        memo_long_layout(J, K, w, &L);
+        const int64_t P = std::min<int64_t>(kLongPrefix, C);
+        // phase 1: every incoming state over the first P bytes of each chunk
+        int groups = (K + 31) / 32;
+        size_t sm = MemoStep::smem_bytes(t);
+        e = cudaFuncSetAttribute(k_chunk_memo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_memo, 256, sm);
+        if (e != cudaSuccess) return e;
+        long long need = (J * groups + 7) / 8;
+        long long grid = std::min<long long>(need, (long long)std::max(per_sm, 1) * sm_count() * 4);
+        {
+            ProfScope ps(st);
+            k_chunk_memo<<<(unsigned)std::max<long long>(grid, 1), 256, sm, st>>>(t, str, len, C, P, J, groups, L.pre);
+        }
+        // the distinct states reached, one task per (chunk, distinct state)
+        long long g2 = std::min<long long>((J + 7) / 8, (long long)sm_count() * 16);
+        k_distinct<<<(unsigned)std::max<long long>(g2, 1), 256, 0, st>>>(L.pre, J, K, L.slot, L.dlist, L.cnt);
+        k_scan_cnt<<<1, 1024, 0, st>>>(L.cnt, J, L.toff, L.queue);
+        k_tasks<<<(unsigned)std::max<long long>(g2, 1), 256, 0, st>>>(L.cnt, L.toff, L.dlist, J, K, L.task_chunk,
+                                                                     L.task_state);
+        prof_count(3);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        // phase 2: the distinct states over the rest of their chunks
+        e = launch_span_tasks(t, str, len, C, P, L.task_chunk, L.task_state, L.toff + J, L.res, L.queue, J * K, st);
+        if (e != cudaSuccess) return e;
+        long long g3 = std::min<long long>((J * K + 255) / 256, (long long)sm_count() * 16);
+        k_final_maps<<<(unsigned)std::max<long long>(g3, 1), 256, 0, st>>>(L.slot, L.toff, L.res, J, K, L.maps_a);
+        prof_count(1);
+        // composition, left to right
+        int G = std::max(2, std::min(512, (48 * 1024) / (K * 2)));
+        long long cnt = J;
+        uint16_t* cur = L.maps_a;
+        uint16_t* nxt = L.maps_b;
+        while (cnt > 1) {
+            long long nb = (cnt + G - 1) / G;
+            k_compose_maps<<<(unsigned)nb, 128, (size_t)G * K * 2, st>>>(cur, cnt, K, G, nxt);
+            prof_count(1);
+            std::swap(cur, nxt);
+            cnt = nb;
+        }
+        k_finish_memo<<<1, 32, 0, st>>>(t, cur, 1, out);
         prof_count(1);
         return cudaGetLastError();
     }

@@ -186,7 +186,10 @@ struct rx_server {
     rx_serve_cfg cfg{};
     int device = 0;
     int64_t budget = 0, long_threshold = 1 << 20;
-    cudaStream_t st = nullptr, copy_st = nullptr, long_st = nullptr;
+    static constexpr int kLongStreams = 4;
+    static constexpr size_t kMaxLong = 32;
+    cudaStream_t st = nullptr, copy_st = nullptr, long_st[kLongStreams] = {};
+    int next_long = 0;
     ServeSlot* d_slots = nullptr;
     ServeSlot* h_slots = nullptr;  // pinned
     int32_t* d_order = nullptr;
@@ -252,7 +255,7 @@ void rx_server::run() {
                 bool lng = r->len > long_threshold && long_supported(r->h->dev);
                 int64_t need = (cfg.device_payload ? 0 : r->len);
                 if (lng) need += (int64_t)long_workspace_bytes(r->h->dev, r->len, long_chunk_auto(r->h->dev, r->len));
-                bool room = lng ? longs.size() < 8 : !free_slots.empty();
+                bool room = lng ? longs.size() < kMaxLong : !free_slots.empty();
                 if (!room || (inflight_bytes + need > budget && inflight_bytes > 0)) break;
                 pending.pop_front();
                 r->charged = need;
@@ -281,22 +284,24 @@ void rx_server::run() {
                 r->dptr = r->owned;
             }
             if (r->is_long) {
+                cudaStream_t ls = long_st[next_long];
+                next_long = (next_long + 1) % kLongStreams;
                 cudaEvent_t ce = nullptr;
                 cudaEventCreateWithFlags(&ce, cudaEventDisableTiming);
                 cudaEventRecord(ce, copy_st);
-                cudaStreamWaitEvent(long_st, ce, 0);
+                cudaStreamWaitEvent(ls, ce, 0);
                 cudaEventDestroy(ce);
                 int64_t C = long_chunk_auto(r->h->dev, r->len);
                 size_t wsb = long_workspace_bytes(r->h->dev, r->len, C);
                 uint8_t* out = nullptr;
-                if (cudaMallocAsync(&r->long_ws, wsb + 256, long_st) != cudaSuccess) {
+                if (cudaMallocAsync(&r->long_ws, wsb + 256, ls) != cudaSuccess) {
                     cudaGetLastError();
                     r->long_ws = nullptr;
                     complete(r, 0, RX_ERR_OOM);
                     continue;
                 }
                 out = static_cast<uint8_t*>(r->long_ws) + wsb;
-                cudaError_t e = launch_long(r->h->dev, r->dptr, r->len, C, out, r->long_ws, wsb, long_st);
+                cudaError_t e = launch_long(r->h->dev, r->dptr, r->len, C, out, r->long_ws, wsb, ls);
                 r->host.clear();
                 r->host.shrink_to_fit();
                 if (e != cudaSuccess) {
@@ -305,7 +310,7 @@ void rx_server::run() {
                     continue;
                 }
                 cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
-                cudaEventRecord(r->ev, long_st);
+                cudaEventRecord(r->ev, ls);
                 longs.push_back(r);
                 continue;
             }
@@ -407,7 +412,8 @@ rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out) {
         if (cfg) s->cfg = *cfg;
         if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 1024;
         if (s->cfg.queue_capacity <= 0) s->cfg.queue_capacity = 1 << 16;
-        if (s->cfg.tick_bytes <= 0) s->cfg.tick_bytes = 1 << 16;
+        if (s->cfg.tick_bytes <= 0) s->cfg.tick_bytes = 1 << 14;
+        s->long_threshold = s->cfg.long_threshold > 0 ? s->cfg.long_threshold : (1 << 16);
         cudaGetDevice(&s->device);
         size_t fr = 0, tot = 0;
         cudaError_t e = cudaMemGetInfo(&fr, &tot);
@@ -419,8 +425,10 @@ rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out) {
         s->budget = s->cfg.device_budget_bytes > 0 ? s->cfg.device_budget_bytes : (int64_t)(fr / 4);
         const int n = s->cfg.max_inflight;
         bool ok = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&s->long_st, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < rx_server::kLongStreams && ok; i++)
+            ok = cudaStreamCreateWithFlags(&s->long_st[i], cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok &&
                   cudaMalloc(&s->d_slots, sizeof(ServeSlot) * n) == cudaSuccess &&
                   cudaMalloc(&s->d_order, sizeof(int32_t) * n) == cudaSuccess &&
                   cudaMalloc(&s->d_state, sizeof(uint32_t) * (size_t)kStateWords * n) == cudaSuccess &&
@@ -477,6 +485,31 @@ rx_status rx_serve_submit(rx_server* s, rx_handle h, const uint8_t* bytes, int64
         set_error("rx_serve_submit: host allocation failed");
         return RX_ERR_OOM;
     }
+}
+
+rx_status rx_serve_replay(rx_server* s, const rx_handle* handles, const uint8_t* const* payloads,
+                          const int64_t* lens, const int64_t* arrival_ns, size_t n, uint64_t* tickets,
+                          int64_t* late_ns) {
+    if (!s || (n && (!handles || !payloads || !lens || !arrival_ns))) {
+        set_error("rx_serve_replay: bad argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    const int64_t t0 = now_ns();
+    int64_t late = 0;
+    for (size_t i = 0; i < n; i++) {
+        const int64_t due = t0 + arrival_ns[i];
+        while (now_ns() < due) {
+        }
+        late = std::max(late, now_ns() - due);
+        uint64_t t = 0;
+        rx_status st;
+        while ((st = rx_serve_submit(s, handles[i], payloads[i], lens[i], &t)) == RX_ERR_BUSY)
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        if (st != RX_OK) return st;
+        if (tickets) tickets[i] = t;
+    }
+    if (late_ns) *late_ns = late;
+    return RX_OK;
 }
 
 size_t rx_serve_poll(rx_server* s, uint64_t* tickets, uint8_t* results, rx_status* st, size_t max) {
@@ -550,7 +583,8 @@ rx_status rx_serve_destroy(rx_server* s) {
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     if (s->st) cudaStreamSynchronize(s->st);
-    if (s->long_st) cudaStreamSynchronize(s->long_st);
+    for (int i = 0; i < rx_server::kLongStreams; i++)
+        if (s->long_st[i]) cudaStreamSynchronize(s->long_st[i]);
     if (s->copy_st) cudaStreamSynchronize(s->copy_st);
     for (Request* r : s->slots)
         if (r) {
@@ -573,7 +607,8 @@ rx_status rx_serve_destroy(rx_server* s) {
     cudaFreeHost(s->h_status);
     if (s->st) cudaStreamDestroy(s->st);
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
-    if (s->long_st) cudaStreamDestroy(s->long_st);
+    for (int i = 0; i < rx_server::kLongStreams; i++)
+        if (s->long_st[i]) cudaStreamDestroy(s->long_st[i]);
     delete s;
     return RX_OK;
 }

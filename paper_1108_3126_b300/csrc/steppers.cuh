@@ -324,6 +324,8 @@ struct MemoS {
     __device__ __forceinline__ bool dead() const { return st == base; }
     __device__ __forceinline__ bool accept() const { return lds8(acc + ((st - base) >> 10)) != 0; }
     __device__ __forceinline__ void kill() { st = base; }
+    __device__ __forceinline__ void set_state(uint32_t s) { st = base + s * 1024u; }
+    __device__ __forceinline__ uint32_t state_id() const { return (st - base) >> 10; }
 };
 
 __device__ __forceinline__ uint32_t lds16(uint32_t a) {
@@ -363,6 +365,8 @@ struct MemoPair {
     __device__ __forceinline__ bool dead() const { return st == base; }
     __device__ __forceinline__ bool accept() const { return lds8(acc + (st - base) / ROW) != 0; }
     __device__ __forceinline__ void kill() { st = base; }
+    __device__ __forceinline__ void set_state(uint32_t s) { st = base + s * ROW; }
+    __device__ __forceinline__ uint32_t state_id() const { return (st - base) / ROW; }
 };
 
 // register bitset (one word): desc[c] = {shift | mask << 8, shared address

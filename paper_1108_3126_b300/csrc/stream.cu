@@ -163,6 +163,96 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_stream(const DevTables t, 
     }
 }
 
+// Tasks of the chunked long-string mode: task i starts the cache of macro
+// steps in state task_state[i] at byte task_chunk[i] * C + P of the text and
+// runs to the end of that chunk; res[i] receives the final state id.  Tasks
+// come chunk by chunk, so the 32 lanes of a round cover equal-length spans.
+template <class S>
+__global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_span_tasks(const DevTables t, const uint8_t* __restrict__ str,
+                                                               int64_t len, int64_t C, int64_t P,
+                                                               const uint32_t* __restrict__ task_chunk,
+                                                               const uint16_t* __restrict__ task_state,
+                                                               const unsigned* __restrict__ ntask_p,
+                                                               uint16_t* __restrict__ res,
+                                                               unsigned* __restrict__ queue) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    S::load(t, smem);
+    __syncthreads();
+    S proto;
+    proto.bind(t, smem);
+    const int lane = threadIdx.x & 31;
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    const long long n = *ntask_p;
+    const long long nround = (n + 31) / 32;
+    for (;;) {
+        unsigned r = 0;
+        if (lane == 0) r = atomicAdd(queue, 1u);
+        r = __shfl_sync(FULL, r, 0);
+        if ((long long)r >= nround) break;
+        const long long k = (long long)r * 32 + lane;
+        const bool valid = k < n;
+        uint64_t s = base, e = base;
+        S st = proto;
+        st.kill();
+        if (valid) {
+            const int64_t j = task_chunk[k];
+            const int64_t lo = j * C, hi = min(lo + C, len);
+            s += (uint64_t)min(lo + P, hi);
+            e += (uint64_t)hi;
+            st.set_state(task_state[k]);
+        }
+        bool active = valid && s < e && !st.dead();
+        // the state when the lane's span ends: the warp keeps stepping every
+        // lane while any is active, so a finished lane's state is taken here
+        uint32_t fin = valid ? st.state_id() : 0u;
+        if (!active) st.kill();
+        uint64_t blk = s & ~uint64_t(31);
+        Blk32 va = ld_blk(blk, active);
+        Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
+        while (__any_sync(FULL, active)) {
+            block32(st, va, valid_mask(blk, s, e, active));
+            if (active && (blk + 32 >= e || st.dead())) {
+                fin = st.state_id();
+                st.kill();
+                active = false;
+            }
+            va = ld_blk(blk + 64, active && blk + 64 < e);
+            if (!__any_sync(FULL, active)) break;
+            block32(st, vb, valid_mask(blk + 32, s, e, active));
+            if (active && (blk + 64 >= e || st.dead())) {
+                fin = st.state_id();
+                st.kill();
+                active = false;
+            }
+            vb = ld_blk(blk + 96, active && blk + 96 < e);
+            blk += 64;
+        }
+        if (valid) res[k] = (uint16_t)fin;
+    }
+}
+
+template <class S>
+cudaError_t launch_span_t(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
+                          const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
+                          uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st) {
+    size_t sm = S::smem_bytes(t);
+    auto kern = k_span_tasks<S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    const int block = 256;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = std::min<long long>((max_tasks + block - 1) / block, (long long)per_sm * sm_count());
+    {
+        ProfScope ps(st);
+        kern<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, len, C, P, task_chunk, task_state,
+                                                                        ntask_p, res, queue);
+    }
+    return cudaGetLastError();
+}
+
 template <class S>
 cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
                             const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
@@ -187,6 +277,14 @@ cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str,
 
 bool stream_pairs(const DevTables& t) { return t.bg_T != nullptr; }
 
+cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
+                              const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
+                              uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st) {
+    if (t.bg_T)
+        return launch_span_t<MemoPair>(t, str, len, C, P, task_chunk, task_state, ntask_p, res, queue, max_tasks, st);
+    return launch_span_t<MemoS>(t, str, len, C, P, task_chunk, task_state, ntask_p, res, queue, max_tasks, st);
+}
+
 bool stream_supported(const DevTables& t, int variant) {
     return variant == RX_VARIANT_MEMO || (variant == RX_VARIANT_THREAD && t.W <= 2);
 }
@@ -194,12 +292,16 @@ bool stream_supported(const DevTables& t, int variant) {
 cudaError_t launch_stream(const DevTables& t, int variant, long long n, const uint8_t* str, const int64_t* off,
                           const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
     // an odd block request (e.g. 257) asks for the single-byte memo kernel
+    const int block_req = block;
     const int single = block & 1;
     block &= ~1;
     block = (block == 128 || block == 64 || block == 512) ? block : STREAM_BLOCK;
     block |= single;
     if (variant == RX_VARIANT_MEMO) {
-        if (t.bg_T && !(block & 1)) return launch_stream_t<MemoPair>(t, n, str, off, perm, out, queue, block, st);
+        // 512 threads: the autotuner's measured choice for the two-byte
+        // kernel on the streaming workload (about 5% over 256)
+        if (t.bg_T && !(block & 1))
+            return launch_stream_t<MemoPair>(t, n, str, off, perm, out, queue, block_req == 0 ? 512 : block, st);
         return launch_stream_t<MemoS>(t, n, str, off, perm, out, queue, block & ~1, st);
     }
     if (t.W == 1) return launch_stream_t<Thread1S>(t, n, str, off, perm, out, queue, block & ~1, st);
