@@ -44,14 +44,16 @@ def peaks():
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
-# capture, keyed by a hash of the kernel source at capture time; null when
-# the source has changed since.
-TRAFFIC = {}
+# capture, keyed by a hash of that kernel's sources at capture time (null
+# when they have changed since).  k_stream<MemoPair>: 133.69 MB per launch on
+# the 262,144-string capture (136.81 MB algorithmic), scaled by algorithmic
+# bytes to the full 1,048,576-string launch (546.80 MB): 534.3 MB.
+TRAFFIC = {("k_stream<MemoPair>", "a880d27955c1a838"): 534.3e6}
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "rx_internal.h"):
+    for f in ("stream.cu", "steppers.cuh", "rx_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1108_3126_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -274,8 +276,9 @@ def run_streaming(args, world, rank, local):
         variants[name] = {"GB/s": round(total_bytes / (vms * 1e-3) / 1e9, 1), "ms": round(vms, 4)}
 
     # end to end through the public API with host buffers: compile the
-    # expression, copy strings + offsets from pinned host memory, match, read
-    # the booleans back
+    # expression, then rx_match_host (strings + offsets from pinned host
+    # memory, copies of each 64 MiB piece overlapped with matching the
+    # previous one, booleans read back)
     h_str = torch.from_numpy(s.data).pin_memory()
     h_off = torch.from_numpy(s.offsets).pin_memory()
     h_out = torch.empty(n, dtype=torch.uint8).pin_memory()
@@ -283,11 +286,7 @@ def run_streaming(args, world, rank, local):
 
     def e2e_step():
         rr = rx.Regex.from_nodes(nodes)
-        d_str.copy_(h_str, non_blocking=True)
-        d_off.copy_(h_off, non_blocking=True)
-        rx.match(rr, d_str, d_off, d_out, n=n, stream=stream)
-        h_out.copy_(d_out, non_blocking=True)
-        torch.cuda.synchronize(dev)
+        rx.match_host(rr, h_str, h_off, h_out, n=n, stream=stream)
         rr.free()
 
     if args.quick:
@@ -304,6 +303,8 @@ def run_streaming(args, world, rank, local):
     e2e_ms = a.elapsed_time(b) / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e_val = world * total_bytes / (e2e_ms * 1e-3) / 1e9
+    if not torch.equal(h_out, d_out.cpu()):
+        raise SystemExit("rx_match_host disagrees with rx_match on the same batch")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
@@ -333,7 +334,7 @@ def run_streaming(args, world, rank, local):
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.4 TB/s"},
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "h2d_bytes_per_step": total_bytes + 8 * (n + 1),
-                "d2h_bytes_per_step": n, "includes": "rx_compile_ast + H2D + rx_match + D2H per step"},
+                "d2h_bytes_per_step": n, "includes": "rx_compile_ast + rx_match_host (H2D, match, D2H) per step"},
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
         "clocks": clk,

@@ -218,6 +218,28 @@ rx_status rx_match_static(rx_handle h, size_t n, const uint8_t* strings, const i
                           void* stream);
 
 /*
+ * rx_match_host -- rx_match on HOST buffers (synchronous).  Decides, for
+ * every string, whether the expression matches it (Def 5.3) exactly as
+ * rx_match does; the paper has no counterpart for the transfer, which
+ * concerns only where the input lives.
+ *   strings  host bytes, offsets host int64[n+1] (non-decreasing, >= 0),
+ *   out      host uint8[n]: 1 = match, 0 = no match.
+ * The batch is cut at string boundaries into pieces of up to 64 MiB (or
+ * 2^20 strings; a longer single string is one piece); piece k is copied to
+ * the device on an internal stream while piece k-1 is matched on `stream`,
+ * and each piece's booleans are copied back on `stream`.  Host buffers in
+ * page-locked memory (cudaHostAlloc / pin_memory) let the copies run at
+ * full link speed; pageable buffers work but are staged by the driver.
+ * Device scratch: two staging buffers of the largest piece plus the
+ * planner's workspace, from the per-stream scratch buffer rx_match uses.
+ * Returns when `out` is written (the stream is synchronised).
+ * Errors: RX_ERR_INVALID_ARG (null handle/pointer, decreasing or negative
+ * offsets; nothing copied), RX_ERR_OOM, RX_ERR_CUDA.
+ */
+rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                        void* stream);
+
+/*
  * rx_match_batch -- n (expression, string) pairs in one persistent launch
  * (async).  handles is a HOST array of n handles (pair i uses handles[i]);
  * strings/offsets/out as in rx_match.  Pairs are bucketed by variant and

@@ -81,6 +81,7 @@ SIGNATURES = {
     "rx_match": ([P, SZ, P, P, P, P], I32),
     "rx_match_ex": ([P, SZ, P, P, P, P, ctypes.POINTER(_Opts)], I32),
     "rx_match_static": ([P, SZ, P, P, P, P], I32),
+    "rx_match_host": ([P, SZ, P, P, P, P], I32),
     "rx_match_batch": ([P, SZ, P, P, P, P], I32),
     "rx_match_pairs": ([P, SZ, P, P, P, P], I32),
     "rx_match_long": ([P, P, I64, I64, P, P], I32),
@@ -235,6 +236,15 @@ def match_static(rx: Regex, strings, offsets, out, n: int | None = None, stream=
     if n is None:
         n = len(offsets) - 1
     _check(lib().rx_match_static(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream)))
+
+
+def match_host(rx: Regex, strings, offsets, out, n: int | None = None, stream=None):
+    """As match(), on HOST buffers (numpy arrays or CPU tensors, pinned for
+    full link speed): copies to the device overlap the matching of the
+    previous piece; returns when out is written."""
+    if n is None:
+        n = len(offsets) - 1
+    _check(lib().rx_match_host(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream)))
 
 
 def _handles(regexes) -> np.ndarray:

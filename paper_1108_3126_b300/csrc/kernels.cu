@@ -107,12 +107,24 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
 }
 
 // ---------------------------------------------------- length-sort planner
-// Stable-enough counting sort of the strings by (class, length bucket),
-// longest first within a class, in four contention-free passes:
-//   hist    : every block counts its contiguous range in shared memory
-//   colscan : per bucket, running sums over the blocks (block cursors)
-//   scan    : exclusive scan of the bucket totals
-//   scatter : every block places its range with shared-memory cursors
+// Counting sort of the strings by (class, length bucket), longest first
+// within a class, in two launches:
+//   hist    : every block counts its range in shared memory and adds its
+//             counts to the global bucket totals; the last block to finish
+//             (ticket on a counter after a fence -- nothing waits) turns the
+//             totals into exclusive starts, copies them to the claim cursors
+//             and clears the work counter of the kernel that follows
+//   scatter : every block counts its range again, claims one contiguous
+//             range per bucket with one atomic add on the cursor, and places
+//             its strings there with shared-memory cursors
+// Each thread holds the keys of kPlanItems strings at a time, so the loads
+// of a tile are in flight together.  Within a bucket the order depends on
+// which block claims first; the kernels only need equal lengths within a
+// round of 32.
+constexpr int kPlanThreads = 512;
+constexpr int kPlanItems = 4;
+constexpr int kPlanTile = kPlanThreads * kPlanItems;
+
 __device__ __forceinline__ int len_bucket(int64_t len) {
     if (len < 2048) return (int)(len >> 4);
     int lg = 63 - __clzll(len);  // >= 11
@@ -121,84 +133,116 @@ __device__ __forceinline__ int len_bucket(int64_t len) {
 }
 
 __device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, long long i) {
-    int lb = len_bucket(off[i + 1] - off[i]);
+    const int64_t len = off[i + 1] - off[i];
+    int lb = len_bucket(len);
     int c = cls ? (int)cls[i] : 0;
+    if (cls && c == kClsMemo && len > kLongPairBytes) c = kClsMemoLong;
     return c * kLenBuckets + (kLenBuckets - 1 - lb);
 }
 
-__global__ void k_plan_hist(const int64_t* __restrict__ off, const uint8_t* __restrict__ cls, long long n,
-                            long long per, int nbk, unsigned* __restrict__ hist_blk) {
+// keys of the tile at `base` (-1 past hi)
+__device__ __forceinline__ void plan_tile_keys(const int64_t* off, const uint8_t* cls, long long base, long long hi,
+                                               int (&key)[kPlanItems]) {
+#pragma unroll
+    for (int k = 0; k < kPlanItems; k++) {
+        const long long i = base + k * kPlanThreads + threadIdx.x;
+        key[k] = i < hi ? plan_key(off, cls, i) : -1;
+    }
+}
+
+__device__ void plan_count(const int64_t* off, const uint8_t* cls, long long lo, long long hi, unsigned* sh) {
+    for (long long base = lo; base < hi; base += kPlanTile) {
+        int key[kPlanItems];
+        plan_tile_keys(off, cls, base, hi, key);
+#pragma unroll
+        for (int k = 0; k < kPlanItems; k++)
+            if (key[k] >= 0) atomicAdd(&sh[key[k]], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __restrict__ off,
+                                                            const uint8_t* __restrict__ cls, long long n,
+                                                            long long per, int nbk, unsigned* __restrict__ totals,
+                                                            unsigned* __restrict__ cursor, unsigned* __restrict__ done,
+                                                            unsigned* __restrict__ queue) {
     extern __shared__ unsigned sh[];
-    for (int b = threadIdx.x; b < nbk; b += blockDim.x) sh[b] = 0;
+    __shared__ unsigned ticket;
+    __shared__ unsigned wsum[kPlanThreads / 32];
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
-    long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&sh[plan_key(off, cls, i)], 1u);
+    const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
+    plan_count(off, cls, lo, hi, sh);
     __syncthreads();
-    for (int b = threadIdx.x; b < nbk; b += blockDim.x) hist_blk[(size_t)blockIdx.x * nbk + b] = sh[b];
-}
-
-__global__ void k_plan_colscan(unsigned* __restrict__ hist_blk, int nblk, int nbk, unsigned* __restrict__ totals) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbk) return;
-    unsigned run = 0;
-    int g = 0;
-    for (; g + 8 <= nblk; g += 8) {
-        unsigned h[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) h[k] = hist_blk[(size_t)(g + k) * nbk + b];
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            hist_blk[(size_t)(g + k) * nbk + b] = run;
-            run += h[k];
-        }
-    }
-    for (; g < nblk; g++) {
-        unsigned h = hist_blk[(size_t)g * nbk + b];
-        hist_blk[(size_t)g * nbk + b] = run;
-        run += h;
-    }
-    totals[b] = run;
-}
-
-__global__ void k_plan_scan(unsigned* __restrict__ totals, int nbk, unsigned* __restrict__ queue) {
-    __shared__ unsigned part[1024];
-    int t = threadIdx.x;
-    if (t == 0 && queue) *queue = 0;  // the work counter of the kernel that follows
-    int per = (nbk + 1023) / 1024;
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
+        if (sh[b]) atomicAdd(&totals[b], sh[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(done, 1u);
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    // the last block: every other block's counts are in the totals
+    __threadfence();
+    const int per_t = (nbk + kPlanThreads - 1) / kPlanThreads;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     unsigned sum = 0;
-    for (int j = 0; j < per; j++) {
-        int b = t * per + j;
-        if (b < nbk) sum += totals[b];
-    }
-    part[t] = sum;
-    __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {
-        unsigned v = (t >= d) ? part[t - d] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    unsigned run = part[t] - sum;
-    for (int j = 0; j < per; j++) {
-        int b = t * per + j;
+    for (int j = 0; j < per_t; j++) {
+        const int b = t * per_t + j;
         if (b < nbk) {
-            unsigned h = totals[b];
-            totals[b] = run;
-            run += h;
+            const unsigned v = __ldcg(&totals[b]);
+            sh[b] = v;
+            sum += v;
         }
     }
+    unsigned incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned w = lane < kPlanThreads / 32 ? wsum[lane] : 0u, wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += v;
+        }
+        if (lane < kPlanThreads / 32) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    unsigned run = wsum[wid] + incl - sum;
+    for (int j = 0; j < per_t; j++) {
+        const int b = t * per_t + j;
+        if (b < nbk) {
+            totals[b] = run;
+            cursor[b] = run;
+            run += sh[b];
+        }
+    }
+    if (t == 0 && queue) *queue = 0;
 }
 
-__global__ void k_plan_scatter(const int64_t* __restrict__ off, const uint8_t* __restrict__ cls, long long n,
-                               long long per, int nbk, const unsigned* __restrict__ cur_blk,
-                               const unsigned* __restrict__ starts, uint32_t* __restrict__ perm) {
+__global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __restrict__ off,
+                                                               const uint8_t* __restrict__ cls, long long n,
+                                                               long long per, int nbk,
+                                                               unsigned* __restrict__ cursor,
+                                                               uint32_t* __restrict__ perm) {
     extern __shared__ unsigned sh[];
-    for (int b = threadIdx.x; b < nbk; b += blockDim.x) sh[b] = starts[b] + cur_blk[(size_t)blockIdx.x * nbk + b];
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
-    long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        unsigned pos = atomicAdd(&sh[plan_key(off, cls, i)], 1u);
-        perm[pos] = (uint32_t)i;
+    const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
+    plan_count(off, cls, lo, hi, sh);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
+        if (sh[b]) sh[b] = atomicAdd(&cursor[b], sh[b]);
+    __syncthreads();
+    for (long long base = lo; base < hi; base += kPlanTile) {
+        int key[kPlanItems];
+        plan_tile_keys(off, cls, base, hi, key);
+#pragma unroll
+        for (int k = 0; k < kPlanItems; k++)
+            if (key[k] >= 0) perm[atomicAdd(&sh[key[k]], 1u)] = (uint32_t)(base + k * kPlanThreads + threadIdx.x);
     }
 }
 
@@ -348,36 +392,36 @@ int sm_count() {
     return cached[dev];
 }
 
+// one tile per block up to 64 blocks per SM, then several tiles per block
 int plan_blocks(size_t n) {
-    long long g = ((long long)n + 8191) / 8192;
-    return (int)std::max<long long>(1, std::min<long long>(g, (long long)sm_count()));
+    long long g = ((long long)n + kPlanTile - 1) / kPlanTile;
+    return (int)std::max<long long>(1, std::min<long long>(g, (long long)sm_count() * 64));
 }
 
+// totals (+ the finish counter after them), cursors, permutation
 size_t plan_workspace_bytes(size_t n, int nclasses) {
     size_t nbk = (size_t)kLenBuckets * nclasses;
-    return align16((size_t)plan_blocks(n) * nbk * 4) + align16(nbk * 4) + align16(n * 4);
+    return align16(nbk * 4 + 4) + align16(nbk * 4) + align16(n * 4);
 }
 
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
                         unsigned** starts, cudaStream_t st, unsigned* queue) {
-    const int nbk = kLenBuckets * nclasses;
+    const int nbk = kLenBuckets * nclasses;  // at most 7 x 384 buckets: 10.5 KiB of shared memory
     const int G = plan_blocks(n);
-    const long long per = ((long long)n + G - 1) / G;
+    long long per = ((long long)n + G - 1) / G;
+    per = (per + kPlanTile - 1) / kPlanTile * kPlanTile;
     uint8_t* w = static_cast<uint8_t*>(ws);
-    unsigned* hist_blk = reinterpret_cast<unsigned*>(w);
-    unsigned* totals = reinterpret_cast<unsigned*>(w + align16((size_t)G * nbk * 4));
-    *perm = reinterpret_cast<uint32_t*>(w + align16((size_t)G * nbk * 4) + align16((size_t)nbk * 4));
+    unsigned* totals = reinterpret_cast<unsigned*>(w);
+    unsigned* done = totals + nbk;
+    unsigned* cursor = reinterpret_cast<unsigned*>(w + align16((size_t)nbk * 4 + 4));
+    *perm = reinterpret_cast<uint32_t*>(w + align16((size_t)nbk * 4 + 4) + align16((size_t)nbk * 4));
     *starts = totals;
-    size_t shb = (size_t)nbk * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_plan_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_plan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+    const size_t shb = (size_t)nbk * 4;
+    cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)nbk * 4 + 4, st);
     if (e != cudaSuccess) return e;
-    k_plan_hist<<<G, 512, shb, st>>>(off, cls, (long long)n, per, nbk, hist_blk);
-    k_plan_colscan<<<(nbk + 255) / 256, 256, 0, st>>>(hist_blk, G, nbk, totals);
-    k_plan_scan<<<1, 1024, 0, st>>>(totals, nbk, queue);
-    k_plan_scatter<<<G, 512, shb, st>>>(off, cls, (long long)n, per, nbk, hist_blk, totals, *perm);
-    prof_count(4);
+    k_plan_hist<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, totals, cursor, done, queue);
+    k_plan_scatter<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, cursor, *perm);
+    prof_count(2);
     return cudaGetLastError();
 }
 

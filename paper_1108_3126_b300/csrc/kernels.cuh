@@ -45,8 +45,12 @@ cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, si
 struct BatchTab {
     DevTables t;
 };
-constexpr int kBatchClasses = 6;
-enum { kClsWarp = 0, kClsSparse8 = 1, kClsSparse4 = 2, kClsThread2 = 3, kClsThread1 = 4, kClsMemo = 5 };
+// kClsMemoLong: memo pairs longer than kLongPairBytes (assigned on the device
+// by the planner from the pair's length), one warp per pair, chunked.
+constexpr int kBatchClasses = 7;
+enum { kClsMemoLong = 0, kClsWarp = 1, kClsSparse8 = 2, kClsSparse4 = 3, kClsThread2 = 4, kClsThread1 = 5,
+       kClsMemo = 6 };
+constexpr int64_t kLongPairBytes = 8192;
 size_t batch_workspace_bytes(size_t n, size_t ntabs);
 cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
                          size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,

@@ -59,9 +59,12 @@ int serve_class(const rx_regex* h) {
 template <class S>
 __device__ __forceinline__ void tick_lane(const ServeSlot& sl, bool valid, int64_t tick, uint32_t* state,
                                           uint8_t* status) {
+    // every lane binds a table -- a lane past the class's slots gets the
+    // table of the class's first slot -- because the span loop steps every
+    // lane (killed ones on the empty set) and a step reads the table
     S st;
+    st.bind_global(*sl.tab);
     if (valid) {
-        st.bind_global(*sl.tab);
         if (sl.pos > 0) st.restore(state);
     } else {
         st.kill();

@@ -191,3 +191,39 @@ def test_batched_edges():
     rx.match_batch([], d, o, out)  # n = 0 is a no-op
     with pytest.raises(rx.RxError):
         rx.match_batch([rx.Regex.compile(b"a", rx.COMPILE_HOST_ONLY)], d, o, out)
+
+
+def test_batched_long_pairs_chunked_per_warp():
+    """Pairs longer than 8 KiB whose expression has a cache of macro steps run
+    one warp per pair (32 chunks, exact transfer functions composed by lane
+    0).  Mix them with short pairs of the same and other expressions."""
+    rng = np.random.default_rng(0xE9)
+    regs, strs, rid = [], [], []
+    for i in range(40):
+        alpha = [synth.LOWER, synth.ALL_BYTES, b"abc"][i % 3]
+        e = synth.gen_regex([12, 40, 100, 300][i % 4], 12, alpha, synth.item_seed(0xEA, i), eps_loop_p=0.05)
+        regs.append(e)
+        s = synth.gen_strings(e, 8, 0, 70000, alpha, synth.item_seed(0xEB, i), p_lang=0.7, log_len=True)
+        for k in range(s.n):
+            strs.append(s.get(k))
+            rid.append(i)
+        # some long ones for sure
+        s2 = synth.gen_strings(e, 3, 9000, 70000, alpha, synth.item_seed(0xEC, i), p_lang=0.8)
+        for k in range(s2.n):
+            strs.append(s2.get(k))
+            rid.append(i)
+    order = rng.permutation(len(strs))
+    strs = [strs[k] for k in order]
+    rid = [rid[k] for k in order]
+    assert sum(len(w) > 8192 for w in strs) >= 100
+    handles = [rx.Regex.from_nodes(nd) for nd in regs]
+    assert all(h.info()["memo_states"] > 0 for h in handles)
+    pk = synth.pack(strs)
+    d, o = dev(pk.data), dev(pk.offsets)
+    out = torch.full((pk.n,), 7, dtype=torch.uint8, device="cuda")
+    hl = [handles[i] for i in rid]
+    rx.match_batch(hl, d, o, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    want = np.array([oracle.o2(regs[rid[k]], strs[k]) for k in range(pk.n)], np.uint8)
+    assert (got == want).all(), np.nonzero(got != want)[0][:10]

@@ -205,6 +205,33 @@ def test_seq_and_pairs_forms():
         assert int(one.item()) == want[i]
 
 
+def test_pair_kernel_fallback_outside_the_byte_window():
+    """The two-byte cache applies to 32-byte blocks whose bytes all lie in the
+    expression's label window; blocks with other bytes (for some lanes or
+    all) take the one-byte path.  Mix such bytes into language samples."""
+    rng = np.random.default_rng(5)
+    for i in range(6):
+        e = synth.gen_regex(64, 10, synth.LOWER, synth.item_seed(0xDE, i))
+        r = rx.Regex.from_nodes(e)
+        s = synth.gen_strings(e, 3000, 1, 700, synth.LOWER, synth.item_seed(0xDF, i), p_lang=0.8)
+        data = s.data.copy()
+        # sprinkle bytes outside [0x60, 0x80) into a third of the strings
+        for k in range(0, s.n, 3):
+            a, b = int(s.offsets[k]), int(s.offsets[k + 1])
+            if b > a:
+                pos = rng.integers(a, b, size=max(1, (b - a) // 97))
+                data[pos] = rng.choice([0x00, 0x41, 0x5F, 0x80, 0x7B, 0xFF], size=len(pos))
+        mixed = synth.Strings(data, s.offsets, s.kind, 0)
+        want = oracle.o2_batch(e, data, s.offsets)
+        for v, block in ((0, 0), (rx.VARIANT_MEMO, 0), (rx.VARIANT_MEMO, 257), (rx.VARIANT_THREAD, 0)):
+            got = run(r, mixed, v, block=block)
+            assert (got == want).all(), (i, v, block, np.nonzero(got != want)[0][:10])
+        # and strings made only of out-of-window bytes
+        junk = synth.pack([bytes(rng.integers(0x80, 0x100, size=n).tolist()) for n in rng.integers(0, 300, 200)])
+        wantj = oracle.o2_batch(e, junk.data, junk.offsets)
+        assert (run(r, junk) == wantj).all()
+
+
 def test_autotune_records_and_is_used():
     w = synth.cfg_streaming(seed=synth.SEED_BASE + 77, n=20000)
     nodes = w.regexes[0]
@@ -237,3 +264,75 @@ def test_errors_do_not_poison_the_context():
         run(r2, s, rx.VARIANT_MEMO)
     assert ei.value.status == 8
     assert (run(r, synth.pack([b"abbb", b"ba"])) == np.array([1, 0])).all()
+
+
+def test_host_buffers_pipelined_pieces():
+    """rx_match_host on host buffers: the full-size streaming batch (537 MB,
+    about nine 64 MiB pieces) equals the device-buffer path element by
+    element, and strings around every piece boundary agree with O2."""
+    w = synth.cfg_streaming()
+    nodes = w.regexes[0]
+    r = rx.Regex.from_nodes(nodes)
+    dref = run(r, w.strings)
+    h_str = torch.from_numpy(w.strings.data).pin_memory()
+    h_off = torch.from_numpy(w.strings.offsets).pin_memory()
+    h_out = torch.full((w.strings.n,), 7, dtype=torch.uint8).pin_memory()
+    rx.match_host(r, h_str, h_off, h_out)
+    got = h_out.numpy()
+    assert (got == dref).all(), np.nonzero(got != dref)[0][:10]
+    # strings at and next to each 64 MiB cut, plus a random sample, vs O2
+    offs = w.strings.offsets
+    cuts = np.searchsorted(offs, np.arange(1, 10) * (64 << 20))
+    rng = np.random.default_rng(3)
+    idx = set(rng.choice(w.strings.n, 1500, replace=False).tolist())
+    for c in cuts:
+        idx.update(range(max(0, int(c) - 4), min(w.strings.n, int(c) + 4)))
+    idx = np.array(sorted(idx))
+    sub = synth.pack([w.strings.get(int(i)) for i in idx])
+    want = oracle.o2_batch(nodes, sub.data, sub.offsets)
+    assert (got[idx] == want).all()
+    # pageable numpy buffers, a second call on the same stream
+    out2 = np.full(w.strings.n, 9, np.uint8)
+    rx.match_host(r, w.strings.data, w.strings.offsets, out2)
+    assert (out2 == dref).all()
+
+
+def test_host_buffers_many_short_strings_and_offsets_not_at_zero():
+    """More than 2^20 strings (pieces cut by count), empty strings, offsets
+    that start past byte 0 and end before the buffer does."""
+    rng = np.random.default_rng(11)
+    e = oracle.parse(b"(a|b)*a(a|b)")  # second-to-last byte is 'a'
+    r = rx.Regex.from_nodes(e)
+    n = (1 << 20) * 2 + 12345
+    lens = rng.integers(0, 6, size=n)
+    offs = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    body = rng.choice(np.frombuffer(b"ab", np.uint8), size=int(offs[-1]))
+    data = np.concatenate([np.frombuffer(b"zzzzz", np.uint8), body, np.frombuffer(b"zz", np.uint8)])
+    offs5 = offs + 5
+    out = np.full(n, 7, np.uint8)
+    rx.match_host(r, data, offs5, out)
+    # closed form of the language: length >= 2 and byte len-2 is 'a'
+    ends = offs5[1:]
+    want = (lens >= 2) & (data[np.maximum(ends - 2, 0)] == ord("a"))
+    assert (out == want.astype(np.uint8)).all()
+    # and O2 on a sample spanning the count cuts
+    idx = np.unique(np.concatenate([rng.choice(n, 3000, replace=False), np.arange((1 << 20) - 3, (1 << 20) + 3),
+                                    np.arange((2 << 20) - 3, (2 << 20) + 3)]))
+    sub = synth.pack([data[offs5[i]:offs5[i + 1]].tobytes() for i in idx])
+    assert (out[idx] == oracle.o2_batch(e, sub.data, sub.offsets)).all()
+
+
+def test_host_buffers_edges_and_errors():
+    r = rx.Regex.compile(b"a*")
+    out = np.zeros(1, np.uint8)
+    rx.match_host(r, np.zeros(1, np.uint8), np.zeros(1, np.int64), out, n=0)
+    s = synth.pack([b"", b"aaa", b"ab", b"a" * (70 << 20)])  # one string above the piece size
+    got = np.full(4, 7, np.uint8)
+    rx.match_host(r, s.data, s.offsets, got)
+    assert got.tolist() == [1, 1, 0, 1]
+    bad = np.array([0, 5, 3], np.int64)
+    with pytest.raises(rx.RxError) as ei:
+        rx.match_host(r, np.zeros(8, np.uint8), bad, np.zeros(2, np.uint8))
+    assert ei.value.status == 2
+    assert (run(r, synth.pack([b"aa", b"b"])) == np.array([1, 0])).all()
