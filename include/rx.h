@@ -259,6 +259,48 @@ rx_status rx_match_pairs(const rx_handle* handles, size_t n, const uint8_t* stri
                          uint8_t* out, void* stream);
 
 /*
+ * Prepared batches -- the pairs' expressions fixed once, every run replayed
+ * from a captured CUDA graph.  Each pair is decided as in rx_match_batch
+ * (Def 5.3 for its own expression); the paper has no counterpart for the
+ * preparation, which concerns only how launches are issued.
+ *
+ * rx_batch_prepare: handles is a HOST array of n handles (pair i uses
+ *   handles[i]; they must outlive the plan).  Uploads the distinct tables,
+ *   the per-pair table index and class, and allocates the plan's device
+ *   scratch (9 bytes per pair, a table header per expression and the
+ *   planner's buckets) with cudaMalloc on the current device; synchronous.
+ *   Errors: RX_ERR_INVALID_ARG (null or host-only handle), RX_ERR_TOO_LARGE
+ *   (n >= 2^31), RX_ERR_OOM, RX_ERR_CUDA.  On error *out is NULL.
+ * rx_batch_run: strings/offsets/out are DEVICE buffers laid out as in
+ *   rx_match_batch, for the plan's n pairs (async on `stream`).  The first
+ *   run with a given (strings, offsets, out) captures the run's launches
+ *   (work-counter reset, planner, persistent kernel) into a graph on a
+ *   private stream; later runs with the same three pointers replay it, a
+ *   different triple captures anew.  Runs on one plan must not overlap on
+ *   the GPU (they share the plan's scratch): serialise them on one stream.
+ *   Errors: RX_ERR_INVALID_ARG, RX_ERR_CUDA.
+ * rx_batch_autotune: runs the batch (results written to out) with every
+ *   launch shape -- 128, 256 or 512 threads per block; cached pairs longer
+ *   than 2, 4, 8, 16 or 32 KiB, or never, taking a whole warp (chunked) --
+ *   timed with CUDA events on `stream`, and keeps the fastest for later
+ *   runs; *chosen (optional) receives it and its rate.  Synchronous.
+ *   Errors: as rx_batch_run.
+ * rx_batch_free: releases the plan; no run of it may still be in flight.
+ */
+typedef struct rx_batch* rx_batch_handle;
+typedef struct rx_batch_tune {
+    int64_t long_pair_bytes;  /* cached pairs longer than this take a warp */
+    int32_t block;            /* threads per block of the persistent kernel */
+    float gb_per_s;           /* measured input bytes per second / 1e9     */
+} rx_batch_tune;
+rx_status rx_batch_prepare(const rx_handle* handles, size_t n, rx_batch_handle* out);
+rx_status rx_batch_run(rx_batch_handle b, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                       void* stream);
+rx_status rx_batch_autotune(rx_batch_handle b, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
+                            void* stream, rx_batch_tune* chosen);
+void rx_batch_free(rx_batch_handle b);
+
+/*
  * rx_match_long -- one long string, exact chunked mode (async).  The input
  * is cut into chunks; for each chunk the transfer function of the macro
  * step (Def 5.2) over the chunk is computed in parallel from every possible

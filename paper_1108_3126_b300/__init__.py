@@ -56,6 +56,10 @@ class TuneEntry(ctypes.Structure):
                 ("variant", ctypes.c_int32), ("block", ctypes.c_int32), ("gb_per_s", ctypes.c_float)]
 
 
+class BatchTune(ctypes.Structure):
+    _fields_ = [("long_pair_bytes", ctypes.c_int64), ("block", ctypes.c_int32), ("gb_per_s", ctypes.c_float)]
+
+
 class ServeCfg(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("tick_bytes", ctypes.c_int64),
@@ -84,6 +88,10 @@ SIGNATURES = {
     "rx_match_host": ([P, SZ, P, P, P, P], I32),
     "rx_match_batch": ([P, SZ, P, P, P, P], I32),
     "rx_match_pairs": ([P, SZ, P, P, P, P], I32),
+    "rx_batch_prepare": ([P, SZ, ctypes.POINTER(P)], I32),
+    "rx_batch_run": ([P, P, P, P, P], I32),
+    "rx_batch_autotune": ([P, P, P, P, P, ctypes.POINTER(BatchTune)], I32),
+    "rx_batch_free": ([P], None),
     "rx_match_long": ([P, P, I64, I64, P, P], I32),
     "rx_match_seq": ([P, P, I64, P, P], I32),
     "rx_trace": ([P, P, I64, P, P], I32),
@@ -264,6 +272,39 @@ def match_batch(regexes, strings, offsets, out, stream=None):
     hs = _handles(regexes)
     _check(lib().rx_match_batch(hs.ctypes.data, len(hs), _ptr(strings), _ptr(offsets), _ptr(out),
                                 _stream(stream)))
+
+
+class Batch:
+    """A prepared batch: pair i = (regexes[i], string i) for a fixed list of
+    expressions; run() replays a captured CUDA graph of the batched launch."""
+
+    def __init__(self, regexes):
+        self._hs = _handles(regexes)
+        self._keep = None if isinstance(regexes, np.ndarray) else list(regexes)
+        self.n = len(self._hs)
+        h = P()
+        _check(lib().rx_batch_prepare(self._hs.ctypes.data, self.n, ctypes.byref(h)))
+        self.handle = h.value
+
+    def run(self, strings, offsets, out, stream=None):
+        _check(lib().rx_batch_run(self.handle, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream)))
+
+    def autotune(self, strings, offsets, out, stream=None) -> dict:
+        t = BatchTune()
+        _check(lib().rx_batch_autotune(self.handle, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream),
+                                       ctypes.byref(t)))
+        return {"long_pair_bytes": int(t.long_pair_bytes), "block": int(t.block), "gb_per_s": float(t.gb_per_s)}
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().rx_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def match_pairs(regexes, strings, offsets, out, stream=None):

@@ -81,6 +81,7 @@ static rx_status upload(rx_regex* h) {
     size_t o_start = take(W * 4), o_B = take((size_t)256 * W * 4), o_fol = take((size_t)C.nbits * W * 4);
     size_t o_desc = take(256 * sizeof(uint2)), o_tt = take(std::max<size_t>(C.gl_tt.size(), 1) * 4);
     size_t o_T = take(std::max<size_t>(C.memo_T.size(), 1) * 4), o_acc = take(std::max<size_t>(C.memo_acc.size(), 1));
+    size_t o_T8 = take(std::max<size_t>(C.memo_T.size(), 1));
     size_t o_nd = take(C.nodes.size() * sizeof(int4));
     const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
     size_t o_sps = take(spW * 4 + 16), o_spB = take((size_t)256 * spW * 4 + 16),
@@ -98,6 +99,7 @@ static rx_status upload(rx_regex* h) {
     put(o_desc, C.gl_desc.data(), 256 * sizeof(uint2));
     put(o_tt, C.gl_tt.data(), C.gl_tt.size() * 4);
     put(o_T, C.memo_T.data(), C.memo_T.size() * 4);
+    for (size_t i = 0; i < C.memo_T.size(); i++) blob[o_T8 + i] = (uint8_t)(C.memo_T[i] / 256u);  // ids < 192
     put(o_acc, C.memo_acc.data(), C.memo_acc.size());
     std::vector<int4> pn(C.nodes.size());
     for (size_t i = 0; i < C.nodes.size(); i++)
@@ -145,6 +147,7 @@ static rx_status upload(rx_regex* h) {
     t.sp_follow = reinterpret_cast<const uint32_t*>(b + o_spF);
     t.memo_K = C.memo_K;
     t.memo_T = reinterpret_cast<const uint32_t*>(b + o_T);
+    t.memo_T8 = b + o_T8;
     t.memo_acc = b + o_acc;
     t.memo_start = C.memo_start;
     t.bg_T = C.bg_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bg);
@@ -469,36 +472,34 @@ static int batch_class(const rx_regex* h) {
     return rx::kClsWarp;
 }
 
-rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
-                         uint8_t* out, void* stream) {
-    RX_GUARD_BEGIN
-    if (n == 0) return RX_OK;
-    if (!handles || !offsets || !out) {
-        rx::set_error("rx_match_batch: null argument");
-        return RX_ERR_INVALID_ARG;
-    }
+}  // extern "C"
+
+namespace rx {
+// Distinct tables of the pairs' expressions, the table index and the class
+// of every pair (host arrays for the batched kernel).
+rx_status collect_pairs(const rx_handle* handles, size_t n, const char* who, std::vector<BatchTab>& tabs,
+                        std::vector<uint32_t>& pair_tab, std::vector<uint8_t>& cls) {
     if (n > 0x7fffffffull) {
-        rx::set_error("rx_match_batch: more than 2^31 pairs");
+        set_error(std::string(who) + ": more than 2^31 pairs");
         return RX_ERR_TOO_LARGE;
     }
     std::unordered_map<const rx_regex*, uint32_t> index;
-    std::vector<rx::BatchTab> tabs;
-    std::vector<uint32_t> pair_tab(n);
-    std::vector<uint8_t> cls(n);
     std::vector<uint8_t> tab_cls;
+    pair_tab.resize(n);
+    cls.resize(n);
     const rx_regex* last = nullptr;
     uint32_t last_i = 0;
     for (size_t i = 0; i < n; i++) {
         const rx_regex* h = handles[i];
         if (h != last) {
             if (!h || h->host_only) {
-                rx::set_error("rx_match_batch: null or host-only handle at pair " + std::to_string(i));
+                set_error(std::string(who) + ": null or host-only handle at pair " + std::to_string(i));
                 return RX_ERR_INVALID_ARG;
             }
             auto it = index.find(h);
             if (it == index.end()) {
                 it = index.emplace(h, (uint32_t)tabs.size()).first;
-                rx::BatchTab bt;
+                BatchTab bt;
                 bt.t = h->dev;
                 tabs.push_back(bt);
                 tab_cls.push_back((uint8_t)batch_class(h));
@@ -509,10 +510,29 @@ rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* stri
         pair_tab[i] = last_i;
         cls[i] = tab_cls[last_i];
     }
+    return RX_OK;
+}
+}  // namespace rx
+
+extern "C" {
+
+rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
+                         uint8_t* out, void* stream) {
+    RX_GUARD_BEGIN
+    if (n == 0) return RX_OK;
+    if (!handles || !offsets || !out) {
+        rx::set_error("rx_match_batch: null argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    std::vector<rx::BatchTab> tabs;
+    std::vector<uint32_t> pair_tab;
+    std::vector<uint8_t> cls;
+    rx_status s = rx::collect_pairs(handles, n, "rx_match_batch", tabs, pair_tab, cls);
+    if (s != RX_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     size_t need = rx::batch_workspace_bytes(n, tabs.size());
     void* ws = nullptr;
-    rx_status s = rx::get_workspace(st, need, &ws);
+    s = rx::get_workspace(st, need, &ws);
     if (s != RX_OK) return s;
     cudaError_t e = rx::launch_batch(tabs.data(), tabs.size(), pair_tab.data(), cls.data(), n, strings, offsets, out,
                                      ws, need, st);

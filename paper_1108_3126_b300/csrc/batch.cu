@@ -11,11 +11,11 @@
 //
 // Long pairs with a cache of macro steps (kClsMemoLong) would make one lane
 // the critical path of the whole launch, so a warp takes such a pair alone:
-// its 32 lanes cut the string into 32 chunks; each lane runs every cache
-// state over a short prefix of its chunk, then only the distinct states
-// reached over the rest (the chunk's transfer function, exactly: a macro step
-// acts on states, Def 5.2), and lane 0 composes the 32 functions from the
-// start state.
+// its 32 lanes cut the string into 32 chunks; each lane computes its chunk's
+// transfer function on cache states (exact: a macro step acts on states,
+// Def 5.2), advancing every incoming state through prefix stages of growing
+// length and keeping only the distinct states after each, and lane 0
+// composes the 32 functions from the start state.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -27,62 +27,92 @@ namespace {
 
 using namespace rx::dev;
 
-constexpr int kPairPrefix = 32;
 static_assert(kMemoMaxStates <= 256, "chunk maps hold cache state ids in one byte");
 
-// one lane, bytes [s, e) (absolute addresses), cache state st (row offset
-// in words), table T in global memory; stops when the set is empty
-__device__ uint32_t lane_memo_run(const uint32_t* __restrict__ T, uint32_t st, uint64_t s, uint64_t e) {
+// one lane, bytes [s, e) (absolute addresses), cache state st (id * 256),
+// one-byte table T in global memory; stops when the set is empty
+__device__ uint32_t lane_memo_run(const uint8_t* __restrict__ T, uint32_t st, uint64_t s, uint64_t e) {
     uint64_t blk = s & ~uint64_t(15);
     while (blk < e && st != 0) {
         uint4 v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             uint64_t p = blk + k;
-            if (p >= s && p < e) st = __ldg(T + st + byte_of(v, k));
+            if (p >= s && p < e) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
         }
         blk += 16;
     }
     return st;
 }
 
-// one warp, one long pair: returns whether the pair matches (all lanes);
-// wsm holds 32 chunk maps of `stride` bytes (stride >= memo_K)
+constexpr int kBmWords = (kMemoMaxStates + 31) / 32;
+constexpr int kStage0 = 4;  // bytes of the first prefix stage; each stage doubles
+
+// number of set bits of bm below bit v
+__device__ __forceinline__ uint32_t rank_below(const uint32_t (&bm)[kBmWords], uint32_t v) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int w = 0; w < kBmWords; w++) {
+        const uint32_t x = (w < (int)(v >> 5)) ? bm[w] : (w == (int)(v >> 5) ? (bm[w] & ((1u << (v & 31)) - 1u)) : 0u);
+        r += __popc(x);
+    }
+    return r;
+}
+
+// one warp, one long pair: returns whether the pair matches (all lanes).
+// Lane l computes the transfer map of chunk l for every cache state.  The
+// incoming states are advanced in stages of 4, 8, 16, ... bytes; after each
+// stage the states reached are deduplicated (a bitmap; rank = index), so
+// only the distinct ones go on -- states merge within a few bytes, and two
+// incoming states that meet stay together (Def 5.2 is a function of the
+// set).  wsm holds, per lane, map[K] (incoming state -> index of its
+// representative) and then, after the 32 maps, dv[K] (each representative's
+// current state); `stride` >= memo_K bytes each.
 __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
     const int lane = threadIdx.x & 31;
     const int K = t.memo_K;
-    const uint32_t* T = t.memo_T;
+    const uint8_t* T = t.memo_T8;
     const uint64_t L = e - s;
     const uint64_t C = ((L + 31) / 32 + 15) & ~uint64_t(15);
     uint64_t cs = s + (uint64_t)lane * C;
     if (cs > e) cs = e;
-    uint64_t ce = cs + C < e ? cs + C : e;
-    uint64_t cp = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
+    const uint64_t ce = cs + C < e ? cs + C : e;
     uint8_t* map = wsm + lane * stride;
-    // every incoming state over the prefix
-    for (int k = 0; k < K; k++) map[k] = (uint8_t)(lane_memo_run(T, (uint32_t)k * 256u, cs, cp) >> 8);
-    // the distinct states over the rest; a small cache of (state, result)
-    uint32_t cv[8], cr[8];
-    int nc = 0;
+    uint8_t* dv = wsm + (32 + lane) * stride;
     for (int k = 0; k < K; k++) {
-        uint32_t v = map[k], r = 0xffffffffu;
+        map[k] = (uint8_t)k;
+        dv[k] = (uint8_t)k;
+    }
+    int nd = K;
+    uint64_t pos = cs, len = kStage0;
+    while (nd > 1 && pos < ce) {
+        const uint64_t end = pos + len < ce ? pos + len : ce;
+        uint32_t bm[kBmWords];
 #pragma unroll
-        for (int q = 0; q < 8; q++)
-            if (q < nc && cv[q] == v) r = cr[q];
-        if (r == 0xffffffffu) {
-            r = lane_memo_run(T, v * 256u, cp, ce) >> 8;
-            if (nc < 8) {
+        for (int w = 0; w < kBmWords; w++) bm[w] = 0;
+        for (int i = 0; i < nd; i++) {
+            const uint32_t v = lane_memo_run(T, (uint32_t)dv[i] * 256u, pos, end) >> 8;
+            dv[i] = (uint8_t)v;
 #pragma unroll
-                for (int q = 0; q < 8; q++)
-                    if (q == nc) {
-                        cv[q] = v;
-                        cr[q] = r;
-                    }
-                nc++;
+            for (int w = 0; w < kBmWords; w++)
+                if (w == (int)(v >> 5)) bm[w] |= 1u << (v & 31);
+        }
+        for (int k = 0; k < K; k++) map[k] = (uint8_t)rank_below(bm, dv[map[k]]);
+        int j = 0;
+#pragma unroll
+        for (int w = 0; w < kBmWords; w++) {
+            uint32_t x = bm[w];
+            while (x) {
+                dv[j++] = (uint8_t)(w * 32 + __ffs(x) - 1);
+                x &= x - 1;
             }
         }
-        map[k] = (uint8_t)r;
+        nd = j;
+        pos = end;
+        len *= 2;
     }
+    for (int i = 0; i < nd; i++) dv[i] = (uint8_t)(lane_memo_run(T, (uint32_t)dv[i] * 256u, pos, ce) >> 8);
+    for (int k = 0; k < K; k++) map[k] = dv[map[k]];
     __syncwarp();
     uint32_t acc = 0;
     if (lane == 0) {
@@ -94,12 +124,12 @@ __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8
     return __shfl_sync(FULL, acc, 0) != 0;
 }
 
-__global__ void __launch_bounds__(256) k_batch(const BatchTab* __restrict__ tabs, const uint32_t* __restrict__ pair_tab,
+__global__ void __launch_bounds__(512) k_batch(const BatchTab* __restrict__ tabs, const uint32_t* __restrict__ pair_tab,
                                                const uint32_t* __restrict__ perm, const unsigned* __restrict__ starts,
                                                long long n, const uint8_t* __restrict__ str,
                                                const int64_t* __restrict__ off, uint8_t* __restrict__ out,
                                                unsigned* __restrict__ queue, int stride) {
-    extern __shared__ __align__(16) uint8_t bsm[];  // 32 x stride bytes per warp
+    extern __shared__ __align__(16) uint8_t bsm[];  // 64 x stride bytes per warp
     __shared__ long long seg[kBatchClasses + 1];
     __shared__ long long tfirst[kBatchClasses + 1];
     if (threadIdx.x == 0) {
@@ -129,7 +159,7 @@ __global__ void __launch_bounds__(256) k_batch(const BatchTab* __restrict__ tabs
             const uint32_t p = perm[seg[c] + g];
             const DevTables& t = tabs[pair_tab[p]].t;
             const uint64_t s = base + (uint64_t)off[p], e = base + (uint64_t)off[p + 1];
-            bool acc = warp_long_memo(t, s, e, bsm + (threadIdx.x >> 5) * 32 * stride, stride);
+            bool acc = warp_long_memo(t, s, e, bsm + (threadIdx.x >> 5) * 64 * stride, stride);
             if (lane == 0) out[p] = acc;
             continue;
         }
@@ -155,7 +185,7 @@ __global__ void __launch_bounds__(256) k_batch(const BatchTab* __restrict__ tabs
         }
         switch (c) {
         case kClsMemo: {
-            MemoStep st;
+            MemoStep8 st;
             st.bind_global(t);
             run_lane(st, s, e, valid, out + p);
             break;
@@ -190,49 +220,100 @@ __global__ void __launch_bounds__(256) k_batch(const BatchTab* __restrict__ tabs
 
 }  // namespace
 
+namespace {
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct BatchWs {
+    unsigned* queue;
+    BatchTab* tabs;
+    uint32_t* pair_tab;
+    uint8_t* cls;
+    void* plan_ws;
+};
+
+BatchWs batch_ws(void* ws, size_t n, size_t ntabs) {
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    BatchWs b;
+    b.queue = reinterpret_cast<unsigned*>(w);
+    b.tabs = reinterpret_cast<BatchTab*>(w + 256);
+    b.pair_tab = reinterpret_cast<uint32_t*>(w + 256 + a256(ntabs * sizeof(BatchTab)));
+    b.cls = w + 256 + a256(ntabs * sizeof(BatchTab)) + a256(n * 4);
+    b.plan_ws = w + 256 + a256(ntabs * sizeof(BatchTab)) + a256(n * 4) + a256(n);
+    return b;
+}
+}  // namespace
+
 size_t batch_workspace_bytes(size_t n, size_t ntabs) {
-    auto a = [](size_t x) { return (x + 255) & ~size_t(255); };
-    return 256 + a(ntabs * sizeof(BatchTab)) + a(n * 4) + a(n) + plan_workspace_bytes(n, kBatchClasses);
+    return 256 + a256(ntabs * sizeof(BatchTab)) + a256(n * 4) + a256(n) + plan_workspace_bytes(n, kBatchClasses);
+}
+
+// chunk maps of long pairs: 32 lanes x (largest cache over the batch's
+// expressions, rounded to 16) bytes per warp; none without a cache
+int batch_stride(const BatchTab* h_tabs, size_t ntabs) {
+    int stride = 0;
+    for (size_t i = 0; i < ntabs; i++) stride = std::max(stride, (int)((h_tabs[i].t.memo_K + 15) & ~15));
+    return stride;
+}
+
+cudaError_t batch_upload(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
+                         size_t n, void* ws, cudaStream_t st) {
+    BatchWs b = batch_ws(ws, n, ntabs);
+    cudaError_t e = cudaMemcpyAsync(b.tabs, h_tabs, ntabs * sizeof(BatchTab), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.pair_tab, h_pair_tab, n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.cls, h_cls, n, cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+// kernel attribute and resident blocks per SM for (stride, block)
+cudaError_t batch_configure(BatchLaunch& L) {
+    if (L.block != 128 && L.block != 256 && L.block != 512) return cudaErrorInvalidValue;
+    const size_t sm = (size_t)L.block * 2 * L.stride;  // at most 192 KiB (512 threads, 192 states)
+    cudaError_t e = allow_smem(k_batch, sm);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, L.block, sm);
+    if (e != cudaSuccess) return e;
+    L.grid_cap = (long long)std::max(per_sm, 1) * sm_count();
+    return cudaSuccess;
+}
+
+// counter reset, planner, persistent kernel: every launch of one batched
+// run, all on `st` (capturable into a graph)
+cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws,
+                      const BatchLaunch& L, cudaStream_t st, bool profile) {
+    if (n == 0) return cudaSuccess;
+    BatchWs b = batch_ws(ws, n, ntabs);
+    cudaError_t e = cudaMemsetAsync(b.queue, 0, 256, st);
+    if (e != cudaSuccess) return e;
+    uint32_t* perm = nullptr;
+    unsigned* starts = nullptr;
+    e = launch_plan(off, b.cls, kBatchClasses, n, b.plan_ws, &perm, &starts, st, nullptr, L.long_bytes);
+    if (e != cudaSuccess) return e;
+    const size_t sm = (size_t)L.block * 2 * L.stride;
+    long long grid = std::min<long long>(L.grid_cap, ((long long)n * 32 + L.block - 1) / L.block);
+    grid = std::max<long long>(grid, 1);
+    if (profile) {
+        ProfScope ps(st);
+        k_batch<<<(unsigned)grid, L.block, sm, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
+                                                     b.queue, L.stride);
+    } else {
+        k_batch<<<(unsigned)grid, L.block, sm, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
+                                                     b.queue, L.stride);
+        prof_count(1);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
                          size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
                          cudaStream_t st) {
-    // chunk maps of long pairs: 32 lanes x (largest cache over the batch's
-    // expressions, rounded to 16) bytes per warp; none without a cache
-    int stride = 0;
-    for (size_t i = 0; i < ntabs; i++)
-        stride = std::max(stride, (int)((h_tabs[i].t.memo_K + 15) & ~15));
     if (n == 0) return cudaSuccess;
     if (ws_bytes < batch_workspace_bytes(n, ntabs)) return cudaErrorInvalidValue;
-    auto a = [](size_t x) { return (x + 255) & ~size_t(255); };
-    uint8_t* w = static_cast<uint8_t*>(ws);
-    unsigned* queue = reinterpret_cast<unsigned*>(w);
-    BatchTab* tabs = reinterpret_cast<BatchTab*>(w + 256);
-    uint32_t* pair_tab = reinterpret_cast<uint32_t*>(w + 256 + a(ntabs * sizeof(BatchTab)));
-    uint8_t* cls = w + 256 + a(ntabs * sizeof(BatchTab)) + a(n * 4);
-    void* plan_ws = w + 256 + a(ntabs * sizeof(BatchTab)) + a(n * 4) + a(n);
-    cudaError_t e = cudaMemsetAsync(queue, 0, 256, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(tabs, h_tabs, ntabs * sizeof(BatchTab), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pair_tab, h_pair_tab, n * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cls, h_cls, n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    uint32_t* perm = nullptr;
-    unsigned* starts = nullptr;
-    e = launch_plan(off, cls, kBatchClasses, n, plan_ws, &perm, &starts, st, nullptr);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    const size_t sm = (size_t)8 * 32 * stride;  // at most 48 KiB (192 states)
-    e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1));
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, sm);
-    if (e != cudaSuccess) return e;
-    long long grid = std::min<long long>((long long)std::max(per_sm, 1) * sm_count(), ((long long)n * 32 + 255) / 256);
-    {
-        ProfScope ps(st);
-        k_batch<<<(unsigned)std::max<long long>(grid, 1), 256, sm, st>>>(tabs, pair_tab, perm, starts, (long long)n,
-                                                                         str, off, out, queue, stride);
-    }
-    return cudaGetLastError();
+    BatchLaunch L;
+    L.stride = batch_stride(h_tabs, ntabs);
+    cudaError_t e = batch_configure(L);
+    if (e == cudaSuccess) e = batch_upload(h_tabs, ntabs, h_pair_tab, h_cls, n, ws, st);
+    if (e == cudaSuccess) e = batch_run(n, ntabs, str, off, out, ws, L, st, true);
+    return e;
 }
 
 }  // namespace rx

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -132,28 +133,30 @@ __device__ __forceinline__ int len_bucket(int64_t len) {
     return b < kLenBuckets ? b : kLenBuckets - 1;
 }
 
-__device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, long long i) {
+// long_bytes: cached pairs longer than this go to kClsMemoLong
+__device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, long long i, long long long_bytes) {
     const int64_t len = off[i + 1] - off[i];
     int lb = len_bucket(len);
     int c = cls ? (int)cls[i] : 0;
-    if (cls && c == kClsMemo && len > kLongPairBytes) c = kClsMemoLong;
+    if (cls && c == kClsMemo && len > long_bytes) c = kClsMemoLong;
     return c * kLenBuckets + (kLenBuckets - 1 - lb);
 }
 
 // keys of the tile at `base` (-1 past hi)
 __device__ __forceinline__ void plan_tile_keys(const int64_t* off, const uint8_t* cls, long long base, long long hi,
-                                               int (&key)[kPlanItems]) {
+                                               long long long_bytes, int (&key)[kPlanItems]) {
 #pragma unroll
     for (int k = 0; k < kPlanItems; k++) {
         const long long i = base + k * kPlanThreads + threadIdx.x;
-        key[k] = i < hi ? plan_key(off, cls, i) : -1;
+        key[k] = i < hi ? plan_key(off, cls, i, long_bytes) : -1;
     }
 }
 
-__device__ void plan_count(const int64_t* off, const uint8_t* cls, long long lo, long long hi, unsigned* sh) {
+__device__ void plan_count(const int64_t* off, const uint8_t* cls, long long lo, long long hi, long long long_bytes,
+                           unsigned* sh) {
     for (long long base = lo; base < hi; base += kPlanTile) {
         int key[kPlanItems];
-        plan_tile_keys(off, cls, base, hi, key);
+        plan_tile_keys(off, cls, base, hi, long_bytes, key);
 #pragma unroll
         for (int k = 0; k < kPlanItems; k++)
             if (key[k] >= 0) atomicAdd(&sh[key[k]], 1u);
@@ -164,14 +167,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __res
                                                             const uint8_t* __restrict__ cls, long long n,
                                                             long long per, int nbk, unsigned* __restrict__ totals,
                                                             unsigned* __restrict__ cursor, unsigned* __restrict__ done,
-                                                            unsigned* __restrict__ queue) {
+                                                            unsigned* __restrict__ queue, long long long_bytes) {
     extern __shared__ unsigned sh[];
     __shared__ unsigned ticket;
     __shared__ unsigned wsum[kPlanThreads / 32];
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
     const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
-    plan_count(off, cls, lo, hi, sh);
+    plan_count(off, cls, lo, hi, long_bytes, sh);
     __syncthreads();
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
         if (sh[b]) atomicAdd(&totals[b], sh[b]);
@@ -227,19 +230,19 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __
                                                                const uint8_t* __restrict__ cls, long long n,
                                                                long long per, int nbk,
                                                                unsigned* __restrict__ cursor,
-                                                               uint32_t* __restrict__ perm) {
+                                                               uint32_t* __restrict__ perm, long long long_bytes) {
     extern __shared__ unsigned sh[];
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
     const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
-    plan_count(off, cls, lo, hi, sh);
+    plan_count(off, cls, lo, hi, long_bytes, sh);
     __syncthreads();
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
         if (sh[b]) sh[b] = atomicAdd(&cursor[b], sh[b]);
     __syncthreads();
     for (long long base = lo; base < hi; base += kPlanTile) {
         int key[kPlanItems];
-        plan_tile_keys(off, cls, base, hi, key);
+        plan_tile_keys(off, cls, base, hi, long_bytes, key);
 #pragma unroll
         for (int k = 0; k < kPlanItems; k++)
             if (key[k] >= 0) perm[atomicAdd(&sh[key[k]], 1u)] = (uint32_t)(base + k * kPlanThreads + threadIdx.x);
@@ -274,7 +277,7 @@ cudaError_t launch_thread_kernel(const DevTables& t, long long n, const uint8_t*
                                  const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
     size_t sm = S::smem_bytes(t);
     auto kern = k_thread<S>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t err = allow_smem(kern, sm);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm);
@@ -298,7 +301,7 @@ cudaError_t launch_warp_kernel(const DevTables& t, long long n, const uint8_t* s
     size_t bw = (size_t)256 * t.W, fw = (size_t)t.nbits * t.W;
     size_t sm = ((bw + fw) * 4 <= 160 * 1024) ? align16(bw * 4) + align16(fw * 4) : 0;
     auto kern = k_warp<K>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t err = allow_smem(kern, sm);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm);
@@ -379,6 +382,20 @@ cudaError_t prof_read(int64_t* launches, int64_t* timed, double* ms) {
     return err;
 }
 
+cudaError_t allow_smem_raw(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> high;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& h = high[std::make_pair(dev, func)];
+    if (bytes <= h && h > 0) return cudaSuccess;
+    const size_t want = std::max<size_t>(bytes, 1);
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+    if (e == cudaSuccess) h = want;
+    return e;
+}
+
 int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
@@ -405,7 +422,7 @@ size_t plan_workspace_bytes(size_t n, int nclasses) {
 }
 
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
-                        unsigned** starts, cudaStream_t st, unsigned* queue) {
+                        unsigned** starts, cudaStream_t st, unsigned* queue, long long long_bytes) {
     const int nbk = kLenBuckets * nclasses;  // at most 7 x 384 buckets: 10.5 KiB of shared memory
     const int G = plan_blocks(n);
     long long per = ((long long)n + G - 1) / G;
@@ -419,8 +436,9 @@ cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, si
     const size_t shb = (size_t)nbk * 4;
     cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)nbk * 4 + 4, st);
     if (e != cudaSuccess) return e;
-    k_plan_hist<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, totals, cursor, done, queue);
-    k_plan_scatter<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, cursor, *perm);
+    k_plan_hist<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, totals, cursor, done, queue,
+                                              long_bytes);
+    k_plan_scatter<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, cursor, *perm, long_bytes);
     prof_count(2);
     return cudaGetLastError();
 }

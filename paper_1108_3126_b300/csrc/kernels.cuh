@@ -38,23 +38,42 @@ cudaError_t launch_stream(const DevTables& t, int variant, long long n, const ui
 // cls (device, n bytes) may be NULL (one class).  Writes *perm (n u32) and
 // *starts (first slot of every bucket) inside ws.
 size_t plan_workspace_bytes(size_t n, int nclasses);
+// long_bytes: with classes, cached pairs longer than this are planned as
+// kClsMemoLong (see below)
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
-                        unsigned** starts, cudaStream_t st, unsigned* queue = nullptr);
+                        unsigned** starts, cudaStream_t st, unsigned* queue = nullptr,
+                        long long long_bytes = 8192);
 
 // Batched pairs (batch.cu).  Variant classes, in task order.
 struct BatchTab {
     DevTables t;
 };
-// kClsMemoLong: memo pairs longer than kLongPairBytes (assigned on the device
-// by the planner from the pair's length), one warp per pair, chunked.
+// kClsMemoLong: memo pairs longer than BatchLaunch::long_bytes (assigned on
+// the device by the planner from the pair's length), one warp per pair,
+// chunked.
 constexpr int kBatchClasses = 7;
 enum { kClsMemoLong = 0, kClsWarp = 1, kClsSparse8 = 2, kClsSparse4 = 3, kClsThread2 = 4, kClsThread1 = 5,
        kClsMemo = 6 };
-constexpr int64_t kLongPairBytes = 8192;
+struct BatchLaunch {
+    int stride = 0;               // chunk-map bytes per lane (largest cache, rounded to 16)
+    int block = 256;              // threads per block: 128, 256 or 512
+    long long long_bytes = 8192;  // cached pairs longer than this take a warp
+    long long grid_cap = 1;       // resident blocks (set by batch_configure)
+};
 size_t batch_workspace_bytes(size_t n, size_t ntabs);
+int batch_stride(const BatchTab* h_tabs, size_t ntabs);
+cudaError_t batch_upload(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
+                         size_t n, void* ws, cudaStream_t st);
+cudaError_t batch_configure(BatchLaunch& L);
+cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws,
+                      const BatchLaunch& L, cudaStream_t st, bool profile);
 cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
                          size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
                          cudaStream_t st);
+// host arrays of a batch: distinct tables, table index and class per pair
+// (api.cpp); `who` prefixes error messages
+rx_status collect_pairs(const rx_handle* handles, size_t n, const char* who, std::vector<BatchTab>& tabs,
+                        std::vector<uint32_t>& pair_tab, std::vector<uint8_t>& cls);
 
 // Spans of the chunked mode run from given cache states (stream.cu).
 cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
@@ -91,5 +110,14 @@ cudaError_t paper_match_one(const DevTables& t, const uint8_t* str, int64_t len,
 
 // Device properties cached per device.
 int sm_count();
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (never
+// lowers it, so a launch or a captured graph made for a larger size by
+// another thread or plan stays valid).
+cudaError_t allow_smem_raw(const void* func, size_t bytes);
+template <class F>
+cudaError_t allow_smem(F* func, size_t bytes) {
+    return allow_smem_raw(reinterpret_cast<const void*>(func), bytes);
+}
 
 }  // namespace rx

@@ -286,7 +286,7 @@ cudaError_t launch_chunk_rows(const DevTables& t, const uint8_t* str, int64_t le
     int groups = (t.nbits + 31) / 32;
     size_t sm = S::smem_bytes(t);
     auto kern = k_chunk_rows<S>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm);
@@ -304,8 +304,7 @@ template <int RW>
 cudaError_t compose_rows(const DevTables& t, uint32_t* a, uint32_t* b, long long J, uint8_t* out, cudaStream_t st) {
     const size_t mat = (size_t)t.nbits * RW * 4;
     int G = (int)std::max<size_t>(2, std::min<size_t>(64, (96 * 1024) / std::max<size_t>(mat, 1)));
-    cudaError_t e = cudaFuncSetAttribute(k_compose_rows<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(G * mat));
+    cudaError_t e = allow_smem(k_compose_rows<RW>, G * mat);
     if (e != cudaSuccess) return e;
     long long cnt = J;
     uint32_t* cur = a;
@@ -414,7 +413,7 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         // phase 1: every incoming state over the first P bytes of each chunk
         int groups = (K + 31) / 32;
         size_t sm = MemoStep::smem_bytes(t);
-        e = cudaFuncSetAttribute(k_chunk_memo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = allow_smem(k_chunk_memo, sm);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_memo, 256, sm);

@@ -45,6 +45,7 @@ struct DevTables {
     // macro-step cache
     int32_t memo_K;          // states (0: unavailable); state 0 is the empty set
     const uint32_t* memo_T;  // [K*256] next state * 256 (row start, in words)
+    const uint8_t* memo_T8;  // [K*256] next state id (the same table, one byte per entry, for global reads)
     const uint8_t* memo_acc; // [K] 1 iff the state's set holds null
     uint32_t memo_start;     // start state * 256
     // two-byte cache: for labels inside one 32-value window [bg_lo, bg_lo+32),

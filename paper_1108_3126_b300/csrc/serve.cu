@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_serve_tick(const ServeSlot* __restrict_
     uint32_t* stp = state + (size_t)slot * kStateWords;
     uint8_t* stt = status + 2 * slot;
     switch (c) {
-    case kClsMemo: tick_lane<MemoStep>(sl, valid, tick, stp, stt); break;
+    case kClsMemo: tick_lane<MemoStep8>(sl, valid, tick, stp, stt); break;
     case kClsThread1: tick_lane<Thread1Step>(sl, valid, tick, stp, stt); break;
     case kClsThread2: tick_lane<Thread2Step>(sl, valid, tick, stp, stt); break;
     case kClsSparse4: tick_lane<SparseStep<4>>(sl, valid, tick, stp, stt); break;

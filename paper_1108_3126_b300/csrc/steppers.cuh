@@ -69,6 +69,27 @@ struct MemoStep {
     __device__ __forceinline__ void restore(const uint32_t* p) { st = p[0]; }
 };
 
+// The same cache read from global memory with one byte per entry (state
+// ids < 256): a quarter of the footprint, so the tables of many expressions
+// stay in L2.  st = state id * 256.
+struct MemoStep8 {
+    const uint8_t* T;
+    const uint8_t* acc;
+    uint32_t st;
+    __device__ void bind_global(const DevTables& t) {
+        T = t.memo_T8;
+        acc = t.memo_acc;
+        st = t.memo_start;
+    }
+    __device__ __forceinline__ void step(uint32_t c) { st = (uint32_t)__ldg(T + st + c) << 8; }
+    __device__ __forceinline__ bool dead() const { return st == 0; }
+    __device__ __forceinline__ bool accept() const { return acc[st >> 8] != 0; }
+    __device__ __forceinline__ void kill() { st = 0; }
+    __device__ __forceinline__ void set_state(uint32_t s) { st = s * 256u; }
+    __device__ __forceinline__ void save(uint32_t* p) const { p[0] = st; }
+    __device__ __forceinline__ void restore(const uint32_t* p) { st = p[0]; }
+};
+
 struct Thread1Step {
     static constexpr int ROW_WORDS = 1;
     const uint2* desc;

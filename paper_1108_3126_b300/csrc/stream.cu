@@ -237,7 +237,7 @@ cudaError_t launch_span_t(const DevTables& t, const uint8_t* str, int64_t len, i
                           uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st) {
     size_t sm = S::smem_bytes(t);
     auto kern = k_span_tasks<S>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     const int block = 256;
@@ -258,7 +258,7 @@ cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str,
                             const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
     size_t sm = S::smem_bytes(t);
     auto kern = k_stream<S>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm);

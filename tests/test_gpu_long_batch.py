@@ -227,3 +227,94 @@ def test_batched_long_pairs_chunked_per_warp():
     got = out.cpu().numpy()
     want = np.array([oracle.o2(regs[rid[k]], strs[k]) for k in range(pk.n)], np.uint8)
     assert (got == want).all(), np.nonzero(got != want)[0][:10]
+
+
+def _counter_workload(seed):
+    """Expressions whose cache states permute under the input, so incoming
+    states never merge within a chunk (every prefix stage keeps several),
+    with strings 0-70000 bytes; plus random expressions."""
+    rng = np.random.default_rng(seed)
+    pats = [b"(aaa)*", b"(aaaaa|b)*", b"((ab)*c)*", b"(a(bb)*a|b)*", b"((aa|b)(aa|b)(aa|b))*",
+            b"(abc|bca|cab)*", b"(a|b)*a(a|b)(a|b)(a|b)"]
+    regs = [oracle.parse(p) for p in pats]
+    for i in range(12):
+        regs.append(synth.gen_regex([12, 40, 100][i % 3], 10, b"abc", synth.item_seed(0xF1, i), eps_loop_p=0.05))
+    strs, rid = [], []
+    for i, e in enumerate(regs):
+        for k in range(6):
+            L = int(rng.choice([int(rng.integers(0, 300)), int(rng.integers(2000, 9000)),
+                                int(rng.integers(9000, 70000))]))
+            if k % 2 == 0:
+                s = synth.gen_strings(e, 1, max(L - 64, 0), L, b"abc", synth.item_seed(0xF2 + i, k), p_lang=1.0)
+                w = s.get(0)
+            else:
+                w = bytes(rng.choice(np.frombuffer(b"abc", np.uint8), size=L).tolist())
+            strs.append(w)
+            rid.append(i)
+    order = rng.permutation(len(strs))
+    return regs, [strs[k] for k in order], [rid[k] for k in order]
+
+
+def test_batched_long_pairs_states_that_never_merge():
+    regs, strs, rid = _counter_workload(0xF0)
+    handles = [rx.Regex.from_nodes(nd) for nd in regs]
+    assert all(h.info()["memo_states"] > 0 for h in handles)
+    pk = synth.pack(strs)
+    d, o = dev(pk.data), dev(pk.offsets)
+    out = torch.full((pk.n,), 7, dtype=torch.uint8, device="cuda")
+    rx.match_batch([handles[i] for i in rid], d, o, out)
+    torch.cuda.synchronize()
+    want = np.array([oracle.o2(regs[rid[k]], strs[k]) for k in range(pk.n)], np.uint8)
+    got = out.cpu().numpy()
+    assert (got == want).all(), np.nonzero(got != want)[0][:10]
+    # (aaa)* on a^L: closed form
+    for k in range(pk.n):
+        if rid[k] == 0 and set(strs[k]) <= {ord("a")}:
+            assert got[k] == (len(strs[k]) % 3 == 0)
+
+
+def test_prepared_batch_graph_replay_recapture_and_autotune():
+    """rx_batch_*: replays of the captured graph, a new capture for new
+    buffers, and every autotuned launch shape, all equal to O2."""
+    regs, strs, rid = _counter_workload(0xF3)
+    for i in range(10):
+        alpha = [synth.LOWER, synth.ALL_BYTES][i % 2]
+        e = synth.gen_regex([20, 200][i % 2], 12, alpha, synth.item_seed(0xF4, i), eps_loop_p=0.05)
+        regs.append(e)
+        s = synth.gen_strings(e, 20, 0, 20000, alpha, synth.item_seed(0xF5, i), p_lang=0.6, log_len=True)
+        for k in range(s.n):
+            strs.append(s.get(k))
+            rid.append(len(regs) - 1)
+    # wide expressions (no cache): thread, sparse and warp classes in the mix
+    for pat in [b"(" + b"|".join(b"x" + bytes([97 + j % 26]) for j in range(150)) + b")*",
+                b"(" + b"|".join(bytes([97 + j % 26]) * 2 for j in range(20)) + b")*z"]:
+        regs.append(oracle.parse(pat))
+        s = synth.gen_strings(regs[-1], 30, 0, 3000, synth.LOWER, 0xF6 + len(regs), p_lang=0.7)
+        for k in range(s.n):
+            strs.append(s.get(k))
+            rid.append(len(regs) - 1)
+    handles = [rx.Regex.from_nodes(nd, 0, rx.COMPILE_NO_MEMO if len(nd) > 250 else 0) for nd in regs]
+    want = np.array([oracle.o2(regs[rid[k]], strs[k]) for k in range(len(strs))], np.uint8)
+    pk = synth.pack(strs)
+    d, o = dev(pk.data), dev(pk.offsets)
+    b = rx.Batch([handles[i] for i in rid])
+    outs = [torch.full((pk.n,), 7, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    for rep in range(3):
+        for out in outs:
+            out.fill_(9)
+            b.run(d, o, out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            assert (got == want).all(), (rep, np.nonzero(got != want)[0][:10])
+    t = b.autotune(d, o, outs[0])
+    assert t["block"] in (128, 256, 512) and t["gb_per_s"] > 0
+    assert (outs[0].cpu().numpy() == want).all()
+    outs[1].fill_(9)
+    b.run(d, o, outs[1])
+    torch.cuda.synchronize()
+    assert (outs[1].cpu().numpy() == want).all()
+    b.free()
+    # an empty prepared batch
+    e = rx.Batch([])
+    e.run(0, 0, 0)
+    e.free()
