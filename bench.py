@@ -45,10 +45,10 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
 # capture, keyed by a hash of that kernel's sources at capture time (null
-# when they have changed since).  k_stream<MemoPair>: 133.69 MB per launch on
-# the 262,144-string capture (136.81 MB algorithmic), scaled by algorithmic
-# bytes to the full 1,048,576-string launch (546.80 MB): 534.3 MB.
-TRAFFIC = {("k_stream<MemoPair>", "a880d27955c1a838"): 534.3e6}
+# when they have changed since).  k_stream<MemoPairP>: 133.33 MB per launch
+# on the 262,144-string capture (136.81 MB algorithmic), scaled by
+# algorithmic bytes to the full 1,048,576-string launch (546.80 MB): 532.9 MB.
+TRAFFIC = {("k_stream<MemoPairP>", "c8ad88ba8ae7efa2"): 532.9e6}
 
 
 def kernel_source_hash() -> str:
@@ -258,8 +258,9 @@ def run_streaming(args, world, rank, local):
 
     # the other kernel variants on the same batch (informational)
     variants = {}
-    for name, v, blk in ((("memo_pair", 1, 0), ("memo_single", 1, 257), ("thread", 2, 0), ("sparse", 3, 0),
-                          ("warp", 4, 0)) if not args.quick else ()):
+    for name, v, blk in ((("memo_pair", 1, 0), ("memo_pair_tma32x3", 1, 4),
+                          ("memo_pair_tma64x2", 1, 12), ("memo_pair_tma64x3", 1, 20), ("memo_single", 1, 257),
+                          ("thread", 2, 0), ("sparse", 3, 0), ("warp", 4, 0)) if not args.quick else ()):
         if not (info["variants"] >> v) & 1:
             continue
         reps = max(3, min(50, args.steps // 20))
@@ -315,7 +316,8 @@ def run_streaming(args, world, rank, local):
         return
     chosen_v = tuned["variant"] if tuned else (variant or (1 if info["memo_states"] else 2))
     chosen_b = tuned["block"] if tuned else 0
-    kname = {1: "k_stream<MemoPair>" if (info.get("pair", True) and not (chosen_b & 1)) else "k_stream<MemoS>",
+    kname = {1: ("k_stream<MemoS>" if (chosen_b & 1) or not info.get("pair", True) else
+                 "k_stream_tma<MemoPairP>" if chosen_b & 28 else "k_stream<MemoPairP>"),
              2: "k_stream<Thread1S|Thread2S>", 3: "k_thread<SparseStep>", 4: "k_warp"}[chosen_v]
     src_hash = kernel_source_hash()
     traffic = TRAFFIC.get((kname, src_hash))
@@ -337,6 +339,7 @@ def run_streaming(args, world, rank, local):
                 "d2h_bytes_per_step": n, "includes": "rx_compile_ast + rx_match_host (H2D, match, D2H) per step"},
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
+        "device_faults": rx.device_faults(),
         "clocks": clk,
         "cpu_baseline": cpu,
         "variants": variants,

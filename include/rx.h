@@ -240,6 +240,16 @@ rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings, const int
                         void* stream);
 
 /*
+ * rx_device_faults -- bounded device-side waits that gave up, counted on
+ * the current device since the last reset (the streaming kernel that stages
+ * input with bulk copies counts one per warp that stopped waiting for a
+ * stage; that warp's strings of the round are left unwritten).  0 in normal
+ * operation.  reset != 0 clears the counter after reading.  Synchronises
+ * the device.  The paper has no counterpart.
+ */
+int64_t rx_device_faults(int32_t reset);
+
+/*
  * rx_match_batch -- n (expression, string) pairs in one persistent launch
  * (async).  handles is a HOST array of n handles (pair i uses handles[i]);
  * strings/offsets/out as in rx_match.  Pairs are bucketed by variant and

@@ -86,6 +86,7 @@ SIGNATURES = {
     "rx_match_ex": ([P, SZ, P, P, P, P, ctypes.POINTER(_Opts)], I32),
     "rx_match_static": ([P, SZ, P, P, P, P], I32),
     "rx_match_host": ([P, SZ, P, P, P, P], I32),
+    "rx_device_faults": ([I32], I64),
     "rx_match_batch": ([P, SZ, P, P, P, P], I32),
     "rx_match_pairs": ([P, SZ, P, P, P, P], I32),
     "rx_batch_prepare": ([P, SZ, ctypes.POINTER(P)], I32),
@@ -244,6 +245,11 @@ def match_static(rx: Regex, strings, offsets, out, n: int | None = None, stream=
     if n is None:
         n = len(offsets) - 1
     _check(lib().rx_match_static(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream)))
+
+
+def device_faults(reset: bool = False) -> int:
+    """Bounded device waits that gave up since the last reset (0 normally)."""
+    return int(lib().rx_device_faults(1 if reset else 0))
 
 
 def match_host(rx: Regex, strings, offsets, out, n: int | None = None, stream=None):

@@ -86,7 +86,7 @@ static rx_status upload(rx_regex* h) {
     const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
     size_t o_sps = take(spW * 4 + 16), o_spB = take((size_t)256 * spW * 4 + 16),
            o_spF = take((size_t)C.nbits * spW * 4 + 16);
-    size_t o_bg = take(std::max<size_t>(C.bg_T.size(), 1) * 2);
+    size_t o_bgp = take(std::max<size_t>(C.bgp_T.size(), 1) * 2);
     size_t o_self = take(sizeof(DevTables));
     size_t total = off;
     std::vector<uint8_t> blob(total, 0);
@@ -105,7 +105,7 @@ static rx_status upload(rx_regex* h) {
     for (size_t i = 0; i < C.nodes.size(); i++)
         pn[i] = make_int4((int)C.nodes[i].kind | ((int)C.nodes[i].byte << 8), C.nodes[i].l, C.nodes[i].r, C.cont[i]);
     put(o_nd, pn.data(), pn.size() * sizeof(int4));
-    put(o_bg, C.bg_T.data(), C.bg_T.size() * 2);
+    put(o_bgp, C.bgp_T.data(), C.bgp_T.size() * 2);
     if (spW) {
         std::vector<uint32_t> ps(spW, 0u), pB((size_t)256 * spW, 0u), pF((size_t)C.nbits * spW, 0u);
         for (int k = 0; k < W; k++) ps[k] = C.start[k];
@@ -150,7 +150,7 @@ static rx_status upload(rx_regex* h) {
     t.memo_T8 = b + o_T8;
     t.memo_acc = b + o_acc;
     t.memo_start = C.memo_start;
-    t.bg_T = C.bg_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bg);
+    t.bgp_T = C.bgp_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bgp);
     t.bg_lo = C.bg_lo;
     t.variants = C.variants;
     t.nullable = C.nullable ? 1 : 0;
@@ -385,6 +385,11 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
     if (e != cudaSuccess) return cuda_fail(e, "rx_match launch");
     return RX_OK;
     RX_GUARD_END
+}
+
+int64_t rx_device_faults(int32_t reset) {
+    cudaDeviceSynchronize();
+    return (int64_t)rx::read_wait_faults(reset != 0);
 }
 
 rx_status rx_match(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,

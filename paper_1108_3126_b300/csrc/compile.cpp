@@ -472,8 +472,11 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
     // ---- 8b. two macro steps per lookup: when every label lies in one
     // aligned window of 32 byte values, entry 32*j + i of a state's pair row
     // is the state after reading byte lo+i then byte lo+j (two steps of the
-    // cache above); bytes outside the window use the single-byte row.
+    // cache above); bytes outside the window use the single-byte row.  The
+    // device gets these rows rearranged into planes of 8 states (see
+    // DevTables::bgp_T), where a lookup is one add to the state's address.
     C.bg_T.clear();
+    C.bgp_T.clear();
     C.bg_lo = -1;
     if (C.memo_K > 0 && C.memo_K <= kPairMaxStates && m > 0) {
         int lo = 256, hi = -1;
@@ -494,6 +497,17 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
                     for (int j = 0; j < 32; j++) row[j * 32 + i] = (uint16_t)(C.memo_T[(size_t)mid * 256 + w0 + j] / 256u);
                 }
                 for (int c = 0; c < 256; c++) row[1024 + c] = (uint16_t)(C.memo_T[(size_t)k * 256 + c] / 256u);
+            }
+            // planes of 8 states (40 rows x 256 entries each)
+            auto code = [](uint32_t s) { return (uint16_t)((s >> 3) * 320u + (s & 7u)); };
+            const int planes = (K + 7) / 8;
+            C.bgp_T.assign((size_t)planes * 10240, 0);
+            for (int k = 0; k < K; k++) {
+                uint16_t* P = &C.bgp_T[(size_t)(k >> 3) * 10240 + (size_t)(k & 7) * 32];
+                const uint16_t* row = &C.bg_T[(size_t)k * 1280];
+                for (int j = 0; j < 32; j++)
+                    for (int i = 0; i < 32; i++) P[j * 256 + i] = code(row[j * 32 + i]);
+                for (int c = 0; c < 256; c++) P[(32 + (c >> 5)) * 256 + (c & 31)] = code(row[1024 + c]);
             }
         }
     }

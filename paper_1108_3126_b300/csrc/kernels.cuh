@@ -108,6 +108,10 @@ void prof_enable(bool on);
 cudaError_t paper_match_one(const DevTables& t, const uint8_t* str, int64_t len, int* scratch, int* hflags,
                             uint8_t* out_host, cudaStream_t st);
 
+// Waits of the bulk-copy streaming kernel that gave up (a device-wide
+// counter; optionally cleared).
+unsigned read_wait_faults(bool reset);
+
 // Device properties cached per device.
 int sm_count();
 

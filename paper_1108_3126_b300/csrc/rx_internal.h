@@ -48,9 +48,14 @@ struct DevTables {
     const uint8_t* memo_T8;  // [K*256] next state id (the same table, one byte per entry, for global reads)
     const uint8_t* memo_acc; // [K] 1 iff the state's set holds null
     uint32_t memo_start;     // start state * 256
-    // two-byte cache: for labels inside one 32-value window [bg_lo, bg_lo+32),
-    // per state a row of 1024 pair successors then 256 byte successors (u16 ids)
-    const uint16_t* bg_T;    // [K * 1280], 0 = unavailable
+    // two-byte cache, for labels inside one 32-value window [bg_lo, bg_lo+32),
+    // in planes of 8 states: plane p = s / 8 holds
+    // 40 rows of 512 bytes; row j < 32 holds, for slot q = s % 8 at byte
+    // 64q, the 32 successors after bytes (lo+i, lo+j); rows 32..39 hold the
+    // 256 byte successors (c at row 32 + c/32, entry c % 32).  Entries are
+    // the successor's shared-memory offset / 64 (plane * 320 + slot), so a
+    // lookup is (state offset) + 2 * (b0 & 31 | (b1 & 31) << 8)
+    const uint16_t* bgp_T;   // [ceil(K/8) * 10240], 0 = unavailable
     int32_t bg_lo;
     uint32_t variants;       // bit v: rx_variant v can run
     int32_t nullable;
@@ -84,8 +89,11 @@ struct Compiled {
     std::vector<uint32_t> memo_T;  // K*256
     std::vector<uint8_t> memo_acc;
     uint32_t memo_start = 0;
-    // two-byte cache (see DevTables::bg_T)
+    // two-byte cache: per state a row of 1024 pair successors (entry
+    // 32*j + i after bytes lo+i, lo+j) then 256 byte successors, u16 ids
+    // (host only; the device gets the planes below)
     std::vector<uint16_t> bg_T;
+    std::vector<uint16_t> bgp_T;  // planes layout (see DevTables::bgp_T)
     int bg_lo = -1;
     uint32_t variants = 0;
 };

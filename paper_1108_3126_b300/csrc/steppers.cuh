@@ -355,39 +355,40 @@ __device__ __forceinline__ uint32_t lds16(uint32_t a) {
     return v;
 }
 
-// two macro steps per lookup (see DevTables::bg_T): st = shared address of
-// the current state's row; the row holds 1024 pair successors (index
-// 32*second + first, bytes relative to the window) then 256 byte successors,
-// as u16 state ids; a row is 2560 bytes.
-struct MemoPair {
+// The two-byte cache in planes (see DevTables::bgp_T): st = shared address
+// of the state's slot in its plane; a pair lookup adds 2 * (x & 0x1F1F) to
+// it and the entry read back is the successor's offset / 64.
+struct MemoPairP {
     static constexpr bool kPairs = true;
-    static constexpr uint32_t ROW = 2560;
+    static constexpr uint32_t PLANE = 20480;  // bytes per 8 states
     uint32_t st, base, acc, win;
-    static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * ROW) + align16(t.memo_K); }
+    __host__ __device__ static size_t planes(const DevTables& t) { return (size_t)(t.memo_K + 7) / 8; }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) { return planes(t) * PLANE + align16(t.memo_K); }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
-        copy_to_smem(sm, t.bg_T, (size_t)t.memo_K * ROW);
-        copy_to_smem(sm + align16((size_t)t.memo_K * ROW), t.memo_acc, t.memo_K);
+        copy_to_smem(sm, t.bgp_T, planes(t) * PLANE);
+        copy_to_smem(sm + planes(t) * PLANE, t.memo_acc, t.memo_K);
     }
     __device__ void bind(const DevTables& t, uint8_t* sm) {
         base = smem_addr(sm);
-        acc = base + (uint32_t)align16((size_t)t.memo_K * ROW);
-        st = base + (t.memo_start >> 8) * ROW;
+        acc = base + (uint32_t)(planes(t) * PLANE);
+        set_state(t.memo_start >> 8);
         win = (uint32_t)t.bg_lo * 0x01010101u;
     }
-    __device__ __forceinline__ void step(uint32_t c) { st = base + lds16(st + 2048u + c * 2u) * ROW; }
-    // x: first byte in bits 0-7, second in bits 8-15 (both inside the window)
-    __device__ __forceinline__ void step2(uint32_t x) {
-        uint32_t t = x & 0x1F1Fu;
-        uint32_t idx = ((t >> 3) & 0xFFE0u) | (t & ~0xFFE0u);
-        st = base + lds16(st + idx * 2u) * ROW;
+    __device__ __forceinline__ void step(uint32_t c) {
+        st = base + lds16(st + 16384u + (c >> 5) * 512u + (c & 31u) * 2u) * 64u;
     }
-    // every byte of w inside the window
+    // x: first byte in bits 0-7, second in bits 8-15 (both inside the
+    // window); higher bits are ignored
+    __device__ __forceinline__ void step2(uint32_t x) { st = base + lds16(st + (x & 0x1F1Fu) * 2u) * 64u; }
     __device__ __forceinline__ uint32_t out_of_window(uint32_t w) const { return (w ^ win) & 0xE0E0E0E0u; }
     __device__ __forceinline__ bool dead() const { return st == base; }
-    __device__ __forceinline__ bool accept() const { return lds8(acc + (st - base) / ROW) != 0; }
+    __device__ __forceinline__ uint32_t state_id() const {
+        const uint32_t o = st - base;
+        return (o / PLANE) * 8u + ((o >> 6) & 7u);
+    }
+    __device__ __forceinline__ bool accept() const { return lds8(acc + state_id()) != 0; }
     __device__ __forceinline__ void kill() { st = base; }
-    __device__ __forceinline__ void set_state(uint32_t s) { st = base + s * ROW; }
-    __device__ __forceinline__ uint32_t state_id() const { return (st - base) / ROW; }
+    __device__ __forceinline__ void set_state(uint32_t s) { st = base + (s >> 3) * PLANE + (s & 7u) * 64u; }
 };
 
 // register bitset (one word): desc[c] = {shift | mask << 8, shared address

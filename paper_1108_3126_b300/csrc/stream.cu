@@ -163,6 +163,179 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_stream(const DevTables t, 
     }
 }
 
+// ------------------------------------------------------------------ TMA
+// The same rounds with the input staged into shared memory by the bulk-copy
+// (TMA) engine instead of per-lane global loads: for every 32*CH-byte step
+// of a round each lane asks for its next CH bytes (whole aligned 32-byte
+// blocks) with one cp.async.bulk into its slot of a stage; the warp's
+// stage completes on an mbarrier (lane 0 arrives with the warp's byte
+// total, the copies complete the transaction count); lanes then read their
+// slot with 128-bit shared loads.  NST stages per warp keep NST-1 steps in
+// flight.  A lane slot is CH + 16 bytes, so the 32 lanes' 128-bit reads
+// cover all 32 banks in four wavefronts.  Every wait is bounded: a warp
+// whose stage does not complete counts a fault (rx_device_faults), waits a
+// bounded time for its copies in flight and leaves.
+
+__device__ unsigned g_wait_faults;
+
+// each try_wait suspends for at most about kWaitHintNs; a wait gives up
+// after kWaitSpins of them (about 0.2 s)
+constexpr uint32_t kWaitSpins = 10000;
+constexpr uint32_t kWaitHintNs = 20000;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kWaitHintNs)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of `bar` with this parity
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitSpins; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, uint64_t src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ Blk32 lds_blk(uint32_t a) {
+    Blk32 r;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.a.x), "=r"(r.a.y), "=r"(r.a.z), "=r"(r.a.w)
+                 : "r"(a));
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.b.x), "=r"(r.b.y), "=r"(r.b.z), "=r"(r.b.w)
+                 : "r"(a + 16));
+    return r;
+}
+
+template <int CH, int NST>
+struct TmaLayout {
+    static constexpr int kSlot = CH + 16;
+    static constexpr size_t per_warp() { return (size_t)NST * 32 * kSlot + (size_t)NST * 8; }
+};
+
+template <class S, int CH, int NST>
+__global__ void __launch_bounds__(1024, 1) k_stream_tma(const DevTables t, const uint8_t* __restrict__ str,
+                                                     const int64_t* __restrict__ off,
+                                                     const uint32_t* __restrict__ perm, long long n,
+                                                     uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
+    static_assert(CH % 32 == 0, "steps of whole 32-byte blocks");
+    using Lay = TmaLayout<CH, NST>;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t tab = align16(S::smem_bytes(t));
+    uint8_t* stg = smem + tab + (size_t)wid * NST * 32 * Lay::kSlot;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tab + (size_t)nw * NST * 32 * Lay::kSlot) + wid * NST;
+    S::load(t, smem);
+    if (lane == 0)
+        for (int q = 0; q < NST; q++) mbar_init(smem_u32(bars + q), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    S proto;
+    proto.bind(t, smem);
+    const uint32_t slot0 = smem_u32(stg) + lane * Lay::kSlot;
+    const uint32_t bar0 = smem_u32(bars);
+    uint32_t parity = 0;  // bit q: the parity of the next phase of stage q
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    const long long nround = (n + 31) / 32;
+    bool failed = false;
+    for (;;) {
+        unsigned r = 0;
+        if (lane == 0) r = atomicAdd(queue, 1u);
+        r = __shfl_sync(FULL, r, 0);
+        if ((long long)r >= nround) break;
+        const long long k = (long long)r * 32 + lane;
+        const bool valid = k < n;
+        const long long id = valid ? (perm ? (long long)perm[k] : k) : 0;
+        uint64_t s = base, e = base;
+        if (valid) {
+            s += (uint64_t)off[id];
+            e += (uint64_t)off[id + 1];
+        }
+        S st = proto;
+        bool active = valid && s < e;
+        if (valid && !active) out[id] = st.accept();
+        if (!active) st.kill();
+        const uint64_t blk0 = s & ~uint64_t(31);
+        // steps of CH bytes this lane needs, and the round's
+        const uint32_t my_steps = active ? (uint32_t)((e - blk0 + CH - 1) / CH) : 0u;
+        const uint32_t nsteps = __reduce_max_sync(FULL, my_steps);
+        // ask for step q of every lane that still reads into stage q % NST
+        auto issue = [&](uint32_t q) {
+            const uint64_t src = blk0 + (uint64_t)q * CH;
+            uint32_t bytes = 0;
+            if (active && src < e) {
+                const uint64_t end = (e + 31) & ~uint64_t(31);
+                bytes = (uint32_t)min((uint64_t)CH, end - src);
+            }
+            const uint32_t total = __reduce_add_sync(FULL, bytes);
+            const uint32_t bar = bar0 + (q % NST) * 8u;
+            if (lane == 0) mbar_arrive_expect(bar, total);
+            __syncwarp();
+            if (bytes) bulk_g2s(slot0 + (q % NST) * 32u * Lay::kSlot, src, bytes, bar);
+        };
+        uint32_t issued = 0;
+        for (; issued < nsteps && issued < (uint32_t)NST - 1u; issued++) issue(issued);
+        for (uint32_t q = 0; q < nsteps; q++) {
+            if (issued < nsteps) {
+                issue(issued);  // into the stage consumed at step q - 1
+                issued++;
+            }
+            const uint32_t sq = q % NST;
+            const bool ok = mbar_wait(bar0 + sq * 8u, (parity >> sq) & 1u);
+            parity ^= 1u << sq;
+            if (!__all_sync(FULL, ok)) {
+                failed = true;
+                break;
+            }
+            const uint32_t slot = slot0 + sq * 32u * Lay::kSlot;
+#pragma unroll
+            for (int b = 0; b < CH / 32; b++) {
+                const Blk32 v = lds_blk(slot + b * 32);
+                const uint64_t blk = blk0 + (uint64_t)q * CH + b * 32;
+                block32(st, v, valid_mask(blk, s, e, active));
+                if (active && (blk + 32 >= e || st.dead())) {
+                    out[id] = st.accept();
+                    st.kill();
+                    active = false;
+                }
+            }
+            // the reads of this stage are done before the next copy into it
+            __syncwarp();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (!__any_sync(FULL, active)) {
+                // drain the steps already asked for
+                for (uint32_t d = q + 1; d < issued; d++) {
+                    const uint32_t sd = d % NST;
+                    if (!__all_sync(FULL, mbar_wait(bar0 + sd * 8u, (parity >> sd) & 1u))) failed = true;
+                    parity ^= 1u << sd;
+                }
+                break;
+            }
+        }
+        if (failed) break;
+    }
+    if (failed) {
+        // bounded waits for any copy still in flight into this warp's stages
+        for (int q = 0; q < NST; q++) mbar_wait(bar0 + q * 8u, (parity >> q) & 1u);
+        if (lane == 0) atomicAdd(&g_wait_faults, 1u);
+    }
+}
+
 // Tasks of the chunked long-string mode: task i starts the cache of macro
 // steps in state task_state[i] at byte task_chunk[i] * C + P of the text and
 // runs to the end of that chunk; res[i] receives the final state id.  Tasks
@@ -273,15 +446,53 @@ cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str,
     return cudaGetLastError();
 }
 
+template <class S, int CH, int NST>
+cudaError_t launch_stream_tma_t(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
+                                const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st) {
+    const size_t tab = align16(S::smem_bytes(t));
+    const size_t per = TmaLayout<CH, NST>::per_warp();
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if ((size_t)optin <= tab + 4 * per) return cudaErrorInvalidConfiguration;
+    const int nw = (int)std::min<size_t>(32, ((size_t)optin - tab) / per);
+    const size_t sm = tab + (size_t)nw * per;
+    auto kern = k_stream_tma<S, CH, NST>;
+    e = allow_smem(kern, sm);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nw * 32, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long rounds = (n + 31) / 32;
+    long long grid = std::min<long long>((rounds + nw - 1) / nw, (long long)per_sm * sm_count());
+    {
+        ProfScope ps(st);
+        kern<<<(unsigned)std::max<long long>(grid, 1), nw * 32, sm, st>>>(t, str, off, perm, n, out, queue);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-bool stream_pairs(const DevTables& t) { return t.bg_T != nullptr; }
+bool stream_pairs(const DevTables& t) { return t.bgp_T != nullptr; }
+
+unsigned read_wait_faults(bool reset) {
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_wait_faults, sizeof(v));
+    if (reset) {
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(g_wait_faults, &z, sizeof(z));
+    }
+    return v;
+}
 
 cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
                               const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
                               uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st) {
-    if (t.bg_T)
-        return launch_span_t<MemoPair>(t, str, len, C, P, task_chunk, task_state, ntask_p, res, queue, max_tasks, st);
+    if (t.bgp_T)
+        return launch_span_t<MemoPairP>(t, str, len, C, P, task_chunk, task_state, ntask_p, res, queue, max_tasks,
+                                        st);
     return launch_span_t<MemoS>(t, str, len, C, P, task_chunk, task_state, ntask_p, res, queue, max_tasks, st);
 }
 
@@ -291,18 +502,28 @@ bool stream_supported(const DevTables& t, int variant) {
 
 cudaError_t launch_stream(const DevTables& t, int variant, long long n, const uint8_t* str, const int64_t* off,
                           const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
-    // an odd block request (e.g. 257) asks for the single-byte memo kernel
-    const int block_req = block;
-    const int single = block & 1;
-    block &= ~1;
+    // the low bits of a block request choose the memo kernel: bit 0 the
+    // single-byte lookup (else two bytes per lookup), bits 2-4 input staged
+    // by the bulk-copy engine (4: 32-byte steps x 3 stages, 12: 64 x 2,
+    // 20: 64 x 3)
+    const int block_req = block & ~31;
+    const int single = block & 1, tma = block & 28;
+    block &= ~31;
     block = (block == 128 || block == 64 || block == 512) ? block : STREAM_BLOCK;
-    block |= single;
     if (variant == RX_VARIANT_MEMO) {
+        if (t.bgp_T && !single && tma) {
+            cudaError_t e = cudaErrorInvalidConfiguration;
+            if (tma == 4) e = launch_stream_tma_t<MemoPairP, 32, 3>(t, n, str, off, perm, out, queue, st);
+            if (tma == 12) e = launch_stream_tma_t<MemoPairP, 64, 2>(t, n, str, off, perm, out, queue, st);
+            if (tma == 20) e = launch_stream_tma_t<MemoPairP, 64, 3>(t, n, str, off, perm, out, queue, st);
+            if (e != cudaErrorInvalidConfiguration) return e;
+            cudaGetLastError();  // tables too large to stage beside: the plain kernel below
+        }
         // 512 threads: the autotuner's measured choice for the two-byte
         // kernel on the streaming workload (about 5% over 256)
-        if (t.bg_T && !(block & 1))
-            return launch_stream_t<MemoPair>(t, n, str, off, perm, out, queue, block_req == 0 ? 512 : block, st);
-        return launch_stream_t<MemoS>(t, n, str, off, perm, out, queue, block & ~1, st);
+        const int pb = block_req == 0 ? 512 : block;
+        if (t.bgp_T && !single) return launch_stream_t<MemoPairP>(t, n, str, off, perm, out, queue, pb, st);
+        return launch_stream_t<MemoS>(t, n, str, off, perm, out, queue, block, st);
     }
     if (t.W == 1) return launch_stream_t<Thread1S>(t, n, str, off, perm, out, queue, block & ~1, st);
     return launch_stream_t<Thread2S>(t, n, str, off, perm, out, queue, block & ~1, st);

@@ -49,7 +49,7 @@ def test_small_config_all_variants_vs_o1_o2():
     assert rx.VARIANT_MEMO in vs and rx.VARIANT_WARP in vs
     for v in [0] + vs:
         for sort in (0, 1, 2, 3):
-            for block in ((0, 257, 128, 512) if v == rx.VARIANT_MEMO else (0,)):
+            for block in ((0, 257, 128, 512, 130, 4, 12, 20) if v == rx.VARIANT_MEMO else (0,)):
                 got = run(r, w.strings, v, sort, block)
                 assert (got == want2).all(), (v, sort, block, np.nonzero(got != want2)[0][:10])
 
@@ -61,7 +61,7 @@ def test_streaming_config_reduced_vs_o2(seed):
     want = oracle.o2_batch(nodes, w.strings.data, w.strings.offsets)
     r = rx.Regex.from_nodes(nodes)
     for v in [0] + variants_of(r):
-        for block in ((0, 257) if v == rx.VARIANT_MEMO else (0,)):
+        for block in ((0, 257, 4, 12, 20) if v == rx.VARIANT_MEMO else (0,)):
             got = run(r, w.strings, v, block=block)
             assert (got == want).all(), (v, block, np.nonzero(got != want)[0][:10])
     # a share of both verdicts, and language samples accepted
@@ -84,6 +84,12 @@ def test_streaming_config_full_size_sampled():
     # every variant agrees with the default on the whole batch
     for v in variants_of(r):
         assert (run(r, w.strings, v) == got).all(), v
+    # and the kernels that stage the input with bulk copies, with no wait
+    # that gave up
+    rx.device_faults(reset=True)
+    for block in (4, 12, 20):
+        assert (run(r, w.strings, rx.VARIANT_MEMO, block=block) == got).all(), block
+    assert rx.device_faults() == 0
 
 
 @pytest.mark.parametrize("seed", range(3))
@@ -223,7 +229,8 @@ def test_pair_kernel_fallback_outside_the_byte_window():
                 data[pos] = rng.choice([0x00, 0x41, 0x5F, 0x80, 0x7B, 0xFF], size=len(pos))
         mixed = synth.Strings(data, s.offsets, s.kind, 0)
         want = oracle.o2_batch(e, data, s.offsets)
-        for v, block in ((0, 0), (rx.VARIANT_MEMO, 0), (rx.VARIANT_MEMO, 257), (rx.VARIANT_THREAD, 0)):
+        for v, block in ((0, 0), (rx.VARIANT_MEMO, 0), (rx.VARIANT_MEMO, 257),
+                         (rx.VARIANT_MEMO, 4), (rx.VARIANT_MEMO, 12), (rx.VARIANT_MEMO, 20), (rx.VARIANT_THREAD, 0)):
             got = run(r, mixed, v, block=block)
             assert (got == want).all(), (i, v, block, np.nonzero(got != want)[0][:10])
         # and strings made only of out-of-window bytes
