@@ -45,19 +45,7 @@ __device__ uint32_t lane_memo_run(const uint8_t* __restrict__ T, uint32_t st, ui
     return st;
 }
 
-constexpr int kBmWords = (kMemoMaxStates + 31) / 32;
 constexpr int kStage0 = 4;  // bytes of the first prefix stage; each stage doubles
-
-// number of set bits of bm below bit v
-__device__ __forceinline__ uint32_t rank_below(const uint32_t (&bm)[kBmWords], uint32_t v) {
-    uint32_t r = 0;
-#pragma unroll
-    for (int w = 0; w < kBmWords; w++) {
-        const uint32_t x = (w < (int)(v >> 5)) ? bm[w] : (w == (int)(v >> 5) ? (bm[w] & ((1u << (v & 31)) - 1u)) : 0u);
-        r += __popc(x);
-    }
-    return r;
-}
 
 // one warp, one long pair: returns whether the pair matches (all lanes).
 // Lane l computes the transfer map of chunk l for every cache state.  The
@@ -93,9 +81,7 @@ __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8
         for (int i = 0; i < nd; i++) {
             const uint32_t v = lane_memo_run(T, (uint32_t)dv[i] * 256u, pos, end) >> 8;
             dv[i] = (uint8_t)v;
-#pragma unroll
-            for (int w = 0; w < kBmWords; w++)
-                if (w == (int)(v >> 5)) bm[w] |= 1u << (v & 31);
+            bm_set(bm, v);
         }
         for (int k = 0; k < K; k++) map[k] = (uint8_t)rank_below(bm, dv[map[k]]);
         int j = 0;

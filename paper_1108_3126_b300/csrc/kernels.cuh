@@ -76,9 +76,11 @@ rx_status collect_pairs(const rx_handle* handles, size_t n, const char* who, std
                         std::vector<uint32_t>& pair_tab, std::vector<uint8_t>& cls);
 
 // Spans of the chunked mode run from given cache states (stream.cu).
+// A task of chunk j starts at j * C + pstart[j] (pstart null: + P).
 cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
                               const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
-                              uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st);
+                              const uint16_t* pstart, uint16_t* res, unsigned* queue, long long max_tasks,
+                              cudaStream_t st);
 
 // Chunked single-string mode (long.cu).
 bool long_supported(const DevTables& t);

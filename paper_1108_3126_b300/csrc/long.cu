@@ -27,128 +27,218 @@ namespace {
 
 using namespace rx::dev;
 
-// Phase 1: one warp per (chunk, group of 32 incoming states); lanes =
-// incoming states; every lane reads the same bytes, the first P of the chunk.
-__global__ void __launch_bounds__(256) k_chunk_memo(const DevTables t, const uint8_t* __restrict__ str, int64_t len,
-                                                    int64_t C, int64_t P, long long J, int groups,
-                                                    uint16_t* __restrict__ maps) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    MemoStep::load(t, smem);
-    __syncthreads();
-    MemoStep proto;
-    proto.bind(t, smem);
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    const uint64_t base = reinterpret_cast<uint64_t>(str);
-    for (long long task = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < J * groups;
-         task += warps) {
-        long long j = task / groups;
-        int g = (int)(task % groups);
-        int s0 = g * 32 + lane;
-        MemoStep st = proto;
-        st.set_state(s0 < t.memo_K ? (uint32_t)s0 : 0u);
-        const int64_t lo = j * C;
-        uint64_t s = base + (uint64_t)lo, e = base + (uint64_t)min(min(lo + P, lo + C), len);
-        run_range_uniform(st, s, e);
-        if (s0 < t.memo_K) maps[j * t.memo_K + s0] = (uint16_t)(st.st >> 8);
+// Phase 1: one thread per chunk.  The K incoming cache states advance over
+// the first 4 bytes of the chunk; the states reached are deduplicated (a
+// bitmap of state ids) into a list of representatives, and each incoming
+// state records its representative.  The representatives then advance
+// through further stages (4, 8, 16, ... bytes, kMaxPrefix in all) until at
+// most one distinct live state is among them (the empty set, state 0, stays
+// empty at no cost) -- two states that meet stay together, since a macro
+// step is a function of the set (Def 5.2).  Each distinct live state left is
+// one task of phase 2 (the rest of the chunk from that state); the tasks of
+// a warp's 32 chunks are allotted with one atomic add.  Per chunk j:
+// slot[j*K + k] = task index (relative to toff[j]) of the state incoming
+// state k has reached, 0xFFFF if it is the empty set; toff[j] = first task;
+// pstart[j] = prefix bytes consumed.  The prefix is kept short because a
+// warp's 32 chunks go through it together.  Each thread keeps map[K]
+// (representative of each incoming state), dv[K] (the representatives'
+// states) and rk[K] (index of a state id in the current list) as bytes in
+// shared memory after the table, interleaved across the block's threads
+// (entry k of thread x at k * blockDim + x) so that a warp's accesses fall
+// in distinct banks.
+constexpr int kMaxPrefix = 128;
+
+// a set of cache state ids (< 192) in six registers
+struct IdSet {
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    __device__ __forceinline__ void add(uint32_t v) {
+        const uint32_t b = 1u << (v & 31), q = v >> 5;
+        w0 |= q == 0 ? b : 0u;
+        w1 |= q == 1 ? b : 0u;
+        w2 |= q == 2 ? b : 0u;
+        w3 |= q == 3 ? b : 0u;
+        w4 |= q == 4 ? b : 0u;
+        w5 |= q == 5 ? b : 0u;
     }
+    __device__ __forceinline__ uint32_t word(int q) const {
+        return q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : q == 3 ? w3 : q == 4 ? w4 : w5;
+    }
+    __device__ __forceinline__ int count() const {
+        return __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3) + __popc(w4) + __popc(w5);
+    }
+};
+static_assert(kMemoMaxStates <= 192, "IdSet holds 192 ids");
+
+// N macro steps over the bytes packed in b (byte q at bits 8*(q%4) of b[q/4])
+template <int N>
+__device__ __forceinline__ void step_bytes(MemoS& st, const uint32_t (&b)[4]) {
+#pragma unroll
+    for (int q = 0; q < N; q++) st.step((b[q >> 2] >> (8 * (q & 3))) & 0xffu);
 }
 
-// The distinct states the K incoming states reach after the prefix: per
-// chunk, slot[s] = rank of pre[s] among them, dlist[r] = the r-th, cnt.
-// One warp per chunk; a bitmap of states (K <= 192) per warp in shared memory.
-__global__ void __launch_bounds__(256) k_distinct(const uint16_t* __restrict__ pre, long long J, int K,
-                                                  uint16_t* __restrict__ slot, uint16_t* __restrict__ dlist,
-                                                  unsigned* __restrict__ cnt) {
-    __shared__ unsigned bm_all[8][8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned* bm = bm_all[wid];
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + wid; j < J; j += warps) {
-        if (lane < 8) bm[lane] = 0;
-        __syncwarp();
-        for (int s = lane; s < K; s += 32) {
-            unsigned v = pre[j * K + s];
-            atomicOr(&bm[v >> 5], 1u << (v & 31));
-        }
-        __syncwarp();
-        unsigned word = lane < 8 ? bm[lane] : 0u;
-        unsigned c = __popc(word), incl = c;
+// the state reached from `s` over the n (<= 16) bytes packed in b
+__device__ __forceinline__ uint32_t step_n(const MemoS& proto, uint32_t s, const uint32_t (&b)[4], int n) {
+    MemoS st = proto;
+    st.set_state(s);
+    if (n == 4) {
+        step_bytes<4>(st, b);
+    } else if (n == 8) {
+        step_bytes<8>(st, b);
+    } else if (n == 16) {
+        step_bytes<16>(st, b);
+    } else {
 #pragma unroll
-        for (int d = 1; d < 8; d <<= 1) {
-            unsigned x = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += x;
-        }
-        unsigned excl = incl - c;
-        unsigned total = __shfl_sync(0xffffffffu, incl, 7);
-        for (int s = lane; s < K; s += 32) {
-            unsigned v = pre[j * K + s];
-            unsigned w = v >> 5;
-            // rank = number of distinct states below v
-            unsigned base_w = 0;
-            for (unsigned q = 0; q < w; q++) base_w += __popc(bm[q]);
-            slot[j * K + s] = (uint16_t)(base_w + __popc(bm[w] & ((1u << (v & 31)) - 1u)));
-        }
-        if (lane < 8) {
-            unsigned r = excl;
-            unsigned x = word;
-            while (x) {
-                int b = __ffs(x) - 1;
-                x &= x - 1;
-                dlist[j * K + r++] = (uint16_t)(lane * 32 + b);
+        for (int q = 0; q < 16; q++)
+            if (q < n) st.step((b[q >> 2] >> (8 * (q & 3))) & 0xffu);
+    }
+    return st.state_id();
+}
+
+// the next n (<= 16) bytes at p, packed
+__device__ __forceinline__ void load_bytes(const uint8_t* p, int n, uint32_t (&b)[4]) {
+    b[0] = b[1] = b[2] = b[3] = 0u;
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+        if (i < n) b[i >> 2] |= (uint32_t)__ldg(p + i) << (8 * (i & 3));
+}
+
+__global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const uint8_t* __restrict__ str, int64_t len,
+                                                     int64_t C, long long J, uint16_t* __restrict__ slot,
+                                                     uint16_t* __restrict__ pstart, unsigned* __restrict__ toff,
+                                                     uint32_t* __restrict__ task_chunk,
+                                                     uint16_t* __restrict__ task_state,
+                                                     unsigned* __restrict__ ntask) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    MemoS::load(t, smem);
+    __syncthreads();
+    MemoS proto;
+    proto.bind(t, smem);
+    const int K = t.memo_K;
+    const int nt = blockDim.x, lane = threadIdx.x & 31;
+    uint8_t* map = smem + align16(MemoS::smem_bytes(t)) + threadIdx.x;
+    uint8_t* dv = map + (size_t)K * nt;
+    uint8_t* rk = dv + (size_t)K * nt;
+    // warp-uniform loop over groups of 32 chunks
+    const long long wstride = (long long)gridDim.x * blockDim.x;
+    for (long long j0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < J; j0 += wstride) {
+        const long long j = j0 + lane;
+        const bool valid = j < J;
+        int nr = 0, nl = 0;
+        int64_t cs = 0, pos = 0;
+        IdSet fin;  // the distinct live states at the end of the prefix
+        if (valid) {
+            cs = j * C;
+            const int64_t pe = min(cs + kMaxPrefix, min(cs + C, len));
+            // first stage: every incoming state
+            const int n1 = (int)min((int64_t)4, pe - cs);
+            uint32_t b[4];
+            load_bytes(str + cs, n1, b);
+            IdSet seen;
+            for (int k = 0; k < K; k++) {
+                const uint32_t v = n1 > 0 ? step_n(proto, (uint32_t)k, b, n1) : (uint32_t)k;
+                map[k * nt] = (uint8_t)v;
+                seen.add(v);
+            }
+            // representatives: the distinct states, in id order
+#pragma unroll
+            for (int w = 0; w < 6; w++) {
+                uint32_t x = seen.word(w);
+                while (x) {
+                    const int id = w * 32 + __ffs(x) - 1;
+                    dv[nr * nt] = (uint8_t)id;
+                    rk[id * nt] = (uint8_t)nr;
+                    nr++;
+                    x &= x - 1;
+                }
+            }
+            for (int k = 0; k < K; k++) map[k * nt] = rk[map[k * nt] * nt];
+            fin = seen;
+            pos = cs + n1;
+            int live = seen.count() - (int)(seen.w0 & 1u);
+            int L = 4, stage = 1;
+            // further stages: the representatives only
+            while (live > 1 && pos < pe) {
+                const int n = (int)min((int64_t)L, pe - pos);
+                load_bytes(str + pos, n, b);
+                IdSet s2;
+                for (int i = 0; i < nr; i++) {
+                    const uint32_t v = step_n(proto, dv[i * nt], b, n);
+                    dv[i * nt] = (uint8_t)v;
+                    s2.add(v);
+                }
+                fin = s2;
+                live = s2.count() - (int)(s2.w0 & 1u);
+                pos += n;
+                stage++;
+                L = stage < 2 ? 4 : (stage == 2 ? 8 : 16);
+            }
+            // tasks: the distinct live states, numbered in id order
+#pragma unroll
+            for (int w = 0; w < 6; w++) {
+                uint32_t x = fin.word(w) & (w == 0 ? ~1u : ~0u);
+                while (x) {
+                    const int id = w * 32 + __ffs(x) - 1;
+                    rk[id * nt] = (uint8_t)nl;
+                    nl++;
+                    x &= x - 1;
+                }
             }
         }
-        if (lane == 0) cnt[j] = total;
-        __syncwarp();
-    }
-}
-
-// exclusive scan of the per-chunk task counts (one block); also clears the
-// work counter of the span kernel that follows
-__global__ void k_scan_cnt(const unsigned* __restrict__ cnt, long long J, unsigned* __restrict__ toff,
-                           unsigned* __restrict__ queue) {
-    __shared__ unsigned part[1024];
-    const int t = threadIdx.x;
-    if (t == 0) *queue = 0;
-    const long long per = (J + 1023) / 1024;
-    unsigned sum = 0;
-    for (long long i = t * per; i < min((long long)(t + 1) * per, J); i++) sum += cnt[i];
-    part[t] = sum;
-    __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {
-        unsigned v = (t >= d) ? part[t - d] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    unsigned run = part[t] - sum;
-    for (long long i = t * per; i < min((long long)(t + 1) * per, J); i++) {
-        toff[i] = run;
-        run += cnt[i];
-    }
-    if (t == 1023) toff[J] = part[1023];
-}
-
-__global__ void k_tasks(const unsigned* __restrict__ cnt, const unsigned* __restrict__ toff,
-                        const uint16_t* __restrict__ dlist, long long J, int K, uint32_t* __restrict__ task_chunk,
-                        uint16_t* __restrict__ task_state) {
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < J; j += warps) {
-        const unsigned c = cnt[j], o = toff[j];
-        for (unsigned r = lane; r < c; r += 32) {
-            task_chunk[o + r] = (uint32_t)j;
-            task_state[o + r] = dlist[j * K + r];
+        // tasks of the warp's chunks: one atomic add
+        int incl = nl;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += x;
+        }
+        unsigned base = 0;
+        if (lane == 31) base = atomicAdd(ntask, (unsigned)incl);
+        base = __shfl_sync(FULL, base, 31) + (unsigned)(incl - nl);
+        if (valid) {
+            for (int k = 0; k < K; k++) {
+                const uint32_t v = dv[map[k * nt] * nt];
+                slot[j * K + k] = v == 0 ? (uint16_t)0xFFFF : (uint16_t)rk[v * nt];
+            }
+            int i = 0;
+#pragma unroll
+            for (int w = 0; w < 6; w++) {
+                uint32_t x = fin.word(w) & (w == 0 ? ~1u : ~0u);
+                while (x) {
+                    task_chunk[base + i] = (uint32_t)j;
+                    task_state[base + i] = (uint16_t)(w * 32 + __ffs(x) - 1);
+                    i++;
+                    x &= x - 1;
+                }
+            }
+            toff[j] = base;
+            pstart[j] = (uint16_t)(pos - cs);
         }
     }
 }
 
-__global__ void k_final_maps(const uint16_t* __restrict__ slot, const unsigned* __restrict__ toff,
-                             const uint16_t* __restrict__ res, long long J, int K, uint16_t* __restrict__ maps) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < J * K;
-         i += (long long)gridDim.x * blockDim.x) {
-        long long j = i / K;
-        maps[i] = res[toff[j] + slot[i]];
+// first level of the composition, reading the chunk maps straight from the
+// tasks' results: map_j[k] = res[toff[j] + slot[j*K + k]] (0 for the empty
+// set); block b composes chunks [b*G, min((b+1)*G, J)) into out[b]
+__global__ void k_compose_first(const uint16_t* __restrict__ slot, const unsigned* __restrict__ toff,
+                                const uint16_t* __restrict__ res, long long J, int K, int G,
+                                uint16_t* __restrict__ out) {
+    extern __shared__ __align__(16) uint16_t sm16[];
+    const long long lo = (long long)blockIdx.x * G;
+    const long long hi = std::min<long long>(lo + G, J);
+    const int nmap = (int)(hi - lo);
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int c = threadIdx.x >> 5; c < nmap; c += warps) {
+        const unsigned o = toff[lo + c];
+        for (int k = lane; k < K; k += 32) {
+            const uint16_t r = slot[(lo + c) * K + k];
+            sm16[c * K + k] = r == 0xFFFF ? (uint16_t)0 : res[o + r];
+        }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < K; s += blockDim.x) {
+        int x = s;
+        for (int j = 0; j < nmap; j++) x = sm16[j * K + x];
+        out[(long long)blockIdx.x * K + s] = (uint16_t)x;
     }
 }
 
@@ -339,13 +429,10 @@ int64_t long_chunk_auto(const DevTables& t, int64_t len) {
     return (C + 15) & ~int64_t(15);
 }
 
-// prefix every incoming state runs before the distinct states are taken
-constexpr int64_t kLongPrefix = 128;
-
 struct MemoLongWs {
-    uint16_t *pre, *slot, *dlist, *task_state, *res, *maps_a, *maps_b;
+    uint16_t *pstart, *slot, *task_state, *res, *maps_a, *maps_b;
     uint32_t* task_chunk;
-    unsigned *cnt, *toff, *queue;
+    unsigned *toff, *ctr;  // ctr[0]: tasks allotted, ctr[1]: work counter of phase 2
 };
 
 static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
@@ -356,29 +443,25 @@ static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
         return w ? w + x : nullptr;
     };
     const size_t JK = (size_t)J * K;
-    uint8_t* p_pre = take(JK * 2);
+    uint8_t* p_pre = take((size_t)J * 2);
     uint8_t* p_slot = take(JK * 2);
-    uint8_t* p_dl = take(JK * 2);
     uint8_t* p_ts = take(JK * 2);
     uint8_t* p_res = take(JK * 2);
     uint8_t* p_ma = take(JK * 2);
     uint8_t* p_mb = take(JK * 2);
     uint8_t* p_tc = take(JK * 4);
-    uint8_t* p_cnt = take((size_t)J * 4);
-    uint8_t* p_toff = take((size_t)(J + 1) * 4);
+    uint8_t* p_toff = take((size_t)J * 4);
     uint8_t* p_q = take(256);
     if (o) {
-        o->pre = reinterpret_cast<uint16_t*>(p_pre);
+        o->pstart = reinterpret_cast<uint16_t*>(p_pre);
         o->slot = reinterpret_cast<uint16_t*>(p_slot);
-        o->dlist = reinterpret_cast<uint16_t*>(p_dl);
         o->task_state = reinterpret_cast<uint16_t*>(p_ts);
         o->res = reinterpret_cast<uint16_t*>(p_res);
         o->maps_a = reinterpret_cast<uint16_t*>(p_ma);
         o->maps_b = reinterpret_cast<uint16_t*>(p_mb);
         o->task_chunk = reinterpret_cast<uint32_t*>(p_tc);
-        o->cnt = reinterpret_cast<unsigned*>(p_cnt);
         o->toff = reinterpret_cast<unsigned*>(p_toff);
-        o->queue = reinterpret_cast<unsigned*>(p_q);
+        o->ctr = reinterpret_cast<unsigned*>(p_q);
     }
     return off;
 }
@@ -409,39 +492,38 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         }
         MemoLongWs L;
         memo_long_layout(J, K, w, &L);
-        const int64_t P = std::min<int64_t>(kLongPrefix, C);
-        // phase 1: every incoming state over the first P bytes of each chunk
-        int groups = (K + 31) / 32;
-        size_t sm = MemoStep::smem_bytes(t);
-        e = allow_smem(k_chunk_memo, sm);
+        // phase 1: staged prefixes, distinct states per chunk
+        const size_t tab = align16(MemoS::smem_bytes(t));
+        int dev = 0, optin = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return e;
+        int threads = (int)std::min<size_t>(256, ((size_t)optin - tab) / (3 * (size_t)K)) & ~31;
+        if (threads < 32) return cudaErrorInvalidConfiguration;
+        const size_t sm = tab + (size_t)threads * 3 * K;
+        e = allow_smem(k_chunk_stage, sm);
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_memo, 256, sm);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_stage, threads, sm);
         if (e != cudaSuccess) return e;
-        long long need = (J * groups + 7) / 8;
-        long long grid = std::min<long long>(need, (long long)std::max(per_sm, 1) * sm_count() * 4);
+        long long grid = std::min<long long>((J + threads - 1) / threads, (long long)std::max(per_sm, 1) * sm_count());
+        e = cudaMemsetAsync(L.ctr, 0, 256, st);
+        if (e != cudaSuccess) return e;
         {
             ProfScope ps(st);
-            k_chunk_memo<<<(unsigned)std::max<long long>(grid, 1), 256, sm, st>>>(t, str, len, C, P, J, groups, L.pre);
+            k_chunk_stage<<<(unsigned)std::max<long long>(grid, 1), threads, sm, st>>>(
+                t, str, len, C, J, L.slot, L.pstart, L.toff, L.task_chunk, L.task_state, L.ctr);
         }
-        // the distinct states reached, one task per (chunk, distinct state)
-        long long g2 = std::min<long long>((J + 7) / 8, (long long)sm_count() * 16);
-        k_distinct<<<(unsigned)std::max<long long>(g2, 1), 256, 0, st>>>(L.pre, J, K, L.slot, L.dlist, L.cnt);
-        k_scan_cnt<<<1, 1024, 0, st>>>(L.cnt, J, L.toff, L.queue);
-        k_tasks<<<(unsigned)std::max<long long>(g2, 1), 256, 0, st>>>(L.cnt, L.toff, L.dlist, J, K, L.task_chunk,
-                                                                     L.task_state);
-        prof_count(3);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        // phase 2: the distinct states over the rest of their chunks
-        e = launch_span_tasks(t, str, len, C, P, L.task_chunk, L.task_state, L.toff + J, L.res, L.queue, J * K, st);
+        // phase 2: the distinct live states over the rest of their chunks
+        e = launch_span_tasks(t, str, len, C, 0, L.task_chunk, L.task_state, L.ctr, L.pstart, L.res, L.ctr + 1,
+                              J * K, st);
         if (e != cudaSuccess) return e;
-        long long g3 = std::min<long long>((J * K + 255) / 256, (long long)sm_count() * 16);
-        k_final_maps<<<(unsigned)std::max<long long>(g3, 1), 256, 0, st>>>(L.slot, L.toff, L.res, J, K, L.maps_a);
+        // composition, left to right; the first level gathers the chunk maps
+        const int G = std::max(2, std::min(512, (48 * 1024) / (K * 2)));
+        long long cnt = (J + G - 1) / G;
+        k_compose_first<<<(unsigned)cnt, 256, (size_t)G * K * 2, st>>>(L.slot, L.toff, L.res, J, K, G, L.maps_a);
         prof_count(1);
-        // composition, left to right
-        int G = std::max(2, std::min(512, (48 * 1024) / (K * 2)));
-        long long cnt = J;
         uint16_t* cur = L.maps_a;
         uint16_t* nxt = L.maps_b;
         while (cnt > 1) {

@@ -469,6 +469,7 @@ rx_status rx_serve_submit(rx_server* s, rx_handle h, const uint8_t* bytes, int64
         r->dptr = s->cfg.device_payload ? bytes : nullptr;
         if (!s->cfg.device_payload && len > 0) r->host.assign(bytes, bytes + len);
         r->t_submit = now_ns();
+        uint64_t tk = 0;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             if ((int64_t)s->pending.size() >= s->cfg.queue_capacity) {
@@ -476,13 +477,14 @@ rx_status rx_serve_submit(rx_server* s, rx_handle h, const uint8_t* bytes, int64
                 set_error("rx_serve_submit: queue full");
                 return RX_ERR_BUSY;
             }
-            r->ticket = s->next_ticket++;
+            tk = r->ticket = s->next_ticket++;
             if (s->submitted == 0) s->t_first = r->t_submit;
             s->submitted++;
             s->pending.push_back(r);
+            // from here on the worker owns r (it may complete and free it at once)
         }
         s->cv_work.notify_one();
-        if (ticket) *ticket = r->ticket;
+        if (ticket) *ticket = tk;
         return RX_OK;
     } catch (...) {
         set_error("rx_serve_submit: host allocation failed");

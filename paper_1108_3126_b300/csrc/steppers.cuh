@@ -45,7 +45,9 @@ struct MemoStep {
     const uint32_t* T;
     const uint8_t* acc;
     uint32_t st;
-    static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * 1024) + align16(t.memo_K); }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) {
+        return align16((size_t)t.memo_K * 1024) + align16(t.memo_K);
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
         copy_to_smem(sm, t.memo_T, (size_t)t.memo_K * 1024);
         copy_to_smem(sm + align16((size_t)t.memo_K * 1024), t.memo_acc, t.memo_K);
@@ -90,12 +92,32 @@ struct MemoStep8 {
     __device__ __forceinline__ void restore(const uint32_t* p) { st = p[0]; }
 };
 
+// Bitmaps of cache state ids (< 192) for deduplicating states: the rank of
+// a state (number of set ids below it) is its index in the sorted list.
+constexpr int kBmWords = (kMemoMaxStates + 31) / 32;
+__device__ __forceinline__ uint32_t rank_below(const uint32_t (&bm)[kBmWords], uint32_t v) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int w = 0; w < kBmWords; w++) {
+        const uint32_t x = (w < (int)(v >> 5)) ? bm[w] : (w == (int)(v >> 5) ? (bm[w] & ((1u << (v & 31)) - 1u)) : 0u);
+        r += __popc(x);
+    }
+    return r;
+}
+__device__ __forceinline__ void bm_set(uint32_t (&bm)[kBmWords], uint32_t v) {
+#pragma unroll
+    for (int w = 0; w < kBmWords; w++)
+        if (w == (int)(v >> 5)) bm[w] |= 1u << (v & 31);
+}
+
 struct Thread1Step {
     static constexpr int ROW_WORDS = 1;
     const uint2* desc;
     const uint32_t* tt;
     uint32_t F, nb;
-    static size_t smem_bytes(const DevTables& t) { return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4); }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) {
+        return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4);
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
         copy_to_smem(sm, t.gl_desc, 256 * sizeof(uint2));
         copy_to_smem(sm + 256 * sizeof(uint2), t.gl_tt, (size_t)t.gl_words * 4);
@@ -131,7 +153,9 @@ struct Thread2Step {
     const uint2* desc;
     const uint2* tt;
     uint32_t F0, F1, nb;
-    static size_t smem_bytes(const DevTables& t) { return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4); }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) {
+        return 256 * sizeof(uint2) + align16((size_t)t.gl_words * 4);
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
         copy_to_smem(sm, t.gl_desc, 256 * sizeof(uint2));
         copy_to_smem(sm + 256 * sizeof(uint2), t.gl_tt, (size_t)t.gl_words * 4);
@@ -185,7 +209,9 @@ struct SparseStep {
     const uint32_t* follow;
     uint32_t F[W];
     uint32_t nb;
-    static size_t smem_bytes(const DevTables& t) { return (size_t)256 * W * 4 + align16((size_t)t.nbits * W * 4); }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) {
+        return (size_t)256 * W * 4 + align16((size_t)t.nbits * W * 4);
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
         copy_to_smem(sm, t.sp_B, (size_t)256 * W * 4);
         copy_to_smem(sm + (size_t)256 * W * 4, t.sp_follow, (size_t)t.nbits * W * 4);
@@ -329,7 +355,9 @@ __device__ __forceinline__ uint32_t byte_k(uint32_t w, int k) { return __byte_pe
 // 256 entries; each entry is the shared address of the successor's row.
 struct MemoS {
     uint32_t st, base, acc;
-    static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * 1024) + align16(t.memo_K); }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) {
+        return align16((size_t)t.memo_K * 1024) + align16(t.memo_K);
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
         uint32_t b = smem_addr(sm);
         uint32_t* T = reinterpret_cast<uint32_t*>(sm);
@@ -395,7 +423,9 @@ struct MemoPairP {
 // of the byte's subset table}; entry x of that table is the new set.
 struct Thread1S {
     uint32_t F, nb, desc;
-    static size_t smem_bytes(const DevTables& t) { return 256 * 8 + align16((size_t)t.gl_words * 4); }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) {
+        return 256 * 8 + align16((size_t)t.gl_words * 4);
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
         uint32_t tt = smem_addr(sm) + 256 * 8;
         uint2* d = reinterpret_cast<uint2*>(sm);
@@ -422,7 +452,9 @@ struct Thread1S {
 
 struct Thread2S {
     uint32_t F0, F1, nb, desc;
-    static size_t smem_bytes(const DevTables& t) { return 256 * 8 + align16((size_t)t.gl_words * 4); }
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) {
+        return 256 * 8 + align16((size_t)t.gl_words * 4);
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
         uint32_t tt = smem_addr(sm) + 256 * 8;
         uint2* d = reinterpret_cast<uint2*>(sm);

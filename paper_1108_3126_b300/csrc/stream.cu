@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(1024, 1) k_stream_tma(const DevTables t, const
 }
 
 // Tasks of the chunked long-string mode: task i starts the cache of macro
-// steps in state task_state[i] at byte task_chunk[i] * C + P of the text and
+// steps in state task_state[i] at byte task_chunk[i] * C + pstart[chunk] of the text and
 // runs to the end of that chunk; res[i] receives the final state id.  Tasks
 // come chunk by chunk, so the 32 lanes of a round cover equal-length spans.
 template <class S>
@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_span_tasks(const DevTables
                                                                const uint32_t* __restrict__ task_chunk,
                                                                const uint16_t* __restrict__ task_state,
                                                                const unsigned* __restrict__ ntask_p,
+                                                               const uint16_t* __restrict__ pstart,
                                                                uint16_t* __restrict__ res,
                                                                unsigned* __restrict__ queue) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_span_tasks(const DevTables
         if (valid) {
             const int64_t j = task_chunk[k];
             const int64_t lo = j * C, hi = min(lo + C, len);
-            s += (uint64_t)min(lo + P, hi);
+            s += (uint64_t)min(lo + (pstart ? (int64_t)pstart[j] : P), hi);
             e += (uint64_t)hi;
             st.set_state(task_state[k]);
         }
@@ -407,7 +408,8 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_span_tasks(const DevTables
 template <class S>
 cudaError_t launch_span_t(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
                           const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
-                          uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st) {
+                          const uint16_t* pstart, uint16_t* res, unsigned* queue, long long max_tasks,
+                          cudaStream_t st) {
     size_t sm = S::smem_bytes(t);
     auto kern = k_span_tasks<S>;
     cudaError_t e = allow_smem(kern, sm);
@@ -421,7 +423,7 @@ cudaError_t launch_span_t(const DevTables& t, const uint8_t* str, int64_t len, i
     {
         ProfScope ps(st);
         kern<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, len, C, P, task_chunk, task_state,
-                                                                        ntask_p, res, queue);
+                                                                        ntask_p, pstart, res, queue);
     }
     return cudaGetLastError();
 }
@@ -489,11 +491,13 @@ unsigned read_wait_faults(bool reset) {
 
 cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
                               const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
-                              uint16_t* res, unsigned* queue, long long max_tasks, cudaStream_t st) {
+                              const uint16_t* pstart, uint16_t* res, unsigned* queue, long long max_tasks,
+                              cudaStream_t st) {
     if (t.bgp_T)
-        return launch_span_t<MemoPairP>(t, str, len, C, P, task_chunk, task_state, ntask_p, res, queue, max_tasks,
-                                        st);
-    return launch_span_t<MemoS>(t, str, len, C, P, task_chunk, task_state, ntask_p, res, queue, max_tasks, st);
+        return launch_span_t<MemoPairP>(t, str, len, C, P, task_chunk, task_state, ntask_p, pstart, res, queue,
+                                        max_tasks, st);
+    return launch_span_t<MemoS>(t, str, len, C, P, task_chunk, task_state, ntask_p, pstart, res, queue, max_tasks,
+                                st);
 }
 
 bool stream_supported(const DevTables& t, int variant) {
