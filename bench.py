@@ -250,7 +250,9 @@ def run_streaming(args, world, rank, local):
     clk = clocks.stop()
     ms = max_over_ranks(ms, world, dev)
     value = world * total_bytes / (ms * 1e-3) / 1e9
-    kernel_ms = kms / max(timed, 1)
+    # the two timed kernels of a step: phase 1 (k_chunk_stage) and phase 2
+    # (k_span_tasks); composition and launch gaps are the rest of the step
+    kernel_ms = kms / max(args.steps, 1)
     alg_bytes = total_bytes + 8 * (n + 1) + n
     peak, peak_kind = peaks()
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
@@ -466,7 +468,9 @@ def run_long(args, world, rank, local):
     torch.cuda.synchronize(dev)
     assert int(out.item()) == agree_prefix
     peak, _ = peaks()
-    kernel_ms = kms / max(timed, 1)
+    # the two timed kernels of a step: phase 1 (k_chunk_stage) and phase 2
+    # (k_span_tasks); composition and launch gaps are the rest of the step
+    kernel_ms = kms / max(args.steps, 1)
     line = {"metric": METRIC, "workload": "long", "value": round(n / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "dtype": "u8", "data": "synthetic",
@@ -475,9 +479,10 @@ def run_long(args, world, rank, local):
                        "accepted": chunked, "last_whole_sample_end": end},
             "sequential_gpu": {"bytes": pre, "ms": round(seq_ms, 2), "GB/s": round(pre / (seq_ms * 1e-3) / 1e9, 4)},
             "chunked_over_sequential": round((n / ms) / (pre / seq_ms), 1),
-            "roofline": {"bound": "hbm", "kernel": "k_chunk_memo", "kernel_ms": round(kernel_ms, 4),
+            "roofline": {"bound": "hbm", "kernel": "k_chunk_stage + k_span_tasks", "kernel_ms": round(kernel_ms, 4),
                          "achieved": round(n / (kernel_ms * 1e-3) / 1e9, 1), "peak": peak,
-                         "frac": round(n / (kernel_ms * 1e-3) / 1e9 / peak, 4)},
+                         "frac": round(n / (kernel_ms * 1e-3) / 1e9 / peak, 4),
+                         "step_frac": round(n / (ms * 1e-3) / 1e9 / peak, 4)},
             "gpu_launches_per_step": launches / args.steps}
     if rank == 0:
         print(json.dumps(line))
