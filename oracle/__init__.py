@@ -10,6 +10,9 @@ and Operational Semantics" (SOS 2011):
 
 * ``o1`` -- the big-step relation of Fig 2.1 as a least relation, memoised
   (``oracle.c``).
+* ``o1_search`` -- unanchored search (not in the paper): the earliest end j
+  of a substring w[i:j] that the expression matches, read off the same
+  memoised tables of Fig 2.1 (``oracle.c``).
 * ``o2`` / ``o2_trace`` -- the sequential lockstep machine of Def 6.2 /
   Fig 6.1 with psi of Def 6.1 (``oracle.c``).
 * ``cont`` -- Def 4.4 (``oracle.c``).
@@ -70,6 +73,10 @@ def _L():
         lib.or_o2_batch.restype = I
         lib.or_o1_batch.argtypes = [P, I, I, P, P, I64, P, I64, I]
         lib.or_o1_batch.restype = I
+        lib.or_o1_search.argtypes = [P, I, I, P, I64, I64]
+        lib.or_o1_search.restype = I64
+        lib.or_o1_search_batch.argtypes = [P, I, I, P, P, I64, P, I64, I]
+        lib.or_o1_search_batch.restype = I
         _lib = lib
     return _lib
 
@@ -110,6 +117,33 @@ def o1(nodes, w, root: int = 0, max_bytes: int = O1_MAX_BYTES) -> bool:
     if r < 0:
         raise MemoryError("O1 tables too large for this string")
     return bool(r)
+
+
+def o1_search(nodes, w, root: int = 0, max_bytes: int = O1_MAX_BYTES) -> int:
+    """Unanchored search from the big-step tables: the smallest j such that
+    some substring w[i:j] (i <= j) is matched (Fig 2.1), or -1.  Raises
+    MemoryError when the tables would exceed max_bytes."""
+    nd = _nodes(nodes)
+    b = _buf(w)
+    r = _L().or_o1_search(_p(nd), len(nd), root, _p(b), len(b) - 1, max_bytes)
+    if r == -2:
+        raise MemoryError("O1 tables too large for this string")
+    return int(r)
+
+
+def o1_search_batch(nodes, data: np.ndarray, offsets: np.ndarray, root: int = 0, threads: int = 0,
+                    max_bytes: int = O1_MAX_BYTES) -> np.ndarray:
+    """o1_search per string (int64; -2 marks strings whose tables would be
+    too large)."""
+    nd = _nodes(nodes)
+    n = len(offsets) - 1
+    out = np.zeros(max(n, 1), np.int64)
+    d = np.ascontiguousarray(data, np.uint8)
+    if d.size == 0:
+        d = np.zeros(1, np.uint8)
+    o = np.ascontiguousarray(offsets, np.int64)
+    _L().or_o1_search_batch(_p(nd), len(nd), root, _p(d), _p(o), n, _p(out), max_bytes, threads)
+    return out[:n]
 
 
 def o2(nodes, w, root: int = 0) -> bool:

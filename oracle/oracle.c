@@ -11,6 +11,8 @@
  *   O1  -- the big-step matching relation e |v w of Fig 2.1 (rules Seq, Match,
  *          Epsilon, Kleene1, Kleene2, Alt1, Alt2), read as the least relation
  *          closed under the rules, memoised over (node, start index).
+ *   O1 search -- unanchored search from the same tables: the earliest end j
+ *          of a substring w[i..j) with e |v w[i..j) (not in the paper).
  *   O2  -- the sequential lockstep machine <c; t; n; w> of Def 6.2 / Fig 6.1
  *          with the add-unique function psi of Def 6.1, over the pointer tree
  *          of Section 4 with the cont function of Def 4.4.
@@ -112,15 +114,19 @@ static int postorder(const or_node* nd, int nn, int root, int32_t* order) {
     return k;
 }
 
-int or_o1(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, int64_t max_bytes) {
+/* The ends tables for every node and start: nn * (L+1) sets of *words
+ * 64-bit words; NULL when they would exceed max_bytes (or on a malformed
+ * tree).  The caller frees. */
+static uint64_t* o1_tables(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, int64_t max_bytes,
+                           int64_t* words_out) {
     int64_t words = (L + 1 + 63) / 64;
     int64_t need = (int64_t)nn * (L + 1) * words * 8;
-    if (need > max_bytes) return -1;
+    if (need > max_bytes) return NULL;
     uint64_t* E = (uint64_t*)calloc((size_t)need / 8, 8);
     int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)nn);
-    if (!E || !order) { free(E); free(order); return -1; }
+    if (!E || !order) { free(E); free(order); return NULL; }
     int k = postorder(nd, nn, root, order);
-    if (k < 0) { free(E); free(order); return -1; }
+    if (k < 0) { free(E); free(order); return NULL; }
 #define ENDS(e, i) (E + (((int64_t)(e) * (L + 1) + (i)) * words))
 #define SETB(s, j) ((s)[(j) >> 6] |= 1ULL << ((j) & 63))
 #define GETB(s, j) (((s)[(j) >> 6] >> ((j) & 63)) & 1ULL)
@@ -163,13 +169,43 @@ int or_o1(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, int6
             }
         }
     }
+    free(order);
+    *words_out = words;
+    return E;
+}
+
+int or_o1(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, int64_t max_bytes) {
+    int64_t words = 0;
+    uint64_t* E = o1_tables(nd, nn, root, w, L, max_bytes, &words);
+    if (!E) return -1;
     int res = (int)GETB(ENDS(root, 0), L);
+    free(E);
+    return res;
+}
+
+/* ------------------------------------------------------------ O1 search
+ * Unanchored search (not in the paper; the hot path's search mode): the
+ * smallest j such that e |v w[i..j) for some i <= j, from the same ends
+ * tables -- min over i of the lowest j in ends(root, i).  -1 if there is no
+ * such j; -2 when the tables would exceed max_bytes. */
+int64_t or_o1_search(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, int64_t max_bytes) {
+    int64_t words = 0;
+    uint64_t* E = o1_tables(nd, nn, root, w, L, max_bytes, &words);
+    if (!E) return -2;
+    int64_t best = -1;
+    for (int64_t i = 0; i <= L; i++) {
+        const uint64_t* s = ENDS(root, i);
+        for (int64_t j = i; j <= L && (best < 0 || j < best); j++)
+            if (GETB(s, j)) {
+                best = j;
+                break;
+            }
+    }
 #undef ENDS
 #undef SETB
 #undef GETB
     free(E);
-    free(order);
-    return res;
+    return best;
 }
 
 /* ------------------------------------------------------------------ O2
@@ -309,6 +345,13 @@ int or_o2_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const
     }
     free(cont);
     return failed ? -1 : 0;
+}
+
+int or_o1_search_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const int64_t* off, int64_t n,
+                       int64_t* out, int64_t max_bytes, int nthreads) {
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    for (int64_t i = 0; i < n; i++) out[i] = or_o1_search(nd, nn, root, bytes + off[i], off[i + 1] - off[i], max_bytes);
+    return 0;
 }
 
 int or_o1_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const int64_t* off, int64_t n,

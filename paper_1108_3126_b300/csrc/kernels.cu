@@ -111,13 +111,13 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
 // Counting sort of the strings by (class, length bucket), longest first
 // within a class, in two launches:
 //   hist    : every block counts its range in shared memory and adds its
-//             counts to the global bucket totals; the last block to finish
-//             (ticket on a counter after a fence -- nothing waits) turns the
-//             totals into exclusive starts, copies them to the claim cursors
-//             and clears the work counter of the kernel that follows
-//   scatter : every block counts its range again, claims one contiguous
-//             range per bucket with one atomic add on the cursor, and places
-//             its strings there with shared-memory cursors
+//             counts to the global bucket totals (block 0 also clears the
+//             work counter of the kernel that follows)
+//   scatter : every block scans the totals itself (the bucket starts; block
+//             0 publishes them), counts its range again, claims one
+//             contiguous range per bucket with one atomic add on a zeroed
+//             cursor, and places its strings there with shared-memory
+//             cursors
 // Each thread holds the keys of kPlanItems strings at a time, so the loads
 // of a tile are in flight together.  Within a bucket the order depends on
 // which block claims first; the kernels only need equal lengths within a
@@ -166,11 +166,9 @@ __device__ void plan_count(const int64_t* off, const uint8_t* cls, long long lo,
 __global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __restrict__ off,
                                                             const uint8_t* __restrict__ cls, long long n,
                                                             long long per, int nbk, unsigned* __restrict__ totals,
-                                                            unsigned* __restrict__ cursor, unsigned* __restrict__ done,
                                                             unsigned* __restrict__ queue, long long long_bytes) {
     extern __shared__ unsigned sh[];
-    __shared__ unsigned ticket;
-    __shared__ unsigned wsum[kPlanThreads / 32];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && queue) *queue = 0;
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
     const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
@@ -178,21 +176,19 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __res
     __syncthreads();
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
         if (sh[b]) atomicAdd(&totals[b], sh[b]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) ticket = atomicAdd(done, 1u);
-    __syncthreads();
-    if (ticket != gridDim.x - 1) return;
-    // the last block: every other block's counts are in the totals
-    __threadfence();
+}
+
+// exclusive scan of in[0..nbk) into out (shared), by the whole block
+__device__ void plan_block_scan(const unsigned* __restrict__ in, int nbk, unsigned* out) {
+    __shared__ unsigned wsum[kPlanThreads / 32];
     const int per_t = (nbk + kPlanThreads - 1) / kPlanThreads;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     unsigned sum = 0;
     for (int j = 0; j < per_t; j++) {
         const int b = t * per_t + j;
         if (b < nbk) {
-            const unsigned v = __ldcg(&totals[b]);
-            sh[b] = v;
+            const unsigned v = in[b];
+            out[b] = v;
             sum += v;
         }
     }
@@ -218,27 +214,35 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __res
     for (int j = 0; j < per_t; j++) {
         const int b = t * per_t + j;
         if (b < nbk) {
-            totals[b] = run;
-            cursor[b] = run;
-            run += sh[b];
+            const unsigned v = out[b];
+            out[b] = run;
+            run += v;
         }
     }
-    if (t == 0 && queue) *queue = 0;
+    __syncthreads();
 }
 
+// every block scans the totals itself (bucket starts), claims a range per
+// bucket with one atomic add on a zeroed cursor, and places its strings;
+// block 0 also publishes the starts
 __global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __restrict__ off,
                                                                const uint8_t* __restrict__ cls, long long n,
                                                                long long per, int nbk,
+                                                               const unsigned* __restrict__ totals,
                                                                unsigned* __restrict__ cursor,
+                                                               unsigned* __restrict__ starts,
                                                                uint32_t* __restrict__ perm, long long long_bytes) {
-    extern __shared__ unsigned sh[];
+    extern __shared__ unsigned sh[];  // [nbk] counts, then [nbk] bucket starts
+    unsigned* sc = sh + nbk;
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
     const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
     plan_count(off, cls, lo, hi, long_bytes, sh);
-    __syncthreads();
+    plan_block_scan(totals, nbk, sc);
+    if (blockIdx.x == 0)
+        for (int b = threadIdx.x; b < nbk; b += kPlanThreads) starts[b] = sc[b];
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
-        if (sh[b]) sh[b] = atomicAdd(&cursor[b], sh[b]);
+        if (sh[b]) sh[b] = sc[b] + atomicAdd(&cursor[b], sh[b]);
     __syncthreads();
     for (long long base = lo; base < hi; base += kPlanTile) {
         int key[kPlanItems];
@@ -415,30 +419,29 @@ int plan_blocks(size_t n) {
     return (int)std::max<long long>(1, std::min<long long>(g, (long long)sm_count() * 64));
 }
 
-// totals (+ the finish counter after them), cursors, permutation
+// totals and claim cursors (zeroed together), bucket starts, permutation
 size_t plan_workspace_bytes(size_t n, int nclasses) {
     size_t nbk = (size_t)kLenBuckets * nclasses;
-    return align16(nbk * 4 + 4) + align16(nbk * 4) + align16(n * 4);
+    return align16(2 * nbk * 4) + align16(nbk * 4) + align16(n * 4);
 }
 
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
                         unsigned** starts, cudaStream_t st, unsigned* queue, long long long_bytes) {
-    const int nbk = kLenBuckets * nclasses;  // at most 7 x 384 buckets: 10.5 KiB of shared memory
+    const int nbk = kLenBuckets * nclasses;  // at most 7 x 384 buckets: 21 KiB of shared memory in the scatter
     const int G = plan_blocks(n);
     long long per = ((long long)n + G - 1) / G;
     per = (per + kPlanTile - 1) / kPlanTile * kPlanTile;
     uint8_t* w = static_cast<uint8_t*>(ws);
     unsigned* totals = reinterpret_cast<unsigned*>(w);
-    unsigned* done = totals + nbk;
-    unsigned* cursor = reinterpret_cast<unsigned*>(w + align16((size_t)nbk * 4 + 4));
-    *perm = reinterpret_cast<uint32_t*>(w + align16((size_t)nbk * 4 + 4) + align16((size_t)nbk * 4));
-    *starts = totals;
-    const size_t shb = (size_t)nbk * 4;
-    cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)nbk * 4 + 4, st);
+    unsigned* cursor = totals + nbk;
+    unsigned* st_out = reinterpret_cast<unsigned*>(w + align16(2 * (size_t)nbk * 4));
+    *perm = reinterpret_cast<uint32_t*>(w + align16(2 * (size_t)nbk * 4) + align16((size_t)nbk * 4));
+    *starts = st_out;
+    cudaError_t e = cudaMemsetAsync(totals, 0, 2 * (size_t)nbk * 4, st);
     if (e != cudaSuccess) return e;
-    k_plan_hist<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, totals, cursor, done, queue,
-                                              long_bytes);
-    k_plan_scatter<<<G, kPlanThreads, shb, st>>>(off, cls, (long long)n, per, nbk, cursor, *perm, long_bytes);
+    k_plan_hist<<<G, kPlanThreads, (size_t)nbk * 4, st>>>(off, cls, (long long)n, per, nbk, totals, queue, long_bytes);
+    k_plan_scatter<<<G, kPlanThreads, 2 * (size_t)nbk * 4, st>>>(off, cls, (long long)n, per, nbk, totals, cursor,
+                                                                 st_out, *perm, long_bytes);
     prof_count(2);
     return cudaGetLastError();
 }

@@ -228,3 +228,55 @@ def test_deep_epsilon_loops_terminate():
     n = oracle.parse(pat)
     assert oracle.o2(n, b"aaab") and not oracle.o2(n, b"aaa")
     assert oracle.o1(n, b"aaab") and not oracle.o1(n, b"aaa")
+
+
+# ------------------------------------------------------------ search oracle
+def _brute_search(lang_sets, w: bytes) -> int:
+    """Earliest end j of a substring w[i:j] in the (truncated) language: the
+    definition, checked against sets built denotationally."""
+    for j in range(len(w) + 1):
+        for i in range(j + 1):
+            if w[i:j] in lang_sets[j - i]:
+                return j
+    return -1
+
+
+def test_o1_search_vs_brute_force():
+    """o1_search against the denotational language on every substring of
+    random strings over {a,b,c} of length <= 8 (so every substring is within
+    the truncated language)."""
+    rng = np.random.default_rng(0xB5)
+    for nodes in small_regexes(120, 0xB4):
+        lang = oracle.brute_language(nodes, b"abc", 8)
+        sets = [set() for _ in range(9)]
+        for n in range(9):
+            strs = [s for s in oracle.all_strings(b"abc", n) if len(s) == n]
+            sets[n] = {s for s, ok in zip(strs, lang[n]) if ok}
+        words = [bytes(rng.choice(list(b"abc"), size=int(rng.integers(0, 9))).tolist()) for _ in range(40)]
+        pk = synth.pack(words)
+        got = oracle.o1_search_batch(nodes, pk.data, pk.offsets)
+        for w, g in zip(words, got):
+            assert g == _brute_search(sets, w), (synth.to_pattern(nodes), w, g)
+
+
+def test_o1_search_closed_forms():
+    rng = np.random.default_rng(0xB6)
+    words = [bytes(rng.choice(list(b"abcx"), size=int(rng.integers(0, 40))).tolist()) for _ in range(300)]
+    pk = synth.pack(words)
+    lit = oracle.o1_search_batch(oracle.parse(b"ab"), pk.data, pk.offsets)
+    cfirst = oracle.o1_search_batch(oracle.parse(b"(a|b)*c"), pk.data, pk.offsets)
+    star = oracle.o1_search_batch(oracle.parse(b"a*"), pk.data, pk.offsets)
+    twice = oracle.o1_search_batch(oracle.parse(b"x(a|b|c|x)*x"), pk.data, pk.offsets)
+    for w, a, b, c, d in zip(words, lit, cfirst, star, twice):
+        k = w.find(b"ab")
+        assert a == (k + 2 if k >= 0 else -1)
+        k = w.find(b"c")
+        assert b == (k + 1 if k >= 0 else -1)
+        assert c == 0  # nullable: the empty substring at 0
+        first = w.find(b"x")
+        second = w.find(b"x", first + 1) if first >= 0 else -1
+        assert d == (second + 1 if second >= 0 else -1)
+    # no string of an empty-ish language: only "" would match \e, found at 0
+    assert oracle.o1_search(oracle.parse(b"\\e"), b"abc") == 0
+    assert oracle.o1_search(oracle.parse(b"(a*)*b"), b"aaaa") == -1
+    assert oracle.o1_search(oracle.parse(b"(a*)*b"), b"aaab") == 4
