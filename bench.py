@@ -278,6 +278,21 @@ def run_streaming(args, world, rank, local):
         vms = a.elapsed_time(b) / reps
         variants[name] = {"GB/s": round(total_bytes / (vms * 1e-3) / 1e9, 1), "ms": round(vms, 4)}
 
+    # unanchored search over the same batch (earliest end of a matching
+    # substring), informational
+    search = None
+    if not args.quick:
+        rs = rx.Regex.from_nodes(nodes, 0, rx.COMPILE_SEARCH)
+        if rs.info()["search_states"]:
+            d_end = torch.empty(n, dtype=torch.int64, device=dev)
+            for _ in range(2):
+                rx.search(rs, d_str, d_off, d_end, n=n, stream=stream)
+            sms = _time(lambda: rx.search(rs, d_str, d_off, d_end, n=n, stream=stream), 20, stream, dev)
+            search = {"GB/s": round(total_bytes / (sms * 1e-3) / 1e9, 1), "ms": round(sms, 4),
+                      "search_states": rs.info()["search_states"], "found": int((d_end >= 0).sum().item()),
+                      "note": "batch bytes / time; a string is read only up to its first match"}
+        rs.free()
+
     # end to end through the public API with host buffers: compile the
     # expression, then rx_match_host (strings + offsets from pinned host
     # memory, copies of each 64 MiB piece overlapped with matching the
@@ -345,6 +360,7 @@ def run_streaming(args, world, rank, local):
         "clocks": clk,
         "cpu_baseline": cpu,
         "variants": variants,
+        "search": search,
         "autotune": tuned,
         "compile_us": round(compile_us, 1),
         "accepted": accepted,

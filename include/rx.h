@@ -83,6 +83,7 @@ typedef enum {
 #define RX_COMPILE_HOST_ONLY 1u /* build host tables only; the handle cannot be
                                    matched (used to inspect the compiler)  */
 #define RX_COMPILE_NO_MEMO 2u   /* do not build the macro-step cache       */
+#define RX_COMPILE_SEARCH 4u    /* also build the search cache (rx_search)  */
 
 typedef struct {
     int32_t nodes;        /* nodes reachable from the root                  */
@@ -92,6 +93,8 @@ typedef struct {
     int32_t memo_states;  /* cached macro-step states, 0 if no cache         */
     uint32_t variants;    /* bit v set iff rx_variant v can run this handle  */
     int64_t device_bytes; /* device memory held by the handle                */
+    int32_t search_states; /* search cache size (0: none; RX_COMPILE_SEARCH) */
+    int32_t pad;
 } rx_info_t;
 
 /* --------------------------------------------------------------- compiling */
@@ -238,6 +241,22 @@ rx_status rx_match_static(rx_handle h, size_t n, const uint8_t* strings, const i
  */
 rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
                         void* stream);
+
+/*
+ * rx_search -- unanchored search (async).  Not in the paper, which decides
+ * whole-string membership only: out_end[i] = the smallest j such that some
+ * substring w[i0..j) of string i (i0 <= j) is matched by the expression
+ * (e |v w[i0..j), Fig 2.1), or -1 when no substring matches; a nullable
+ * expression gives 0.  Computed by the lockstep machine with the start set
+ * added back after every byte (Defs 5.1-5.3 on the Sigma* e machine), as a
+ * cache of macro steps built when the handle is compiled with
+ * RX_COMPILE_SEARCH (at most 192 states).
+ *   strings/offsets as in rx_match; out_end DEVICE int64[n].
+ * Errors: RX_ERR_INVALID_ARG, RX_ERR_UNSUPPORTED (no search cache: flag
+ * missing, or the cache would exceed 192 states), RX_ERR_OOM, RX_ERR_CUDA.
+ */
+rx_status rx_search(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, int64_t* out_end,
+                    void* stream);
 
 /*
  * rx_device_faults -- bounded device-side waits that gave up, counted on

@@ -27,6 +27,7 @@ VARIANT_AUTO, VARIANT_MEMO, VARIANT_THREAD, VARIANT_SPARSE, VARIANT_WARP, VARIAN
 VARIANT_NAMES = {0: "auto", 1: "memo", 2: "thread", 3: "sparse", 4: "warp", 5: "paper"}
 COMPILE_HOST_ONLY = 1
 COMPILE_NO_MEMO = 2
+COMPILE_SEARCH = 4
 
 STATUS = {0: "RX_OK", 1: "RX_ERR_PARSE", 2: "RX_ERR_INVALID_ARG", 3: "RX_ERR_TOO_LARGE", 4: "RX_ERR_OOM",
           5: "RX_ERR_CUDA", 6: "RX_ERR_TIMEOUT", 7: "RX_ERR_BUSY", 8: "RX_ERR_UNSUPPORTED"}
@@ -43,7 +44,7 @@ class RxError(RuntimeError):
 class _Info(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_int32), ("positions", ctypes.c_int32), ("words", ctypes.c_int32),
                 ("nullable", ctypes.c_int32), ("memo_states", ctypes.c_int32), ("variants", ctypes.c_uint32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("search_states", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class _Opts(ctypes.Structure):
@@ -87,6 +88,7 @@ SIGNATURES = {
     "rx_match_static": ([P, SZ, P, P, P, P], I32),
     "rx_match_host": ([P, SZ, P, P, P, P], I32),
     "rx_device_faults": ([I32], I64),
+    "rx_search": ([P, SZ, P, P, P, P], I32),
     "rx_match_batch": ([P, SZ, P, P, P, P], I32),
     "rx_match_pairs": ([P, SZ, P, P, P, P], I32),
     "rx_batch_prepare": ([P, SZ, ctypes.POINTER(P)], I32),
@@ -245,6 +247,15 @@ def match_static(rx: Regex, strings, offsets, out, n: int | None = None, stream=
     if n is None:
         n = len(offsets) - 1
     _check(lib().rx_match_static(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream)))
+
+
+def search(rx: Regex, strings, offsets, out_end, n: int | None = None, stream=None):
+    """out_end[i] (int64) = earliest end of a substring of string i that the
+    expression matches, -1 if none (async; the handle must be compiled with
+    COMPILE_SEARCH)."""
+    if n is None:
+        n = len(offsets) - 1
+    _check(lib().rx_search(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out_end), _stream(stream)))
 
 
 def device_faults(reset: bool = False) -> int:

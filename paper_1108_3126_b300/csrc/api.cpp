@@ -82,6 +82,7 @@ static rx_status upload(rx_regex* h) {
     size_t o_desc = take(256 * sizeof(uint2)), o_tt = take(std::max<size_t>(C.gl_tt.size(), 1) * 4);
     size_t o_T = take(std::max<size_t>(C.memo_T.size(), 1) * 4), o_acc = take(std::max<size_t>(C.memo_acc.size(), 1));
     size_t o_T8 = take(std::max<size_t>(C.memo_T.size(), 1));
+    size_t o_sT = take(std::max<size_t>(C.srch_T.size(), 1) * 4);
     size_t o_nd = take(C.nodes.size() * sizeof(int4));
     const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
     size_t o_sps = take(spW * 4 + 16), o_spB = take((size_t)256 * spW * 4 + 16),
@@ -99,6 +100,7 @@ static rx_status upload(rx_regex* h) {
     put(o_desc, C.gl_desc.data(), 256 * sizeof(uint2));
     put(o_tt, C.gl_tt.data(), C.gl_tt.size() * 4);
     put(o_T, C.memo_T.data(), C.memo_T.size() * 4);
+    put(o_sT, C.srch_T.data(), C.srch_T.size() * 4);
     for (size_t i = 0; i < C.memo_T.size(); i++) blob[o_T8 + i] = (uint8_t)(C.memo_T[i] / 256u);  // ids < 192
     put(o_acc, C.memo_acc.data(), C.memo_acc.size());
     std::vector<int4> pn(C.nodes.size());
@@ -148,6 +150,10 @@ static rx_status upload(rx_regex* h) {
     t.memo_K = C.memo_K;
     t.memo_T = reinterpret_cast<const uint32_t*>(b + o_T);
     t.memo_T8 = b + o_T8;
+    t.srch_K = C.srch_K;
+    t.srch_T = reinterpret_cast<const uint32_t*>(b + o_sT);
+    t.srch_start = C.srch_start;
+    t.srch_acc0 = C.srch_acc0;
     t.memo_acc = b + o_acc;
     t.memo_start = C.memo_start;
     t.bgp_T = C.bgp_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bgp);
@@ -297,6 +303,8 @@ rx_status rx_info(rx_handle h, rx_info_t* out) {
     out->memo_states = h->host.memo_K;
     out->variants = h->host.variants;
     out->device_bytes = h->dev_bytes;
+    out->search_states = h->host.srch_K;
+    out->pad = 0;
     return RX_OK;
 }
 
@@ -383,6 +391,29 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
     if (s != RX_OK) return s;
     cudaError_t e = launch_match(h->dev, variant, n, strings, offsets, out, sort, block, ws, need, st);
     if (e != cudaSuccess) return cuda_fail(e, "rx_match launch");
+    return RX_OK;
+    RX_GUARD_END
+}
+
+rx_status rx_search(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, int64_t* out_end,
+                    void* stream) {
+    RX_GUARD_BEGIN
+    if (!h || h->host_only || (n > 0 && (!offsets || !out_end))) {
+        set_error("rx_search: bad argument");
+        return RX_ERR_INVALID_ARG;
+    }
+    if (n == 0) return RX_OK;
+    if (h->dev.srch_K <= 0) {
+        set_error("rx_search: no search cache (compile with RX_COMPILE_SEARCH; at most 192 states)");
+        return RX_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* ws = nullptr;
+    const size_t need = rx::search_workspace_bytes(n);
+    rx_status s = get_workspace(st, need, &ws);
+    if (s != RX_OK) return s;
+    cudaError_t e = rx::launch_search(h->dev, n, strings, offsets, out_end, ws, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_search launch");
     return RX_OK;
     RX_GUARD_END
 }

@@ -469,6 +469,71 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
             C.memo_start = (uint32_t)s0 * 256u;
         }
     }
+    // ---- 8c. cache for unanchored search (a match may start at any
+    // position): the sets reachable when the start set is added back after
+    // every byte, S' = (macro step of S on c) U Start, from S0 = Start.  A
+    // set holding null marks the end of a match.  States are renumbered so
+    // that these accepting sets come last (ids >= srch_acc0).
+    C.srch_K = 0;
+    C.srch_T.clear();
+    if ((flags & RX_COMPILE_SEARCH) && !(flags & RX_COMPILE_NO_MEMO)) {
+        struct VHash2 {
+            size_t operator()(const std::vector<uint32_t>& v) const {
+                uint64_t h = 1469598103934665603ull;
+                for (uint32_t x : v) h = (h ^ x) * 1099511628211ull;
+                return (size_t)h;
+            }
+        };
+        std::unordered_map<std::vector<uint32_t>, int, VHash2> id;
+        std::vector<std::vector<uint32_t>> states;
+        auto get = [&](const std::vector<uint32_t>& v) -> int {
+            auto it = id.find(v);
+            if (it != id.end()) return it->second;
+            int k = (int)states.size();
+            id.emplace(v, k);
+            states.push_back(v);
+            return k;
+        };
+        get(C.start);
+        std::vector<int> T;
+        bool ok = true;
+        for (size_t k = 0; k < states.size() && ok; k++) {
+            T.resize((k + 1) * 256, 0);
+            for (int c = 0; c < 256; c++) {
+                std::vector<uint32_t> nx(C.start.begin(), C.start.end());
+                if (!groups[c].empty())
+                    for (int w = 0; w < W; w++) {
+                        uint32_t sb = states[k][w] & C.B[(size_t)c * W + w];
+                        while (sb) {
+                            int b = __builtin_ctz(sb);
+                            sb &= sb - 1;
+                            const uint32_t* row = &C.follow_bit[(size_t)(w * 32 + b) * W];
+                            for (int z = 0; z < W; z++) nx[z] |= row[z];
+                        }
+                    }
+                T[k * 256 + c] = get(nx);
+                if ((int)states.size() > kMemoMaxStates) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        if (ok) {
+            const int K = (int)states.size();
+            auto accepts = [&](int k) { return (states[k][C.null_bit >> 5] >> (C.null_bit & 31)) & 1u; };
+            std::vector<int> newid(K);
+            int nacc = 0;
+            for (int k = 0; k < K; k++) nacc += accepts(k) ? 1 : 0;
+            int lo = 0, hi = K - nacc;
+            for (int k = 0; k < K; k++) newid[k] = accepts(k) ? hi++ : lo++;
+            C.srch_K = K;
+            C.srch_acc0 = K - nacc;
+            C.srch_start = (uint32_t)newid[0] * 256u;
+            C.srch_T.assign((size_t)K * 256, 0u);
+            for (int k = 0; k < K; k++)
+                for (int c = 0; c < 256; c++) C.srch_T[(size_t)newid[k] * 256 + c] = (uint32_t)newid[T[k * 256 + c]] * 256u;
+        }
+    }
     // ---- 8b. two macro steps per lookup: when every label lies in one
     // aligned window of 32 byte values, entry 32*j + i of a state's pair row
     // is the state after reading byte lo+i then byte lo+j (two steps of the

@@ -82,6 +82,12 @@ cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t le
                               const uint16_t* pstart, uint16_t* res, unsigned* queue, long long max_tasks,
                               cudaStream_t st);
 
+// Unanchored search over the search cache (stream.cu): out[i] = earliest
+// end of a matching substring of string i, -1 if none.
+size_t search_workspace_bytes(size_t n);
+cudaError_t launch_search(const DevTables& t, size_t n, const uint8_t* str, const int64_t* off, int64_t* out,
+                          void* ws, size_t ws_bytes, cudaStream_t st);
+
 // Chunked single-string mode (long.cu).
 bool long_supported(const DevTables& t);
 int64_t long_chunk_auto(const DevTables& t, int64_t len);

@@ -48,6 +48,12 @@ struct DevTables {
     const uint8_t* memo_T8;  // [K*256] next state id (the same table, one byte per entry, for global reads)
     const uint8_t* memo_acc; // [K] 1 iff the state's set holds null
     uint32_t memo_start;     // start state * 256
+    // cache for unanchored search (start set added after every byte);
+    // states >= srch_acc0 hold null (a match ends there)
+    int32_t srch_K;          // 0: unavailable
+    const uint32_t* srch_T;  // [K*256] next state * 256
+    uint32_t srch_start;     // start state * 256
+    int32_t srch_acc0;
     // two-byte cache, for labels inside one 32-value window [bg_lo, bg_lo+32),
     // in planes of 8 states: plane p = s / 8 holds
     // 40 rows of 512 bytes; row j < 32 holds, for slot q = s % 8 at byte
@@ -87,6 +93,9 @@ struct Compiled {
     // cache of macro steps
     int memo_K = 0;
     std::vector<uint32_t> memo_T;  // K*256
+    int srch_K = 0, srch_acc0 = 0;  // search cache (see DevTables::srch_T)
+    uint32_t srch_start = 0;
+    std::vector<uint32_t> srch_T;
     std::vector<uint8_t> memo_acc;
     uint32_t memo_start = 0;
     // two-byte cache: per state a row of 1024 pair successors (entry

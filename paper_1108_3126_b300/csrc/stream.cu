@@ -336,6 +336,103 @@ __global__ void __launch_bounds__(1024, 1) k_stream_tma(const DevTables t, const
     }
 }
 
+// ---------------------------------------------------------------- search
+// Unanchored search: the earliest end of a matching substring.  The same
+// rounds as k_stream over the search cache (the start set added back after
+// every byte, so a match may begin anywhere); a lane records the first byte
+// after which its state holds null and stops reading.  Accepting states
+// have the highest ids, so the test is one compare of the state's address.
+struct SearchS {
+    uint32_t st, base, thr;
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) { return (size_t)t.srch_K * 1024; }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        const uint32_t b = smem_u32(sm);
+        uint32_t* T = reinterpret_cast<uint32_t*>(sm);
+        for (int i = threadIdx.x; i < t.srch_K * 256; i += blockDim.x) T[i] = b + t.srch_T[i] * 4u;
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        base = smem_u32(sm);
+        st = base + t.srch_start * 4u;
+        thr = base + (uint32_t)t.srch_acc0 * 1024u;
+    }
+    __device__ __forceinline__ void step(uint32_t c) { st = lds32(st + c * 4u); }
+    __device__ __forceinline__ bool accepted() const { return st >= thr; }
+};
+
+// steps over the bytes of a 32-byte block selected by mask; returns the
+// index of the first byte after which the state accepts (-1: none), and
+// stops stepping there
+__device__ __forceinline__ int search32(SearchS& st, const Blk32& v, uint32_t mask) {
+    int hit = -1;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const uint32_t w = word_of(v, q);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int i = 4 * q + k;
+            if (((mask >> i) & 1u) && hit < 0) {
+                st.step(byte_k(w, k));
+                if (st.accepted()) hit = i;
+            }
+        }
+    }
+    return hit;
+}
+
+__global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_search(const DevTables t, const uint8_t* __restrict__ str,
+                                                           const int64_t* __restrict__ off,
+                                                           const uint32_t* __restrict__ perm, long long n,
+                                                           int64_t* __restrict__ out, unsigned* __restrict__ queue) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    SearchS::load(t, smem);
+    __syncthreads();
+    SearchS proto;
+    proto.bind(t, smem);
+    const int lane = threadIdx.x & 31;
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    const long long nround = (n + 31) / 32;
+    for (;;) {
+        unsigned r = 0;
+        if (lane == 0) r = atomicAdd(queue, 1u);
+        r = __shfl_sync(FULL, r, 0);
+        if ((long long)r >= nround) break;
+        const long long k = (long long)r * 32 + lane;
+        const bool valid = k < n;
+        const long long id = valid ? (perm ? (long long)perm[k] : k) : 0;
+        uint64_t s = base, e = base;
+        if (valid) {
+            s += (uint64_t)off[id];
+            e += (uint64_t)off[id + 1];
+        }
+        SearchS st = proto;
+        int64_t found = -1;
+        if (valid && st.accepted()) found = 0;  // the empty substring at 0
+        bool active = valid && found < 0 && s < e;
+        uint64_t blk = s & ~uint64_t(31);
+        Blk32 va = ld_blk(blk, active);
+        Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
+        while (__any_sync(FULL, active)) {
+            int hit = search32(st, va, valid_mask(blk, s, e, active));
+            if (active && hit >= 0) {
+                found = (int64_t)(blk + hit - s) + 1;
+                active = false;
+            }
+            if (active && blk + 32 >= e) active = false;
+            va = ld_blk(blk + 64, active && blk + 64 < e);
+            if (!__any_sync(FULL, active)) break;
+            hit = search32(st, vb, valid_mask(blk + 32, s, e, active));
+            if (active && hit >= 0) {
+                found = (int64_t)(blk + 32 + hit - s) + 1;
+                active = false;
+            }
+            if (active && blk + 64 >= e) active = false;
+            vb = ld_blk(blk + 96, active && blk + 96 < e);
+            blk += 64;
+        }
+        if (valid) out[id] = found;
+    }
+}
+
 // Tasks of the chunked long-string mode: task i starts the cache of macro
 // steps in state task_state[i] at byte task_chunk[i] * C + pstart[chunk] of the text and
 // runs to the end of that chunk; res[i] receives the final state id.  Tasks
@@ -448,6 +545,24 @@ cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str,
     return cudaGetLastError();
 }
 
+cudaError_t launch_search_k(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
+                            const uint32_t* perm, int64_t* out, unsigned* queue, cudaStream_t st) {
+    const size_t sm = SearchS::smem_bytes(t);
+    const int block = 512;
+    cudaError_t e = allow_smem(k_search, sm);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, block, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long rounds = (n + 31) / 32;
+    long long grid = std::min<long long>((rounds * 32 + block - 1) / block, (long long)per_sm * sm_count());
+    {
+        ProfScope ps(st);
+        k_search<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, off, perm, n, out, queue);
+    }
+    return cudaGetLastError();
+}
+
 template <class S, int CH, int NST>
 cudaError_t launch_stream_tma_t(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
                                 const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st) {
@@ -487,6 +602,22 @@ unsigned read_wait_faults(bool reset) {
         cudaMemcpyToSymbol(g_wait_faults, &z, sizeof(z));
     }
     return v;
+}
+
+size_t search_workspace_bytes(size_t n) { return 256 + plan_workspace_bytes(n, 1); }
+
+cudaError_t launch_search(const DevTables& t, size_t n, const uint8_t* str, const int64_t* off, int64_t* out,
+                          void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (t.srch_K <= 0) return cudaErrorInvalidValue;
+    if (ws_bytes < search_workspace_bytes(n)) return cudaErrorInvalidValue;
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    unsigned* queue = reinterpret_cast<unsigned*>(w);
+    uint32_t* perm = nullptr;
+    unsigned* starts = nullptr;
+    cudaError_t e = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st, queue);
+    if (e != cudaSuccess) return e;
+    return launch_search_k(t, (long long)n, str, off, perm, out, queue, st);
 }
 
 cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,

@@ -179,3 +179,15 @@ def test_host_only_handle_cannot_match():
     with pytest.raises(rx.RxError) as ei:
         rx.match(r, 0, 0, 0, n=1, stream=0)
     assert ei.value.status == 2
+
+
+def test_search_cache_built_only_with_the_flag():
+    import paper_1108_3126_b300 as rx
+    for pat, want in ((b"ab", 3), (b"(a*)*b", 2), (b"x(x|a|b)*x", 3)):
+        r = rx.Regex.compile(pat, rx.COMPILE_SEARCH | rx.COMPILE_HOST_ONLY)
+        assert r.info()["search_states"] == want, pat
+        r2 = rx.Regex.compile(pat, rx.COMPILE_HOST_ONLY)
+        assert r2.info()["search_states"] == 0
+    # no cache without the macro-step cache either
+    r3 = rx.Regex.compile(b"ab", rx.COMPILE_SEARCH | rx.COMPILE_NO_MEMO | rx.COMPILE_HOST_ONLY)
+    assert r3.info()["search_states"] == 0
