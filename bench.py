@@ -323,6 +323,13 @@ def run_streaming(args, world, rank, local):
     e2e_val = world * total_bytes / (e2e_ms * 1e-3) / 1e9
     if not torch.equal(h_out, d_out.cpu()):
         raise SystemExit("rx_match_host disagrees with rx_match on the same batch")
+    # the host-to-device link alone: the same bytes copied from pinned memory
+    # (the ceiling of the end-to-end rate)
+    scratch = torch.empty_like(d_str)
+    link_ms = _time(lambda: (scratch.copy_(h_str, non_blocking=True), d_off.copy_(h_off, non_blocking=True)),
+                    max(3, e2e_steps), stream, dev)
+    link_gbs = total_bytes / (link_ms * 1e-3) / 1e9
+    del scratch
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
@@ -353,7 +360,8 @@ def run_streaming(args, world, rank, local):
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.4 TB/s"},
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "h2d_bytes_per_step": total_bytes + 8 * (n + 1),
-                "d2h_bytes_per_step": n, "includes": "rx_compile_ast + rx_match_host (H2D, match, D2H) per step"},
+                "d2h_bytes_per_step": n, "includes": "rx_compile_ast + rx_match_host (H2D, match, D2H) per step",
+                "h2d_link_gbs": round(link_gbs, 2), "of_link": round(e2e_val / link_gbs, 3)},
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
         "device_faults": rx.device_faults(),

@@ -566,12 +566,16 @@ rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* stri
     rx_status s = rx::collect_pairs(handles, n, "rx_match_batch", tabs, pair_tab, cls);
     if (s != RX_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    size_t need = rx::batch_workspace_bytes(n, tabs.size());
+    rx::BatchLaunch L;
+    L.stride = rx::batch_stride(tabs.data(), tabs.size());
+    cudaError_t e = rx::batch_configure(L);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_match_batch configure");
+    size_t need = rx::batch_workspace_bytes(n, tabs.size()) + rx::batch_maps_bytes(L, n);
     void* ws = nullptr;
     s = rx::get_workspace(st, need, &ws);
     if (s != RX_OK) return s;
-    cudaError_t e = rx::launch_batch(tabs.data(), tabs.size(), pair_tab.data(), cls.data(), n, strings, offsets, out,
-                                     ws, need, st);
+    e = rx::launch_batch(tabs.data(), tabs.size(), pair_tab.data(), cls.data(), n, strings, offsets, out, ws, need, L,
+                         st);
     if (e != cudaSuccess) return cuda_fail(e, "rx_match_batch launch");
     return RX_OK;
     RX_GUARD_END

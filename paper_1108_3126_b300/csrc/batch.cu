@@ -13,9 +13,8 @@
 // the critical path of the whole launch, so a warp takes such a pair alone:
 // its 32 lanes cut the string into 32 chunks; each lane computes its chunk's
 // transfer function on cache states (exact: a macro step acts on states,
-// Def 5.2), advancing every incoming state through prefix stages of growing
-// length and keeping only the distinct states after each, and lane 0
-// composes the 32 functions from the start state.
+// Def 5.2), merging incoming states that meet within a short prefix, and
+// lane 0 composes the 32 functions from the start state.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -45,17 +44,21 @@ __device__ uint32_t lane_memo_run(const uint8_t* __restrict__ T, uint32_t st, ui
     return st;
 }
 
-constexpr int kStage0 = 4;  // bytes of the first prefix stage; each stage doubles
+constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states are merged
 
 // one warp, one long pair: returns whether the pair matches (all lanes).
-// Lane l computes the transfer map of chunk l for every cache state.  The
-// incoming states are advanced in stages of 4, 8, 16, ... bytes; after each
-// stage the states reached are deduplicated (a bitmap; rank = index), so
-// only the distinct ones go on -- states merge within a few bytes, and two
-// incoming states that meet stay together (Def 5.2 is a function of the
-// set).  wsm holds, per lane, map[K] (incoming state -> index of its
-// representative) and then, after the 32 maps, dv[K] (each representative's
-// current state); `stride` >= memo_K bytes each.
+// Lane l computes the transfer map of chunk l (of 32) on cache states.
+// Every incoming state advances over the first 4 bytes of the chunk; the
+// states reached are deduplicated (a bitmap; rank = index) into
+// representatives, and each incoming state records its representative.  The
+// representatives then advance in stages of 4, 8, 16, ... bytes (at most
+// kPairPrefix bytes in all) until at most one distinct live state is among
+// them -- the empty set (state 0) stays empty at no cost, and two states that
+// meet stay together (Def 5.2 is a function of the set) -- and each distinct
+// one runs over the rest of the chunk.  wsm holds, per lane, map[K]
+// (incoming state -> representative) and, after the 32 maps, dv[K] (the
+// representatives' states); `stride` >= memo_K bytes each.  Lane 0 composes
+// the 32 maps from the start state.
 __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
     const int lane = threadIdx.x & 31;
     const int K = t.memo_K;
@@ -65,39 +68,70 @@ __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8
     uint64_t cs = s + (uint64_t)lane * C;
     if (cs > e) cs = e;
     const uint64_t ce = cs + C < e ? cs + C : e;
+    const uint64_t pe = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
     uint8_t* map = wsm + lane * stride;
     uint8_t* dv = wsm + (32 + lane) * stride;
+    // first stage: every incoming state
+    uint64_t pos = cs + 4 < pe ? cs + 4 : pe;
+    uint32_t bm[kBmWords];
+#pragma unroll
+    for (int w = 0; w < kBmWords; w++) bm[w] = 0;
     for (int k = 0; k < K; k++) {
-        map[k] = (uint8_t)k;
-        dv[k] = (uint8_t)k;
+        const uint32_t v = lane_memo_run(T, (uint32_t)k * 256u, cs, pos) >> 8;
+        map[k] = (uint8_t)v;
+        bm_set(bm, v);
     }
-    int nd = K;
-    uint64_t pos = cs, len = kStage0;
-    while (nd > 1 && pos < ce) {
-        const uint64_t end = pos + len < ce ? pos + len : ce;
-        uint32_t bm[kBmWords];
+    int nr = 0;
+#pragma unroll
+    for (int w = 0; w < kBmWords; w++) {
+        uint32_t x = bm[w];
+        while (x) {
+            dv[nr++] = (uint8_t)(w * 32 + __ffs(x) - 1);
+            x &= x - 1;
+        }
+    }
+    for (int k = 0; k < K; k++) map[k] = (uint8_t)rank_below(bm, map[k]);
+    int live = nr - (int)(bm[0] & 1u);
+    // further stages: the representatives only
+    uint64_t len = 4;
+    while (live > 1 && pos < pe) {
+        const uint64_t end = pos + len < pe ? pos + len : pe;
 #pragma unroll
         for (int w = 0; w < kBmWords; w++) bm[w] = 0;
-        for (int i = 0; i < nd; i++) {
+        for (int i = 0; i < nr; i++) {
             const uint32_t v = lane_memo_run(T, (uint32_t)dv[i] * 256u, pos, end) >> 8;
             dv[i] = (uint8_t)v;
             bm_set(bm, v);
         }
-        for (int k = 0; k < K; k++) map[k] = (uint8_t)rank_below(bm, dv[map[k]]);
-        int j = 0;
+        int cnt = 0;
 #pragma unroll
-        for (int w = 0; w < kBmWords; w++) {
-            uint32_t x = bm[w];
-            while (x) {
-                dv[j++] = (uint8_t)(w * 32 + __ffs(x) - 1);
-                x &= x - 1;
-            }
-        }
-        nd = j;
+        for (int w = 0; w < kBmWords; w++) cnt += __popc(bm[w]);
+        live = cnt - (int)(bm[0] & 1u);
         pos = end;
         len *= 2;
     }
-    for (int i = 0; i < nd; i++) dv[i] = (uint8_t)(lane_memo_run(T, (uint32_t)dv[i] * 256u, pos, ce) >> 8);
+    // the rest of the chunk, once per distinct state (a small cache of
+    // (state, result) pairs; a repeat beyond it is run again, same result)
+    uint32_t cv[4], cr[4];
+    int nc = 0;
+    for (int i = 0; i < nr; i++) {
+        const uint32_t v = dv[i];
+        uint32_t r = 0xffffffffu;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (q < nc && cv[q] == v) r = cr[q];
+        if (r == 0xffffffffu) {
+            r = v == 0 ? 0u : lane_memo_run(T, v * 256u, pos, ce) >> 8;
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (q == nc) {
+                    cv[q] = v;
+                    cr[q] = r;
+                }
+            if (nc < 4) nc++;
+        }
+        dv[i] = (uint8_t)r;
+    }
     for (int k = 0; k < K; k++) map[k] = dv[map[k]];
     __syncwarp();
     uint32_t acc = 0;
@@ -110,12 +144,14 @@ __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8
     return __shfl_sync(FULL, acc, 0) != 0;
 }
 
-__global__ void __launch_bounds__(512) k_batch(const BatchTab* __restrict__ tabs, const uint32_t* __restrict__ pair_tab,
+// 64 registers per thread (two 512-thread blocks per SM); the chunk maps of
+// long pairs live in a per-warp slot of global scratch (`maps`, 64 * stride
+// bytes per resident warp), which keeps shared memory free for occupancy
+__global__ void __launch_bounds__(512, 2) k_batch(const BatchTab* __restrict__ tabs, const uint32_t* __restrict__ pair_tab,
                                                const uint32_t* __restrict__ perm, const unsigned* __restrict__ starts,
                                                long long n, const uint8_t* __restrict__ str,
                                                const int64_t* __restrict__ off, uint8_t* __restrict__ out,
-                                               unsigned* __restrict__ queue, int stride) {
-    extern __shared__ __align__(16) uint8_t bsm[];  // 64 x stride bytes per warp
+                                               unsigned* __restrict__ queue, int stride, uint8_t* __restrict__ maps) {
     __shared__ long long seg[kBatchClasses + 1];
     __shared__ long long tfirst[kBatchClasses + 1];
     if (threadIdx.x == 0) {
@@ -145,7 +181,8 @@ __global__ void __launch_bounds__(512) k_batch(const BatchTab* __restrict__ tabs
             const uint32_t p = perm[seg[c] + g];
             const DevTables& t = tabs[pair_tab[p]].t;
             const uint64_t s = base + (uint64_t)off[p], e = base + (uint64_t)off[p + 1];
-            bool acc = warp_long_memo(t, s, e, bsm + (threadIdx.x >> 5) * 64 * stride, stride);
+            const size_t slot = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+            bool acc = warp_long_memo(t, s, e, maps + slot * 64 * (size_t)stride, stride);
             if (lane == 0) out[p] = acc;
             continue;
         }
@@ -250,22 +287,29 @@ cudaError_t batch_upload(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h
     return e;
 }
 
-// kernel attribute and resident blocks per SM for (stride, block)
+// resident blocks per SM for this block size
 cudaError_t batch_configure(BatchLaunch& L) {
     if (L.block != 128 && L.block != 256 && L.block != 512) return cudaErrorInvalidValue;
-    const size_t sm = (size_t)L.block * 2 * L.stride;  // at most 192 KiB (512 threads, 192 states)
-    cudaError_t e = allow_smem(k_batch, sm);
     int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, L.block, sm);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, L.block, 0);
     if (e != cudaSuccess) return e;
     L.grid_cap = (long long)std::max(per_sm, 1) * sm_count();
     return cudaSuccess;
 }
 
+long long batch_grid(const BatchLaunch& L, size_t n) {
+    return std::max<long long>(1, std::min<long long>(L.grid_cap, ((long long)n * 32 + L.block - 1) / L.block));
+}
+
+// global scratch for the chunk maps of the warps of one launch
+size_t batch_maps_bytes(const BatchLaunch& L, size_t n) {
+    return (size_t)batch_grid(L, n) * (L.block / 32) * 64 * (size_t)std::max(L.stride, 1);
+}
+
 // counter reset, planner, persistent kernel: every launch of one batched
 // run, all on `st` (capturable into a graph)
 cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws,
-                      const BatchLaunch& L, cudaStream_t st, bool profile) {
+                      const BatchLaunch& L, cudaStream_t st, bool profile, uint8_t* maps) {
     if (n == 0) return cudaSuccess;
     BatchWs b = batch_ws(ws, n, ntabs);
     cudaError_t e = cudaMemsetAsync(b.queue, 0, 256, st);
@@ -274,16 +318,14 @@ cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t*
     unsigned* starts = nullptr;
     e = launch_plan(off, b.cls, kBatchClasses, n, b.plan_ws, &perm, &starts, st, nullptr, L.long_bytes);
     if (e != cudaSuccess) return e;
-    const size_t sm = (size_t)L.block * 2 * L.stride;
-    long long grid = std::min<long long>(L.grid_cap, ((long long)n * 32 + L.block - 1) / L.block);
-    grid = std::max<long long>(grid, 1);
+    const long long grid = batch_grid(L, n);
     if (profile) {
         ProfScope ps(st);
-        k_batch<<<(unsigned)grid, L.block, sm, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
-                                                     b.queue, L.stride);
+        k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
+                                                    b.queue, L.stride, maps);
     } else {
-        k_batch<<<(unsigned)grid, L.block, sm, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
-                                                     b.queue, L.stride);
+        k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
+                                                    b.queue, L.stride, maps);
         prof_count(1);
     }
     return cudaGetLastError();
@@ -291,14 +333,12 @@ cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t*
 
 cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
                          size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
-                         cudaStream_t st) {
+                         const BatchLaunch& L, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    if (ws_bytes < batch_workspace_bytes(n, ntabs)) return cudaErrorInvalidValue;
-    BatchLaunch L;
-    L.stride = batch_stride(h_tabs, ntabs);
-    cudaError_t e = batch_configure(L);
-    if (e == cudaSuccess) e = batch_upload(h_tabs, ntabs, h_pair_tab, h_cls, n, ws, st);
-    if (e == cudaSuccess) e = batch_run(n, ntabs, str, off, out, ws, L, st, true);
+    const size_t base = batch_workspace_bytes(n, ntabs);
+    if (ws_bytes < base + batch_maps_bytes(L, n)) return cudaErrorInvalidValue;
+    cudaError_t e = batch_upload(h_tabs, ntabs, h_pair_tab, h_cls, n, ws, st);
+    if (e == cudaSuccess) e = batch_run(n, ntabs, str, off, out, ws, L, st, true, static_cast<uint8_t*>(ws) + base);
     return e;
 }
 

@@ -26,6 +26,7 @@ struct rx_batch {
     int device = -1;
     size_t n = 0, ntabs = 0;
     void* ws = nullptr;
+    uint8_t* maps = nullptr;  // chunk-map scratch, after the batch workspace in ws
     rx::BatchLaunch L;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -54,7 +55,7 @@ cudaError_t capture(rx_batch* b, const uint8_t* str, const int64_t* off, uint8_t
     drop_graph(b);
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t er = rx::batch_run(b->n, b->ntabs, str, off, out, b->ws, b->L, b->cap, false);
+    cudaError_t er = rx::batch_run(b->n, b->ntabs, str, off, out, b->ws, b->L, b->cap, false, b->maps);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->cap, &g);
     if (er != cudaSuccess) e = er;
@@ -92,7 +93,19 @@ rx_status rx_batch_prepare(const rx_handle* handles, size_t n, rx_batch** out) {
         b->ntabs = tabs.size();
         b->L.stride = rx::batch_stride(tabs.data(), tabs.size());
         cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-        if (e == cudaSuccess && n > 0) e = cudaMalloc(&b->ws, rx::batch_workspace_bytes(n, tabs.size()));
+        // chunk-map scratch for the largest resident grid of any block size
+        // the autotuner may pick
+        size_t maps = 0;
+        const int blocks[3] = {128, 256, 512};
+        for (int i = 0; i < 3 && e == cudaSuccess; i++) {
+            rx::BatchLaunch Lb = b->L;
+            Lb.block = blocks[i];
+            e = rx::batch_configure(Lb);
+            if (e == cudaSuccess) maps = std::max(maps, rx::batch_maps_bytes(Lb, n));
+        }
+        const size_t base = rx::batch_workspace_bytes(n, tabs.size());
+        if (e == cudaSuccess && n > 0) e = cudaMalloc(&b->ws, base + maps);
+        if (e == cudaSuccess && n > 0) b->maps = static_cast<uint8_t*>(b->ws) + base;
         if (e == cudaSuccess && n > 0)
             e = rx::batch_upload(tabs.data(), tabs.size(), pair_tab.data(), cls.data(), n, b->ws, b->cap);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
@@ -153,11 +166,12 @@ rx_status rx_batch_autotune(rx_batch* b, const uint8_t* strings, const int64_t* 
                     e = cudaSuccess;
                     continue;
                 }
-                if (e == cudaSuccess) e = rx::batch_run(b->n, b->ntabs, strings, offsets, out, b->ws, L, st, false);
+                if (e == cudaSuccess)
+                    e = rx::batch_run(b->n, b->ntabs, strings, offsets, out, b->ws, L, st, false, b->maps);
                 const int reps = 3;
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
                 for (int r = 0; r < reps && e == cudaSuccess; r++)
-                    e = rx::batch_run(b->n, b->ntabs, strings, offsets, out, b->ws, L, st, false);
+                    e = rx::batch_run(b->n, b->ntabs, strings, offsets, out, b->ws, L, st, false, b->maps);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;

@@ -65,11 +65,16 @@ int batch_stride(const BatchTab* h_tabs, size_t ntabs);
 cudaError_t batch_upload(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
                          size_t n, void* ws, cudaStream_t st);
 cudaError_t batch_configure(BatchLaunch& L);
+long long batch_grid(const BatchLaunch& L, size_t n);
+// scratch for the chunk maps of long pairs, after batch_workspace_bytes
+size_t batch_maps_bytes(const BatchLaunch& L, size_t n);
 cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws,
-                      const BatchLaunch& L, cudaStream_t st, bool profile);
+                      const BatchLaunch& L, cudaStream_t st, bool profile, uint8_t* maps);
+// L: stride set and batch_configure'd; ws: batch_workspace_bytes +
+// batch_maps_bytes
 cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
                          size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
-                         cudaStream_t st);
+                         const BatchLaunch& L, cudaStream_t st);
 // host arrays of a batch: distinct tables, table index and class per pair
 // (api.cpp); `who` prefixes error messages
 rx_status collect_pairs(const rx_handle* handles, size_t n, const char* who, std::vector<BatchTab>& tabs,
