@@ -491,6 +491,20 @@ def run_long(args, world, rank, local):
     rx.match_seq(r, d, pre, out, stream=stream)
     torch.cuda.synchronize(dev)
     assert int(out.item()) == agree_prefix
+    # chunked unanchored search over the same text for a literal planted
+    # near its end (the whole text is scanned), informational
+    search = None
+    lit = b"zqzqzq"
+    rs = rx.Regex.compile(lit, rx.COMPILE_SEARCH)
+    if rs.info()["search_states"]:
+        p = n - 1000
+        d[p:p + len(lit)] = torch.tensor(list(lit), dtype=torch.uint8, device=dev)
+        d_end = torch.empty(1, dtype=torch.int64, device=dev)
+        rx.search_long(rs, d, n, d_end, stream=stream)
+        sms = _time(lambda: rx.search_long(rs, d, n, d_end, stream=stream), max(3, args.steps), stream, dev)
+        search = {"GB/s": round(n / (sms * 1e-3) / 1e9, 1), "ms": round(sms, 4), "found_end": int(d_end.item()),
+                  "planted_end": p + len(lit)}
+    rs.free()
     peak, _ = peaks()
     # the two timed kernels of a step: phase 1 (k_chunk_stage) and phase 2
     # (k_span_tasks); composition and launch gaps are the rest of the step
@@ -507,7 +521,7 @@ def run_long(args, world, rank, local):
                          "achieved": round(n / (kernel_ms * 1e-3) / 1e9, 1), "peak": peak,
                          "frac": round(n / (kernel_ms * 1e-3) / 1e9 / peak, 4),
                          "step_frac": round(n / (ms * 1e-3) / 1e9 / peak, 4)},
-            "gpu_launches_per_step": launches / args.steps}
+            "gpu_launches_per_step": launches / args.steps, "search_long": search}
     if rank == 0:
         print(json.dumps(line))
 

@@ -259,6 +259,21 @@ rx_status rx_search(rx_handle h, size_t n, const uint8_t* strings, const int64_t
                     void* stream);
 
 /*
+ * rx_search_long -- rx_search on one long string, chunked (async).  Over the
+ * search cache, each chunk's effect on an incoming state is a pair (state at
+ * the chunk's end, end offset of its first accepting byte or none); pairs
+ * compose associatively, so chunks are computed in parallel and composed
+ * left to right, exactly as the one-string answer.
+ *   str DEVICE bytes [len]; chunk_bytes 0 = automatic, else >= 64;
+ *   out_end DEVICE int64[1] = earliest end of a matching substring, -1 if none.
+ * Errors: RX_ERR_INVALID_ARG, RX_ERR_UNSUPPORTED (no search cache),
+ * RX_ERR_TOO_LARGE (chunk size too small for this length), RX_ERR_OOM,
+ * RX_ERR_CUDA.
+ */
+rx_status rx_search_long(rx_handle h, const uint8_t* str, int64_t len, int64_t chunk_bytes, int64_t* out_end,
+                         void* stream);
+
+/*
  * rx_device_faults -- bounded device-side waits that gave up, counted on
  * the current device since the last reset (the streaming kernel that stages
  * input with bulk copies counts one per warp that stopped waiting for a

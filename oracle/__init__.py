@@ -13,6 +13,8 @@ and Operational Semantics" (SOS 2011):
 * ``o1_search`` -- unanchored search (not in the paper): the earliest end j
   of a substring w[i:j] that the expression matches, read off the same
   memoised tables of Fig 2.1 (``oracle.c``).
+* ``o2_search`` -- the same answer from the machine of Fig 6.1 with the root
+  pushed back at every macro step, for texts too long for O1 (``oracle.c``).
 * ``o2`` / ``o2_trace`` -- the sequential lockstep machine of Def 6.2 /
   Fig 6.1 with psi of Def 6.1 (``oracle.c``).
 * ``cont`` -- Def 4.4 (``oracle.c``).
@@ -77,6 +79,10 @@ def _L():
         lib.or_o1_search.restype = I64
         lib.or_o1_search_batch.argtypes = [P, I, I, P, P, I64, P, I64, I]
         lib.or_o1_search_batch.restype = I
+        lib.or_o2_search.argtypes = [P, I, I, P, I64]
+        lib.or_o2_search.restype = I64
+        lib.or_o2_search_batch.argtypes = [P, I, I, P, P, I64, P, I]
+        lib.or_o2_search_batch.restype = I
         _lib = lib
     return _lib
 
@@ -143,6 +149,29 @@ def o1_search_batch(nodes, data: np.ndarray, offsets: np.ndarray, root: int = 0,
         d = np.zeros(1, np.uint8)
     o = np.ascontiguousarray(offsets, np.int64)
     _L().or_o1_search_batch(_p(nd), len(nd), root, _p(d), _p(o), n, _p(out), max_bytes, threads)
+    return out[:n]
+
+
+def o2_search(nodes, w, root: int = 0) -> int:
+    """Unanchored search with the machine of Fig 6.1, the root pushed back at
+    every macro step: the earliest end of a matching substring, or -1."""
+    nd = _nodes(nodes)
+    b = _buf(w)
+    r = _L().or_o2_search(_p(nd), len(nd), root, _p(b), len(b) - 1)
+    if r == -2:
+        raise ValueError("malformed tree")
+    return int(r)
+
+
+def o2_search_batch(nodes, data: np.ndarray, offsets: np.ndarray, root: int = 0, threads: int = 0) -> np.ndarray:
+    nd = _nodes(nodes)
+    n = len(offsets) - 1
+    out = np.zeros(max(n, 1), np.int64)
+    d = np.ascontiguousarray(data, np.uint8)
+    if d.size == 0:
+        d = np.zeros(1, np.uint8)
+    o = np.ascontiguousarray(offsets, np.int64)
+    _L().or_o2_search_batch(_p(nd), len(nd), root, _p(d), _p(o), n, _p(out), threads)
     return out[:n]
 
 

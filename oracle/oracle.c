@@ -13,6 +13,8 @@
  *          closed under the rules, memoised over (node, start index).
  *   O1 search -- unanchored search from the same tables: the earliest end j
  *          of a substring w[i..j) with e |v w[i..j) (not in the paper).
+ *   O2 search -- the same answer from the machine of Fig 6.1 with the root
+ *          pushed back at every macro step (streaming; long texts).
  *   O2  -- the sequential lockstep machine <c; t; n; w> of Def 6.2 / Fig 6.1
  *          with the add-unique function psi of Def 6.1, over the pointer tree
  *          of Section 4 with the cont function of Def 4.4.
@@ -321,6 +323,73 @@ int or_o2(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, uint
     free(cont);
     free(buf);
     return r;
+}
+
+/* ------------------------------------------------------------ O2 search
+ * Unanchored search with the machine of Fig 6.1 (not in the paper): the
+ * root is pushed into c at the start of every macro step, so a match may
+ * begin at any position; the first time null is popped, at input position
+ * pos, pos is the earliest end of a matching substring.  -1 when the input
+ * is exhausted without null. */
+int64_t or_o2_search(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L) {
+    int32_t* cont = (int32_t*)malloc(sizeof(int32_t) * (size_t)nn);
+    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(6 * (nn + 1)));
+    if (!cont || !buf || or_cont(nd, nn, root, cont) != 0) { free(cont); free(buf); return -2; }
+    int cap = 2 * (nn + 1);
+    olist c = {buf, 0}, t = {buf + cap, 0}, n = {buf + 2 * cap, 0}, empty = {NULL, 0};
+    int32_t nul = nn;
+    int64_t pos = 0, res = -1;
+    c.a[c.len++] = root;
+    for (;;) {
+        if (c.len > 0) {
+            int32_t p = c.a[--c.len];
+            if (p == nul) {
+                res = pos;
+                break;
+            }
+            const or_node* x = &nd[p];
+            int32_t k = cont[p] < 0 ? nul : cont[p];
+            switch (x->kind) {
+            case ALT:
+                psi(x->l, &c, &t);
+                psi(x->r, &c, &t);
+                break;
+            case CAT:
+                psi(x->l, &c, &t);
+                break;
+            case STAR:
+                psi(x->l, &c, &t);
+                psi(k, &c, &t);
+                break;
+            case EPS:
+                psi(k, &c, &t);
+                break;
+            case CHAR:
+                if (pos < L && w[pos] == x->byte) psi(k, &n, &empty);
+                break;
+            }
+            t.a[t.len++] = p;
+            continue;
+        }
+        /* c = []: the next macro step, with the root added back */
+        if (pos >= L) break;
+        memcpy(c.a, n.a, sizeof(int32_t) * (size_t)n.len);
+        c.len = n.len;
+        t.len = 0;
+        n.len = 0;
+        pos++;
+        psi(root, &c, &t);
+    }
+    free(cont);
+    free(buf);
+    return res;
+}
+
+int or_o2_search_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const int64_t* off, int64_t n,
+                       int64_t* out, int nthreads) {
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    for (int64_t i = 0; i < n; i++) out[i] = or_o2_search(nd, nn, root, bytes + off[i], off[i + 1] - off[i]);
+    return 0;
 }
 
 /* ------------------------------------------------------------ batches

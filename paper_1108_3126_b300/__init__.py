@@ -89,6 +89,7 @@ SIGNATURES = {
     "rx_match_host": ([P, SZ, P, P, P, P], I32),
     "rx_device_faults": ([I32], I64),
     "rx_search": ([P, SZ, P, P, P, P], I32),
+    "rx_search_long": ([P, P, I64, I64, P, P], I32),
     "rx_match_batch": ([P, SZ, P, P, P, P], I32),
     "rx_match_pairs": ([P, SZ, P, P, P, P], I32),
     "rx_batch_prepare": ([P, SZ, ctypes.POINTER(P)], I32),
@@ -256,6 +257,12 @@ def search(rx: Regex, strings, offsets, out_end, n: int | None = None, stream=No
     if n is None:
         n = len(offsets) - 1
     _check(lib().rx_search(rx.handle, n, _ptr(strings), _ptr(offsets), _ptr(out_end), _stream(stream)))
+
+
+def search_long(rx: Regex, text, length: int, out_end, chunk_bytes: int = 0, stream=None):
+    """out_end[0] (int64, device) = earliest end of a matching substring of
+    one long device text, chunked (async; COMPILE_SEARCH handles)."""
+    _check(lib().rx_search_long(rx.handle, _ptr(text), length, chunk_bytes, _ptr(out_end), _stream(stream)))
 
 
 def device_faults(reset: bool = False) -> int:

@@ -418,6 +418,34 @@ rx_status rx_search(rx_handle h, size_t n, const uint8_t* strings, const int64_t
     RX_GUARD_END
 }
 
+rx_status rx_search_long(rx_handle h, const uint8_t* str, int64_t len, int64_t chunk_bytes, int64_t* out_end,
+                         void* stream) {
+    RX_GUARD_BEGIN
+    if (!h || h->host_only || !out_end || len < 0 || (len > 0 && !str) || chunk_bytes < 0 ||
+        (chunk_bytes > 0 && chunk_bytes < 64)) {
+        set_error("rx_search_long: bad argument (chunk_bytes 0 or >= 64)");
+        return RX_ERR_INVALID_ARG;
+    }
+    if (h->dev.srch_K <= 0) {
+        set_error("rx_search_long: no search cache (compile with RX_COMPILE_SEARCH; at most 192 states)");
+        return RX_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t C = chunk_bytes > 0 ? chunk_bytes : rx::search_long_chunk_auto(h->dev, len);
+    const size_t need = rx::search_long_workspace_bytes(h->dev, len, C);
+    if (need > (size_t(16) << 30)) {
+        set_error("rx_search_long: chunk size too small for this length (tables exceed 16 GiB)");
+        return RX_ERR_TOO_LARGE;
+    }
+    void* ws = nullptr;
+    rx_status s = get_workspace(st, need, &ws);
+    if (s != RX_OK) return s;
+    cudaError_t e = rx::launch_search_long(h->dev, str, len, C, out_end, ws, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rx_search_long launch");
+    return RX_OK;
+    RX_GUARD_END
+}
+
 int64_t rx_device_faults(int32_t reset) {
     cudaDeviceSynchronize();
     return (int64_t)rx::read_wait_faults(reset != 0);

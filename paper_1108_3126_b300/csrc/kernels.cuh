@@ -93,6 +93,19 @@ size_t search_workspace_bytes(size_t n);
 cudaError_t launch_search(const DevTables& t, size_t n, const uint8_t* str, const int64_t* off, int64_t* out,
                           void* ws, size_t ws_bytes, cudaStream_t st);
 
+// Tasks of the chunked search (stream.cu): from byte task_chunk * C + P to
+// the chunk's end or first accepting byte.
+cudaError_t launch_search_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
+                                const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
+                                uint16_t* res, int32_t* res_acc, unsigned* queue, long long max_tasks,
+                                cudaStream_t st);
+// Chunked search of one long text (long.cu): out[0] = earliest end of a
+// matching substring, -1 if none.
+int64_t search_long_chunk_auto(const DevTables& t, int64_t len);
+size_t search_long_workspace_bytes(const DevTables& t, int64_t len, int64_t C);
+cudaError_t launch_search_long(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t* out,
+                               void* ws, size_t ws_bytes, cudaStream_t st);
+
 // Chunked single-string mode (long.cu).
 bool long_supported(const DevTables& t);
 int64_t long_chunk_auto(const DevTables& t, int64_t len);

@@ -560,4 +560,305 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
     return cudaErrorInvalidValue;
 }
 
+
+// ------------------------------------------------------------ chunked search
+// Unanchored search of one long text (not in the paper): the earliest end j
+// of a substring the expression matches.  Over the search cache (the start
+// set added back after every byte), the effect of chunk j on an incoming
+// state k is a pair: the state at the chunk's end, and the end offset of the
+// first accepting byte in the chunk (none: -1).  Pairs compose as
+//   (f1, a1) then (f2, a2) = (f2 o f1, a1(k) if a1(k) >= 0 else
+//                             len1 + a2(f1(k)) if that is >= 0 else -1),
+// which is associative, so chunks are computed in parallel and composed
+// left to right; once a(k) is set, f(k) is never consulted.
+//   phase A: one thread per chunk runs every incoming state over the first
+//            P bytes, recording its first accept; the distinct states that
+//            have not accepted become tasks (one atomic add per 32 chunks)
+//   phase B: each task runs over the rest of its chunk (k_search_tasks)
+//   phase C: the first composition level gathers each chunk's pairs, later
+//            levels fold the blocks; the last pair applied to the start state
+//            is the answer
+namespace {
+
+constexpr int kSearchPrefix = 64;
+
+__global__ void __launch_bounds__(256) k_search_stage(const DevTables t, const uint8_t* __restrict__ str,
+                                                      int64_t len, int64_t C, long long J,
+                                                      uint16_t* __restrict__ slot, uint8_t* __restrict__ pacc,
+                                                      unsigned* __restrict__ toff, uint32_t* __restrict__ task_chunk,
+                                                      uint16_t* __restrict__ task_state,
+                                                      unsigned* __restrict__ ntask) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    SearchS::load(t, smem);
+    __syncthreads();
+    SearchS proto;
+    proto.bind(t, smem);
+    const int K = t.srch_K;
+    const int nt = blockDim.x, lane = threadIdx.x & 31;
+    uint8_t* stv = smem + align16(SearchS::smem_bytes(t)) + threadIdx.x;  // state reached (interleaved)
+    const long long wstride = (long long)gridDim.x * blockDim.x;
+    for (long long j0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < J; j0 += wstride) {
+        const long long j = j0 + lane;
+        const bool valid = j < J;
+        int nl = 0;
+        IdSet live;  // states reached by incoming states that have not accepted
+        if (valid) {
+            const int64_t cs = j * C, pe = min(cs + kSearchPrefix, min(cs + C, len));
+            const int n = (int)(pe - cs);
+            for (int k = 0; k < K; k++) {
+                SearchS st = proto;
+                st.set_state((uint32_t)k);
+                int a = -1;
+                for (int q = 0; q < n; q++) {
+                    st.step(__ldg(str + cs + q));
+                    if (st.accepted()) {
+                        a = q + 1;
+                        break;
+                    }
+                }
+                pacc[j * K + k] = a < 0 ? (uint8_t)0xFF : (uint8_t)a;
+                stv[k * nt] = (uint8_t)st.state_id();
+                if (a < 0) live.add(st.state_id());
+            }
+            nl = live.count();
+        }
+        int incl = nl;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += x;
+        }
+        unsigned base = 0;
+        if (lane == 31) base = atomicAdd(ntask, (unsigned)incl);
+        base = __shfl_sync(FULL, base, 31) + (unsigned)(incl - nl);
+        if (valid) {
+            // rank of each live state id = its task index
+            for (int k = 0; k < K; k++) {
+                const uint32_t v = stv[k * nt];
+                uint32_t r = 0;
+#pragma unroll
+                for (int w = 0; w < 6; w++) {
+                    const uint32_t x = live.word(w);
+                    r += __popc(w < (int)(v >> 5) ? x : (w == (int)(v >> 5) ? x & ((1u << (v & 31)) - 1u) : 0u));
+                }
+                slot[j * K + k] = pacc[j * K + k] != 0xFF ? (uint16_t)0xFFFF : (uint16_t)r;
+            }
+            int i = 0;
+#pragma unroll
+            for (int w = 0; w < 6; w++) {
+                uint32_t x = live.word(w);
+                while (x) {
+                    task_chunk[base + i] = (uint32_t)j;
+                    task_state[base + i] = (uint16_t)(w * 32 + __ffs(x) - 1);
+                    i++;
+                    x &= x - 1;
+                }
+            }
+            toff[j] = base;
+        }
+    }
+}
+
+// each chunk's pair for every incoming state: F = state at the chunk's end,
+// A = end offset of its first accepting byte (-1: none)
+__global__ void k_search_pairs(const uint16_t* __restrict__ slot, const uint8_t* __restrict__ pacc,
+                               const unsigned* __restrict__ toff, const uint16_t* __restrict__ res,
+                               const int32_t* __restrict__ res_acc, long long J, int K, uint16_t* __restrict__ F,
+                               int64_t* __restrict__ A) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < J * K;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint16_t r = slot[i];
+        if (r == 0xFFFF) {
+            F[i] = 0;
+            A[i] = pacc[i];
+        } else {
+            const unsigned q = toff[i / K] + r;
+            F[i] = res[q];
+            A[i] = res_acc[q];
+        }
+    }
+}
+
+// level of the composition: block b folds entries [b*G, min((b+1)*G, cnt))
+// (staged in shared memory) for every incoming state; entry lengths are li,
+// or, with li null, chunk lengths (C, the last one shorter)
+__global__ void k_search_compose(const uint16_t* __restrict__ Fi, const int64_t* __restrict__ Ai,
+                                 const int64_t* __restrict__ li, int64_t C, int64_t len, long long cnt, int K, int G,
+                                 uint16_t* __restrict__ Fo, int64_t* __restrict__ Ao, int64_t* __restrict__ lo_out) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    int64_t* sa = reinterpret_cast<int64_t*>(sm);             // [G*K]
+    int64_t* sl = sa + (size_t)G * K;                         // [G]
+    uint16_t* sf = reinterpret_cast<uint16_t*>(sl + G);       // [G*K]
+    const long long lo = (long long)blockIdx.x * G;
+    const long long hi = std::min<long long>(lo + G, cnt);
+    const int nb = (int)(hi - lo);
+    for (int i = threadIdx.x; i < nb * K; i += blockDim.x) {
+        sf[i] = Fi[lo * K + i];
+        sa[i] = Ai[lo * K + i];
+    }
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        sl[b] = li ? li[lo + b] : std::min<int64_t>(C, len - (lo + b) * C);
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        uint32_t x = (uint32_t)k;
+        int64_t a = -1, off = 0;
+        for (int b = 0; b < nb && a < 0; b++) {
+            const int64_t ab = sa[b * K + x];
+            if (ab >= 0) a = off + ab;
+            else x = sf[b * K + x];
+            off += sl[b];
+        }
+        Fo[(long long)blockIdx.x * K + k] = (uint16_t)x;
+        Ao[(long long)blockIdx.x * K + k] = a;
+    }
+    if (threadIdx.x == 0) {
+        int64_t L = 0;
+        for (int b = 0; b < nb; b++) L += sl[b];
+        lo_out[blockIdx.x] = L;
+    }
+}
+
+__global__ void k_search_finish(const DevTables t, const int64_t* __restrict__ A, int64_t* out) {
+    if (threadIdx.x != 0) return;
+    const uint32_t s0 = t.srch_start >> 8;
+    out[0] = s0 >= (uint32_t)t.srch_acc0 ? 0 : (A ? A[s0] : -1);
+}
+
+struct SearchLongWs {
+    uint16_t *slot, *task_state, *res, *fa, *fb, *fj;
+    int64_t* aj;
+    uint8_t* pacc;
+    int32_t* res_acc;
+    uint32_t* task_chunk;
+    unsigned *toff, *ctr;
+    int64_t *aa, *ab, *la, *lb;
+};
+
+size_t search_long_layout(long long J, int K, uint8_t* w, SearchLongWs* o) {
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t x = off;
+        off += al256(b);
+        return w ? w + x : nullptr;
+    };
+    const size_t JK = (size_t)J * K;
+    const long long B = (J + 1) / 2 + 1;  // entries of the first composition level at most
+    uint8_t* p_slot = take(JK * 2);
+    uint8_t* p_pacc = take(JK);
+    uint8_t* p_ts = take(JK * 2);
+    uint8_t* p_tc = take(JK * 4);
+    uint8_t* p_res = take(JK * 2);
+    uint8_t* p_racc = take(JK * 4);
+    uint8_t* p_toff = take((size_t)J * 4);
+    uint8_t* p_ctr = take(256);
+    uint8_t* p_fa = take((size_t)B * K * 2);
+    uint8_t* p_fb = take((size_t)B * K * 2);
+    uint8_t* p_aa = take((size_t)B * K * 8);
+    uint8_t* p_ab = take((size_t)B * K * 8);
+    uint8_t* p_la = take((size_t)B * 8);
+    uint8_t* p_lb = take((size_t)B * 8);
+    uint8_t* p_fj = take(JK * 2);
+    uint8_t* p_aj = take(JK * 8);
+    if (o) {
+        o->fj = reinterpret_cast<uint16_t*>(p_fj);
+        o->aj = reinterpret_cast<int64_t*>(p_aj);
+        o->slot = reinterpret_cast<uint16_t*>(p_slot);
+        o->pacc = p_pacc;
+        o->task_state = reinterpret_cast<uint16_t*>(p_ts);
+        o->task_chunk = reinterpret_cast<uint32_t*>(p_tc);
+        o->res = reinterpret_cast<uint16_t*>(p_res);
+        o->res_acc = reinterpret_cast<int32_t*>(p_racc);
+        o->toff = reinterpret_cast<unsigned*>(p_toff);
+        o->ctr = reinterpret_cast<unsigned*>(p_ctr);
+        o->fa = reinterpret_cast<uint16_t*>(p_fa);
+        o->fb = reinterpret_cast<uint16_t*>(p_fb);
+        o->aa = reinterpret_cast<int64_t*>(p_aa);
+        o->ab = reinterpret_cast<int64_t*>(p_ab);
+        o->la = reinterpret_cast<int64_t*>(p_la);
+        o->lb = reinterpret_cast<int64_t*>(p_lb);
+    }
+    return off;
+}
+
+}  // namespace
+
+int64_t search_long_chunk_auto(const DevTables& t, int64_t len) {
+    long long target = (long long)sm_count() * 1536 * 2;
+    int64_t C = (len + target - 1) / std::max<long long>(target, 1);
+    C = std::max<int64_t>(C, 1024);
+    return (C + 31) & ~int64_t(31);
+}
+
+size_t search_long_workspace_bytes(const DevTables& t, int64_t len, int64_t C) {
+    long long J = (len + C - 1) / C;
+    return search_long_layout(std::max(J, 1LL), std::max(t.srch_K, 1), nullptr, nullptr) + 256;
+}
+
+cudaError_t launch_search_long(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t* out,
+                               void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (t.srch_K <= 0 || C < kSearchPrefix) return cudaErrorInvalidValue;
+    if (ws_bytes < search_long_workspace_bytes(t, len, C)) return cudaErrorInvalidValue;
+    const long long J = len > 0 ? (len + C - 1) / C : 0;
+    if (J == 0) {
+        k_search_finish<<<1, 32, 0, st>>>(t, nullptr, out);
+        prof_count(1);
+        return cudaGetLastError();
+    }
+    const int K = t.srch_K;
+    SearchLongWs L;
+    search_long_layout(J, K, static_cast<uint8_t*>(ws), &L);
+    // phase A
+    const size_t tab = align16(SearchS::smem_bytes(t));
+    const int threads = 256;
+    const size_t sm = tab + (size_t)threads * K;
+    cudaError_t e = allow_smem(k_search_stage, sm);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_stage, threads, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = std::min<long long>((J + threads - 1) / threads, (long long)per_sm * sm_count());
+    e = cudaMemsetAsync(L.ctr, 0, 256, st);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps(st);
+        k_search_stage<<<(unsigned)std::max<long long>(grid, 1), threads, sm, st>>>(
+            t, str, len, C, J, L.slot, L.pacc, L.toff, L.task_chunk, L.task_state, L.ctr);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // phase B
+    e = launch_search_tasks(t, str, len, C, kSearchPrefix, L.task_chunk, L.task_state, L.ctr, L.res, L.res_acc,
+                            L.ctr + 1, J * K, st);
+    if (e != cudaSuccess) return e;
+    // phase C
+    long long g3 = std::min<long long>((J * K + 255) / 256, (long long)sm_count() * 16);
+    k_search_pairs<<<(unsigned)std::max<long long>(g3, 1), 256, 0, st>>>(L.slot, L.pacc, L.toff, L.res, L.res_acc, J,
+                                                                         K, L.fj, L.aj);
+    prof_count(1);
+    const int G = (int)std::max<size_t>(2, std::min<size_t>(256, (40 * 1024) / ((size_t)K * 10 + 8)));
+    const size_t csm = (size_t)G * K * 10 + (size_t)G * 8 + 16;
+    const uint16_t* fi = L.fj;
+    const int64_t* ai = L.aj;
+    const int64_t* li = nullptr;
+    uint16_t *fc = L.fa, *fn = L.fb;
+    int64_t *ac = L.aa, *an = L.ab, *lc = L.la, *ln = L.lb;
+    long long cnt = J;
+    do {
+        const long long nb = (cnt + G - 1) / G;
+        k_search_compose<<<(unsigned)nb, 64, csm, st>>>(fi, ai, li, C, len, cnt, K, G, fc, ac, lc);
+        prof_count(1);
+        fi = fc;
+        ai = ac;
+        li = lc;
+        std::swap(fc, fn);
+        std::swap(ac, an);
+        std::swap(lc, ln);
+        cnt = nb;
+    } while (cnt > 1);
+    ac = const_cast<int64_t*>(ai);
+    k_search_finish<<<1, 32, 0, st>>>(t, ac, out);
+    prof_count(1);
+    return cudaGetLastError();
+}
+
 }  // namespace rx

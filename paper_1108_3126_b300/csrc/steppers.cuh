@@ -419,6 +419,28 @@ struct MemoPairP {
     __device__ __forceinline__ void set_state(uint32_t s) { st = base + (s >> 3) * PLANE + (s & 7u) * 64u; }
 };
 
+// The search cache (the start set added back after every byte): rows of
+// 256 successors as shared addresses, like MemoS.  Accepting states have the
+// highest ids, so the test is one compare of the state's address.
+struct SearchS {
+    uint32_t st, base, thr;
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) { return (size_t)t.srch_K * 1024; }
+    __device__ static void load(const DevTables& t, uint8_t* sm) {
+        const uint32_t b = smem_addr(sm);
+        uint32_t* T = reinterpret_cast<uint32_t*>(sm);
+        for (int i = threadIdx.x; i < t.srch_K * 256; i += blockDim.x) T[i] = b + t.srch_T[i] * 4u;
+    }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        base = smem_addr(sm);
+        st = base + t.srch_start * 4u;
+        thr = base + (uint32_t)t.srch_acc0 * 1024u;
+    }
+    __device__ __forceinline__ void step(uint32_t c) { st = lds32(st + c * 4u); }
+    __device__ __forceinline__ bool accepted() const { return st >= thr; }
+    __device__ __forceinline__ uint32_t state_id() const { return (st - base) >> 10; }
+    __device__ __forceinline__ void set_state(uint32_t s) { st = base + s * 1024u; }
+};
+
 // register bitset (one word): desc[c] = {shift | mask << 8, shared address
 // of the byte's subset table}; entry x of that table is the new set.
 struct Thread1S {

@@ -340,25 +340,7 @@ __global__ void __launch_bounds__(1024, 1) k_stream_tma(const DevTables t, const
 // Unanchored search: the earliest end of a matching substring.  The same
 // rounds as k_stream over the search cache (the start set added back after
 // every byte, so a match may begin anywhere); a lane records the first byte
-// after which its state holds null and stops reading.  Accepting states
-// have the highest ids, so the test is one compare of the state's address.
-struct SearchS {
-    uint32_t st, base, thr;
-    __host__ __device__ static size_t smem_bytes(const DevTables& t) { return (size_t)t.srch_K * 1024; }
-    __device__ static void load(const DevTables& t, uint8_t* sm) {
-        const uint32_t b = smem_u32(sm);
-        uint32_t* T = reinterpret_cast<uint32_t*>(sm);
-        for (int i = threadIdx.x; i < t.srch_K * 256; i += blockDim.x) T[i] = b + t.srch_T[i] * 4u;
-    }
-    __device__ void bind(const DevTables& t, uint8_t* sm) {
-        base = smem_u32(sm);
-        st = base + t.srch_start * 4u;
-        thr = base + (uint32_t)t.srch_acc0 * 1024u;
-    }
-    __device__ __forceinline__ void step(uint32_t c) { st = lds32(st + c * 4u); }
-    __device__ __forceinline__ bool accepted() const { return st >= thr; }
-};
-
+// after which its state holds null and stops reading (SearchS).
 // steps over the bytes of a 32-byte block selected by mask; returns the
 // index of the first byte after which the state accepts (-1: none), and
 // stops stepping there
@@ -430,6 +412,75 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_search(const DevTables t, 
             blk += 64;
         }
         if (valid) out[id] = found;
+    }
+}
+
+// Tasks of the chunked search: task i starts the search cache in state
+// task_state[i] at byte task_chunk[i] * C + P of the text and runs to the end
+// of that chunk or to its first accepting byte; res_acc[i] = that byte's end
+// offset from the chunk start (-1: none), res[i] = the final state (only used
+// when there is no accept).  Tasks come chunk by chunk.
+__global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_search_tasks(const DevTables t, const uint8_t* __restrict__ str,
+                                                                 int64_t len, int64_t C, int64_t P,
+                                                                 const uint32_t* __restrict__ task_chunk,
+                                                                 const uint16_t* __restrict__ task_state,
+                                                                 const unsigned* __restrict__ ntask_p,
+                                                                 uint16_t* __restrict__ res,
+                                                                 int32_t* __restrict__ res_acc,
+                                                                 unsigned* __restrict__ queue) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    SearchS::load(t, smem);
+    __syncthreads();
+    SearchS proto;
+    proto.bind(t, smem);
+    const int lane = threadIdx.x & 31;
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    const long long n = *ntask_p;
+    const long long nround = (n + 31) / 32;
+    for (;;) {
+        unsigned r = 0;
+        if (lane == 0) r = atomicAdd(queue, 1u);
+        r = __shfl_sync(FULL, r, 0);
+        if ((long long)r >= nround) break;
+        const long long k = (long long)r * 32 + lane;
+        const bool valid = k < n;
+        uint64_t s = base, e = base, c0 = base;
+        SearchS st = proto;
+        if (valid) {
+            const int64_t j = task_chunk[k];
+            const int64_t lo = j * C, hi = min(lo + C, len);
+            c0 += (uint64_t)lo;
+            s += (uint64_t)min(lo + P, hi);
+            e += (uint64_t)hi;
+            st.set_state(task_state[k]);
+        }
+        int32_t acc = -1;
+        bool active = valid && s < e;
+        uint64_t blk = s & ~uint64_t(31);
+        Blk32 va = ld_blk(blk, active);
+        Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
+        while (__any_sync(FULL, active)) {
+            int hit = search32(st, va, valid_mask(blk, s, e, active));
+            if (active && hit >= 0) {
+                acc = (int32_t)(blk + hit - c0) + 1;
+                active = false;
+            }
+            if (active && blk + 32 >= e) active = false;
+            va = ld_blk(blk + 64, active && blk + 64 < e);
+            if (!__any_sync(FULL, active)) break;
+            hit = search32(st, vb, valid_mask(blk + 32, s, e, active));
+            if (active && hit >= 0) {
+                acc = (int32_t)(blk + 32 + hit - c0) + 1;
+                active = false;
+            }
+            if (active && blk + 64 >= e) active = false;
+            vb = ld_blk(blk + 96, active && blk + 96 < e);
+            blk += 64;
+        }
+        if (valid) {
+            res[k] = (uint16_t)st.state_id();
+            res_acc[k] = acc;
+        }
     }
 }
 
@@ -618,6 +669,27 @@ cudaError_t launch_search(const DevTables& t, size_t n, const uint8_t* str, cons
     cudaError_t e = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st, queue);
     if (e != cudaSuccess) return e;
     return launch_search_k(t, (long long)n, str, off, perm, out, queue, st);
+}
+
+cudaError_t launch_search_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
+                                const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
+                                uint16_t* res, int32_t* res_acc, unsigned* queue, long long max_tasks,
+                                cudaStream_t st) {
+    const size_t sm = SearchS::smem_bytes(t);
+    const int block = 256;
+    cudaError_t e = allow_smem(k_search_tasks, sm);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search_tasks, block, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = std::min<long long>((max_tasks + block - 1) / block, (long long)per_sm * sm_count());
+    {
+        ProfScope ps(st);
+        k_search_tasks<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, len, C, P, task_chunk,
+                                                                                 task_state, ntask_p, res, res_acc,
+                                                                                 queue);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,

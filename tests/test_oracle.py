@@ -280,3 +280,19 @@ def test_o1_search_closed_forms():
     assert oracle.o1_search(oracle.parse(b"\\e"), b"abc") == 0
     assert oracle.o1_search(oracle.parse(b"(a*)*b"), b"aaaa") == -1
     assert oracle.o1_search(oracle.parse(b"(a*)*b"), b"aaab") == 4
+
+
+def test_o2_search_equals_o1_search():
+    """The streaming search oracle (Fig 6.1 with the root re-pushed) against
+    the big-step one, which the tests above pin to brute force."""
+    rng = np.random.default_rng(0xB7)
+    for i, nodes in enumerate(small_regexes(150, 0xB8)):
+        words = [bytes(rng.choice(list(b"abc"), size=int(rng.integers(0, 60))).tolist()) for _ in range(30)]
+        pk = synth.pack(words)
+        a = oracle.o1_search_batch(nodes, pk.data, pk.offsets)
+        b = oracle.o2_search_batch(nodes, pk.data, pk.offsets)
+        assert (a == b).all(), (synth.to_pattern(nodes), np.nonzero(a != b)[0][:5])
+    # closed form on a long text
+    t = bytes(rng.choice(list(b"abc"), size=200000).tolist()) + b"xyz"
+    assert oracle.o2_search(oracle.parse(b"xyz"), t) == len(t)
+    assert oracle.o2_search(oracle.parse(b"xyzz"), t) == -1
