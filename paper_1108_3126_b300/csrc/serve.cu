@@ -190,6 +190,7 @@ struct rx_server {
     int device = 0;
     int64_t budget = 0, long_threshold = 1 << 20;
     static constexpr int kLongStreams = 4;
+    static constexpr int64_t kTickGrow = 8;
     static constexpr size_t kMaxLong = 32;
     cudaStream_t st = nullptr, copy_st = nullptr, long_st[kLongStreams] = {};
     int next_long = 0;
@@ -345,6 +346,11 @@ void rx_server::run() {
             peak_inflight = std::max<int64_t>(peak_inflight, inflight + (int64_t)longs.size());
         }
         if (inflight > 0) {
+            // a tick advances every request by `tick` bytes; with few requests
+            // in flight the GPU would idle between short ticks, so the tick
+            // grows (up to kTickGrow times) as the in-flight count falls
+            const int64_t grow = std::max<int64_t>(1, std::min<int64_t>(kTickGrow, kTickGrow / inflight));
+            const int64_t tick = cfg.tick_bytes * grow;
             Segs sg{};
             int k = 0, tasks = 0;
             for (int c = 0; c < kBatchClasses; c++) {
@@ -361,7 +367,7 @@ void rx_server::run() {
             int blocks = (tasks * 32 + 255) / 256;
             {
                 ProfScope ps(st);
-                k_serve_tick<<<blocks, 256, 0, st>>>(d_slots, d_order, sg, cfg.tick_bytes, d_state, d_status);
+                k_serve_tick<<<blocks, 256, 0, st>>>(d_slots, d_order, sg, tick, d_state, d_status);
             }
             cudaMemcpyAsync(h_status, d_status, 2 * (size_t)nslot, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
@@ -378,7 +384,7 @@ void rx_server::run() {
                     free_slots.push_back(i);
                     complete(r, h_status[2 * i + 1], e == cudaSuccess ? RX_OK : RX_ERR_CUDA);
                 } else {
-                    h_slots[i].pos = std::min(h_slots[i].len, h_slots[i].pos + cfg.tick_bytes);
+                    h_slots[i].pos = std::min(h_slots[i].len, h_slots[i].pos + tick);
                 }
             }
         } else if (!longs.empty()) {
