@@ -23,6 +23,12 @@
  *     caller synchronises before reading results.
  *   - Handles are owned by the library and released with rx_free(); all
  *     other buffers are owned by the caller.
+ *   - Threads: handles may be shared by threads for matching.  Calls that
+ *     use the library's per-stream scratch (rx_match*, rx_search*,
+ *     rx_match_batch, rx_match_long) may run concurrently on different
+ *     streams; calls on one stream from several host threads must be
+ *     serialised by the caller (the scratch can be regrown between them).
+ *     rx_match_host serialises itself per device.
  */
 #ifndef RX_H
 #define RX_H

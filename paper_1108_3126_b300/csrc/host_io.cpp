@@ -4,7 +4,9 @@
 // The batch is cut at string boundaries into pieces of about kPieceBytes.
 // Piece k is copied on a copy stream into staging buffer k % 2 while piece
 // k-1 is matched on the caller's stream; its booleans are copied back on the
-// caller's stream.  Events order the reuse of each staging buffer.  The
+// caller's stream.  Events order the reuse of each staging buffer; calls
+// on one device are serialised on the host (the copy stream and its events
+// are shared).  The
 // kernel reads a piece through a base pointer shifted by the piece's first
 // offset, so the caller's offsets are used unchanged.
 #include <algorithm>
@@ -30,6 +32,7 @@ constexpr int64_t kPieceMaxStrings = 1 << 20;
 struct CopyStream {
     cudaStream_t st = nullptr;
     cudaEvent_t ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    std::mutex call;  // one call at a time uses this stream and these events
 };
 std::mutex g_copy_mu;
 CopyStream g_copy[128];
@@ -108,6 +111,7 @@ extern "C" rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings
         CopyStream* cs = nullptr;
         s = copy_stream(&cs);
         if (s != RX_OK) return s;
+        std::lock_guard<std::mutex> call_lock(cs->call);
         uint8_t* w = static_cast<uint8_t*>(ws);
         uint8_t* d_buf[2] = {w, w + buf};
         int64_t* d_off[2] = {reinterpret_cast<int64_t*>(w + 2 * buf), reinterpret_cast<int64_t*>(w + 2 * buf + offb)};
