@@ -335,6 +335,12 @@ rx_status rx_match_pairs(const rx_handle* handles, size_t n, const uint8_t* stri
  *   timed with CUDA events on `stream`, and keeps the fastest for later
  *   runs; *chosen (optional) receives it and its rate.  Synchronous.
  *   Errors: as rx_batch_run.
+ * rx_batch_set_shape: sets the launch shape of later runs without timing
+ *   (e.g. one kept from an earlier rx_batch_autotune): shape->block is 128,
+ *   256 or 512; shape->long_pair_bytes >= 1 (cached pairs longer than it take
+ *   a warp); gb_per_s is ignored.  The next run captures anew.  Must not be
+ *   called while a run of the plan is being issued from another thread.
+ *   Errors: RX_ERR_INVALID_ARG (null, bad block or length), RX_ERR_CUDA.
  * rx_batch_free: releases the plan; no run of it may still be in flight.
  */
 typedef struct rx_batch* rx_batch_handle;
@@ -348,6 +354,7 @@ rx_status rx_batch_run(rx_batch_handle b, const uint8_t* strings, const int64_t*
                        void* stream);
 rx_status rx_batch_autotune(rx_batch_handle b, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
                             void* stream, rx_batch_tune* chosen);
+rx_status rx_batch_set_shape(rx_batch_handle b, const rx_batch_tune* shape);
 void rx_batch_free(rx_batch_handle b);
 
 /*

@@ -95,6 +95,7 @@ SIGNATURES = {
     "rx_batch_prepare": ([P, SZ, ctypes.POINTER(P)], I32),
     "rx_batch_run": ([P, P, P, P, P], I32),
     "rx_batch_autotune": ([P, P, P, P, P, ctypes.POINTER(BatchTune)], I32),
+    "rx_batch_set_shape": ([P, ctypes.POINTER(BatchTune)], I32),
     "rx_batch_free": ([P], None),
     "rx_match_long": ([P, P, I64, I64, P, P], I32),
     "rx_match_seq": ([P, P, I64, P, P], I32),
@@ -318,6 +319,11 @@ class Batch:
         _check(lib().rx_batch_autotune(self.handle, _ptr(strings), _ptr(offsets), _ptr(out), _stream(stream),
                                        ctypes.byref(t)))
         return {"long_pair_bytes": int(t.long_pair_bytes), "block": int(t.block), "gb_per_s": float(t.gb_per_s)}
+
+    def set_shape(self, block: int, long_pair_bytes: int):
+        """Fix the launch shape of later runs (e.g. one autotune() chose)."""
+        t = BatchTune(int(long_pair_bytes), int(block), 0.0)
+        _check(lib().rx_batch_set_shape(self.handle, ctypes.byref(t)))
 
     def free(self):
         if getattr(self, "handle", None):

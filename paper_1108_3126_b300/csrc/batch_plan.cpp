@@ -208,6 +208,27 @@ rx_status rx_batch_autotune(rx_batch* b, const uint8_t* strings, const int64_t* 
     return RX_OK;
 }
 
+rx_status rx_batch_set_shape(rx_batch* b, const rx_batch_tune* shape) {
+    if (!b || !shape || (shape->block != 128 && shape->block != 256 && shape->block != 512) ||
+        shape->long_pair_bytes < 1) {
+        rx::set_error("rx_batch_set_shape: null argument, block not 128/256/512, or long_pair_bytes < 1");
+        return RX_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(b->mu);
+    rx::BatchLaunch L = b->L;
+    L.block = shape->block;
+    L.long_bytes = shape->long_pair_bytes;
+    cudaError_t e = rx::batch_configure(L);
+    if (e == cudaSuccess && L.grid_cap < 1) e = cudaErrorInvalidValue;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "rx_batch_set_shape");
+    }
+    b->L = L;
+    drop_graph(b);
+    return RX_OK;
+}
+
 void rx_batch_free(rx_batch* b) {
     if (!b) return;
     {

@@ -42,7 +42,7 @@ size_t plan_workspace_bytes(size_t n, int nclasses);
 // kClsMemoLong (see below)
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
                         unsigned** starts, cudaStream_t st, unsigned* queue = nullptr,
-                        long long long_bytes = 8192);
+                        long long long_bytes = 4096);
 
 // Batched pairs (batch.cu).  Variant classes, in task order.
 struct BatchTab {
@@ -57,7 +57,7 @@ enum { kClsMemoLong = 0, kClsWarp = 1, kClsSparse8 = 2, kClsSparse4 = 3, kClsThr
 struct BatchLaunch {
     int stride = 0;               // chunk-map bytes per lane (largest cache, rounded to 16)
     int block = 256;              // threads per block: 128, 256 or 512
-    long long long_bytes = 8192;  // cached pairs longer than this take a warp
+    long long long_bytes = 4096;  // cached pairs longer than this take a warp
     long long grid_cap = 1;       // resident blocks (set by batch_configure)
 };
 size_t batch_workspace_bytes(size_t n, size_t ntabs);

@@ -194,7 +194,7 @@ def test_batched_edges():
 
 
 def test_batched_long_pairs_chunked_per_warp():
-    """Pairs longer than 8 KiB whose expression has a cache of macro steps run
+    """Pairs longer than 4 KiB (the default threshold) whose expression has a cache of macro steps run
     one warp per pair (32 chunks, exact transfer functions composed by lane
     0).  Mix them with short pairs of the same and other expressions."""
     rng = np.random.default_rng(0xE9)
@@ -313,8 +313,52 @@ def test_prepared_batch_graph_replay_recapture_and_autotune():
     b.run(d, o, outs[1])
     torch.cuda.synchronize()
     assert (outs[1].cpu().numpy() == want).all()
+    # shapes set by hand: every block size, never / always chunked
+    for block, lb in ((128, 1 << 40), (512, 1), (256, 3000)):
+        b.set_shape(block, lb)
+        outs[1].fill_(9)
+        b.run(d, o, outs[1])
+        torch.cuda.synchronize()
+        assert (outs[1].cpu().numpy() == want).all(), (block, lb)
+    for block, lb in ((64, 4096), (256, 0)):
+        with pytest.raises(rx.RxError):
+            b.set_shape(block, lb)
     b.free()
     # an empty prepared batch
     e = rx.Batch([])
     e.run(0, 0, 0)
     e.free()
+
+
+def test_batched_full_size_sampled():
+    """The batched workload at its full size (10,000 expressions, 148,077
+    pairs, 844 MB), run as the benchmark runs it: a prepared batch replaying
+    its captured graph, before and after the launch-shape autotuner, and the
+    unprepared call.  1500 random pairs and the 100 longest (the per-warp
+    chunked path) are checked one by one against O2; the three runs must
+    agree on every pair."""
+    w = synth.cfg_batched()
+    s = w.strings
+    assert s.n == 148077
+    lens = np.diff(s.offsets)
+    handles = [rx.Regex.from_nodes(nd) for nd in w.regexes]
+    hs = rx.handle_array([handles[i] for i in w.regex_of])
+    d, o = dev(s.data), dev(s.offsets)
+    outs = [torch.full((s.n,), 7, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    b = rx.Batch(hs)
+    b.run(d, o, outs[0])
+    b.autotune(d, o, outs[1])
+    outs[1].fill_(7)
+    b.run(d, o, outs[1])
+    b.free()
+    rx.match_batch(hs, d, o, outs[2])
+    torch.cuda.synchronize()
+    got = [x.cpu().numpy() for x in outs]
+    assert (got[0] == got[1]).all() and (got[0] == got[2]).all()
+    assert set(np.unique(got[0]).tolist()) <= {0, 1}
+    rng = np.random.default_rng(0x5A3)
+    idx = np.unique(np.concatenate([rng.choice(s.n, 1500, replace=False), np.argsort(lens, kind="stable")[-100:]]))
+    want = np.array([oracle.o2(w.regexes[w.regex_of[k]], s.get(k)) for k in idx], np.uint8)
+    bad = idx[got[0][idx] != want]
+    assert bad.size == 0, bad[:10]
+    assert 0 < want.sum() < len(want)

@@ -191,3 +191,14 @@ def test_search_cache_built_only_with_the_flag():
     # no cache without the macro-step cache either
     r3 = rx.Regex.compile(b"ab", rx.COMPILE_SEARCH | rx.COMPILE_NO_MEMO | rx.COMPILE_HOST_ONLY)
     assert r3.info()["search_states"] == 0
+
+
+def test_batch_entry_points_reject_null_arguments():
+    import ctypes
+    import paper_1108_3126_b300 as rx
+    L = rx.lib()
+    t = rx.BatchTune(4096, 256, 0.0)
+    assert L.rx_batch_set_shape(None, ctypes.byref(t)) == 2
+    assert L.rx_batch_run(None, None, None, None, None) == 2
+    assert L.rx_batch_autotune(None, None, None, None, None, None) == 2
+    L.rx_batch_free(None)
