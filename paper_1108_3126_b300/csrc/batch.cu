@@ -316,7 +316,7 @@ cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t*
     if (e != cudaSuccess) return e;
     uint32_t* perm = nullptr;
     unsigned* starts = nullptr;
-    e = launch_plan(off, b.cls, kBatchClasses, n, b.plan_ws, &perm, &starts, st, nullptr, L.long_bytes);
+    e = launch_plan(off, b.cls, kBatchClasses, n, b.plan_ws, &perm, &starts, st, nullptr, L.long_bytes, str);
     if (e != cudaSuccess) return e;
     const long long grid = batch_grid(L, n);
     if (profile) {

@@ -126,17 +126,23 @@ constexpr int kPlanThreads = 512;
 constexpr int kPlanItems = 4;
 constexpr int kPlanTile = kPlanThreads * kPlanItems;
 
+// span = the string's length plus its start's offset in its 32-byte block:
+// below 2 KiB the bucket is the number of 32-byte blocks the string
+// touches, so the lanes of a round start and end their strings in the same
+// iteration of the kernels' block loops
 __device__ __forceinline__ int len_bucket(int64_t len) {
-    if (len < 2048) return (int)(len >> 4);
+    if (len < 2048) return (int)((len + 31) >> 5);
     int lg = 63 - __clzll(len);  // >= 11
     int b = 128 + 4 * (lg - 11) + (int)((len >> (lg - 2)) & 3);
     return b < kLenBuckets ? b : kLenBuckets - 1;
 }
 
 // long_bytes: cached pairs longer than this go to kClsMemoLong
-__device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, long long i, long long long_bytes) {
-    const int64_t len = off[i + 1] - off[i];
-    int lb = len_bucket(len);
+// mis: the strings buffer's address mod 32
+__device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, long long i, long long long_bytes,
+                                        int mis) {
+    const int64_t o = off[i], len = off[i + 1] - o;
+    int lb = len_bucket(len > 0 ? len + ((o + mis) & 31) : 0);
     int c = cls ? (int)cls[i] : 0;
     if (cls && c == kClsMemo && len > long_bytes) c = kClsMemoLong;
     return c * kLenBuckets + (kLenBuckets - 1 - lb);
@@ -144,19 +150,19 @@ __device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, 
 
 // keys of the tile at `base` (-1 past hi)
 __device__ __forceinline__ void plan_tile_keys(const int64_t* off, const uint8_t* cls, long long base, long long hi,
-                                               long long long_bytes, int (&key)[kPlanItems]) {
+                                               long long long_bytes, int mis, int (&key)[kPlanItems]) {
 #pragma unroll
     for (int k = 0; k < kPlanItems; k++) {
         const long long i = base + k * kPlanThreads + threadIdx.x;
-        key[k] = i < hi ? plan_key(off, cls, i, long_bytes) : -1;
+        key[k] = i < hi ? plan_key(off, cls, i, long_bytes, mis) : -1;
     }
 }
 
 __device__ void plan_count(const int64_t* off, const uint8_t* cls, long long lo, long long hi, long long long_bytes,
-                           unsigned* sh) {
+                           int mis, unsigned* sh) {
     for (long long base = lo; base < hi; base += kPlanTile) {
         int key[kPlanItems];
-        plan_tile_keys(off, cls, base, hi, long_bytes, key);
+        plan_tile_keys(off, cls, base, hi, long_bytes, mis, key);
 #pragma unroll
         for (int k = 0; k < kPlanItems; k++)
             if (key[k] >= 0) atomicAdd(&sh[key[k]], 1u);
@@ -166,13 +172,14 @@ __device__ void plan_count(const int64_t* off, const uint8_t* cls, long long lo,
 __global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __restrict__ off,
                                                             const uint8_t* __restrict__ cls, long long n,
                                                             long long per, int nbk, unsigned* __restrict__ totals,
-                                                            unsigned* __restrict__ queue, long long long_bytes) {
+                                                            unsigned* __restrict__ queue, long long long_bytes,
+                                                            int mis) {
     extern __shared__ unsigned sh[];
     if (blockIdx.x == 0 && threadIdx.x == 0 && queue) *queue = 0;
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
     const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
-    plan_count(off, cls, lo, hi, long_bytes, sh);
+    plan_count(off, cls, lo, hi, long_bytes, mis, sh);
     __syncthreads();
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
         if (sh[b]) atomicAdd(&totals[b], sh[b]);
@@ -231,13 +238,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __
                                                                const unsigned* __restrict__ totals,
                                                                unsigned* __restrict__ cursor,
                                                                unsigned* __restrict__ starts,
-                                                               uint32_t* __restrict__ perm, long long long_bytes) {
+                                                               uint32_t* __restrict__ perm, long long long_bytes,
+                                                               int mis) {
     extern __shared__ unsigned sh[];  // [nbk] counts, then [nbk] bucket starts
     unsigned* sc = sh + nbk;
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
     __syncthreads();
     const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
-    plan_count(off, cls, lo, hi, long_bytes, sh);
+    plan_count(off, cls, lo, hi, long_bytes, mis, sh);
     plan_block_scan(totals, nbk, sc);
     if (blockIdx.x == 0)
         for (int b = threadIdx.x; b < nbk; b += kPlanThreads) starts[b] = sc[b];
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __
     __syncthreads();
     for (long long base = lo; base < hi; base += kPlanTile) {
         int key[kPlanItems];
-        plan_tile_keys(off, cls, base, hi, long_bytes, key);
+        plan_tile_keys(off, cls, base, hi, long_bytes, mis, key);
 #pragma unroll
         for (int k = 0; k < kPlanItems; k++)
             if (key[k] >= 0) perm[atomicAdd(&sh[key[k]], 1u)] = (uint32_t)(base + k * kPlanThreads + threadIdx.x);
@@ -426,7 +434,9 @@ size_t plan_workspace_bytes(size_t n, int nclasses) {
 }
 
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
-                        unsigned** starts, cudaStream_t st, unsigned* queue, long long long_bytes) {
+                        unsigned** starts, cudaStream_t st, unsigned* queue, long long long_bytes,
+                        const void* strings) {
+    const int mis = (int)(reinterpret_cast<uintptr_t>(strings) & 31);
     const int nbk = kLenBuckets * nclasses;  // at most 7 x 384 buckets: 21 KiB of shared memory in the scatter
     const int G = plan_blocks(n);
     long long per = ((long long)n + G - 1) / G;
@@ -439,9 +449,10 @@ cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, si
     *starts = st_out;
     cudaError_t e = cudaMemsetAsync(totals, 0, 2 * (size_t)nbk * 4, st);
     if (e != cudaSuccess) return e;
-    k_plan_hist<<<G, kPlanThreads, (size_t)nbk * 4, st>>>(off, cls, (long long)n, per, nbk, totals, queue, long_bytes);
+    k_plan_hist<<<G, kPlanThreads, (size_t)nbk * 4, st>>>(off, cls, (long long)n, per, nbk, totals, queue, long_bytes,
+                                                                 mis);
     k_plan_scatter<<<G, kPlanThreads, 2 * (size_t)nbk * 4, st>>>(off, cls, (long long)n, per, nbk, totals, cursor,
-                                                                 st_out, *perm, long_bytes);
+                                                                 st_out, *perm, long_bytes, mis);
     prof_count(2);
     return cudaGetLastError();
 }
@@ -479,7 +490,7 @@ cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_
     const int req_block = block;
     if (sort >= 1) {
         unsigned* starts = nullptr;
-        err = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st, queue);
+        err = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st, queue, 4096, str);
         if (err != cudaSuccess) return err;
         if (sort == 2) return launch_stream(t, variant, (long long)n, str, off, perm, out, queue, req_block, st);
     }

@@ -39,10 +39,11 @@ cudaError_t launch_stream(const DevTables& t, int variant, long long n, const ui
 // *starts (first slot of every bucket) inside ws.
 size_t plan_workspace_bytes(size_t n, int nclasses);
 // long_bytes: with classes, cached pairs longer than this are planned as
-// kClsMemoLong (see below)
+// kClsMemoLong (see below).  strings: the buffer the offsets index (only its
+// address mod 32 is used: below 2 KiB the length key counts 32-byte blocks)
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
-                        unsigned** starts, cudaStream_t st, unsigned* queue = nullptr,
-                        long long long_bytes = 4096);
+                        unsigned** starts, cudaStream_t st, unsigned* queue, long long long_bytes,
+                        const void* strings);
 
 // Batched pairs (batch.cu).  Variant classes, in task order.
 struct BatchTab {

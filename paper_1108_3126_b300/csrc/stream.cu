@@ -67,22 +67,77 @@ struct has_pairs<S, decltype(void(S::kPairs))> {
     static constexpr bool value = S::kPairs;
 };
 
+// byte i (0..31, any lane-dependent value) of the block
+__device__ __forceinline__ uint32_t byte_at(const Blk32& v, uint32_t i) {
+    const uint32_t q = i >> 2;
+    const uint32_t lo = q & 1u ? (q & 2u ? v.a.w : v.a.y) : (q & 2u ? v.a.z : v.a.x);
+    const uint32_t hi = q & 1u ? (q & 2u ? v.b.w : v.b.y) : (q & 2u ? v.b.z : v.b.x);
+    return byte_k(q & 4u ? hi : lo, (int)(i & 3u));
+}
+
+// bytes 4q..4q+3 of `mask` widened to 0x00 / 0xFF per byte
+__device__ __forceinline__ uint32_t byte_lanes(uint32_t mask, int q) {
+    return (((mask >> (4 * q)) & 0xFu) * 0x00204081u & 0x01010101u) * 0xFFu;
+}
+
+// A block whose valid bytes [lo, hi) do not fill it (the first or last
+// block of a string), with the two-byte table: an odd first byte alone,
+// then the pairs that lie inside the range, then an odd last byte alone.
+// Every lane issues every lookup; a lookup outside its range is dropped.
+template <class S>
+__device__ __forceinline__ void block32_pairs_masked(S& st, const Blk32& v, uint32_t mask) {
+    const uint32_t lo = mask ? (uint32_t)__ffs(mask) - 1u : 0u;
+    const uint32_t hi = mask ? 32u - (uint32_t)__clz(mask) : 0u;
+    {
+        S nx = st;
+        nx.step(byte_at(v, lo));
+        if (lo & 1u) st = nx;
+    }
+    const uint32_t lo2 = (lo + 1u) >> 1, hi2 = hi >> 1;  // pairs [lo2, hi2)
+    const uint32_t pm = ((1u << hi2) - 1u) & ~((1u << lo2) - 1u);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const uint32_t w = word_of(v, q);
+        S nx = st;
+        nx.step2(w);
+        if ((pm >> (2 * q)) & 1u) st = nx;
+        nx = st;
+        nx.step2(w >> 16);
+        if ((pm >> (2 * q + 1)) & 1u) st = nx;
+    }
+    S nx = st;
+    nx.step(byte_at(v, hi - 1u));
+    if (hi & 1u) st = nx;
+}
+
 template <class S>
 __device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
     if constexpr (has_pairs<S>::value) {
-        // two bytes per lookup when the block is whole and inside the window
-        // for every lane that still has bytes
+        // two bytes per lookup when every valid byte of every lane is inside
+        // the window; one vote decides between whole and partial blocks
+        const bool whole = mask == 0u || mask == 0xffffffffu;
         uint32_t out = 0;
+        if (whole) {
+            if (mask) {
 #pragma unroll
-        for (int q = 0; q < 8; q++) out |= st.out_of_window(word_of(v, q));
-        bool pair_ok = mask == 0u || (mask == 0xffffffffu && out == 0u);
-        if (__all_sync(FULL, pair_ok)) {
+                for (int q = 0; q < 8; q++) out |= st.out_of_window(word_of(v, q));
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++) out |= st.out_of_window(word_of(v, q)) & byte_lanes(mask, q);
+        }
+        const unsigned f = __reduce_or_sync(FULL, (whole ? 0u : 1u) | (out ? 2u : 0u));
+        if (f == 0u) {
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 uint32_t w = word_of(v, q);
                 st.step2(w);
                 st.step2(w >> 16);
             }
+            return;
+        }
+        if (f == 1u) {
+            block32_pairs_masked(st, v, mask);
             return;
         }
     }
@@ -107,8 +162,11 @@ __device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
     }
 }
 
+// the two-byte stepper is held to 40 registers: three 512-thread blocks
+// (48 warps) per SM, which its shared memory (up to 3 planes) also allows
 template <class S>
-__global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_stream(const DevTables t, const uint8_t* __restrict__ str,
+__global__ void __launch_bounds__(STREAM_MAX_BLOCK, has_pairs<S>::value ? 3 : 1)
+    k_stream(const DevTables t, const uint8_t* __restrict__ str,
                                                          const int64_t* __restrict__ off,
                                                          const uint32_t* __restrict__ perm, long long n,
                                                          uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
@@ -666,7 +724,7 @@ cudaError_t launch_search(const DevTables& t, size_t n, const uint8_t* str, cons
     unsigned* queue = reinterpret_cast<unsigned*>(w);
     uint32_t* perm = nullptr;
     unsigned* starts = nullptr;
-    cudaError_t e = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st, queue);
+    cudaError_t e = launch_plan(off, nullptr, 1, n, w + 256, &perm, &starts, st, queue, 4096, str);
     if (e != cudaSuccess) return e;
     return launch_search_k(t, (long long)n, str, off, perm, out, queue, st);
 }
