@@ -283,7 +283,9 @@ rx_status rx_search_long(rx_handle h, const uint8_t* str, int64_t len, int64_t c
  * rx_device_faults -- bounded device-side waits that gave up, counted on
  * the current device since the last reset (the streaming kernel that stages
  * input with bulk copies counts one per warp that stopped waiting for a
- * stage; that warp's strings of the round are left unwritten).  0 in normal
+ * stage; that warp's strings of the round are left unwritten; the
+ * one-launch length planner counts one per block that stopped waiting at
+ * its grid barrier, whose strings then keep their input order).  0 in normal
  * operation.  reset != 0 clears the counter after reading.  Synchronises
  * the device.  The paper has no counterpart.
  */

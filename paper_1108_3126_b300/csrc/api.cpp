@@ -448,7 +448,7 @@ rx_status rx_search_long(rx_handle h, const uint8_t* str, int64_t len, int64_t c
 
 int64_t rx_device_faults(int32_t reset) {
     cudaDeviceSynchronize();
-    return (int64_t)rx::read_wait_faults(reset != 0);
+    return (int64_t)rx::read_wait_faults(reset != 0) + (int64_t)rx::read_plan_faults(reset != 0);
 }
 
 rx_status rx_match(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,

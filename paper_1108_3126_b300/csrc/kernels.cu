@@ -118,6 +118,12 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
 //             contiguous range per bucket with one atomic add on a zeroed
 //             cursor, and places its strings there with shared-memory
 //             cursors
+// When every block can be resident at once (one tile of kPlanTile strings
+// per block) and the stream is not being captured, both passes run as ONE
+// cooperative launch (k_plan_one): the keys stay in registers across a grid
+// barrier, so the offsets are read once.  The barrier's wait is bounded; a
+// block that gives up counts a planner fault (rx_device_faults) and writes
+// the identity for its own tile, so every entry stays a valid index.
 // Each thread holds the keys of kPlanItems strings at a time, so the loads
 // of a tile are in flight together.  Within a bucket the order depends on
 // which block claims first; the kernels only need equal lengths within a
@@ -194,7 +200,7 @@ __device__ void plan_block_scan(const unsigned* __restrict__ in, int nbk, unsign
     for (int j = 0; j < per_t; j++) {
         const int b = t * per_t + j;
         if (b < nbk) {
-            const unsigned v = in[b];
+            const unsigned v = __ldcg(in + b);
             out[b] = v;
             sum += v;
         }
@@ -259,6 +265,76 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __
         for (int k = 0; k < kPlanItems; k++)
             if (key[k] >= 0) perm[atomicAdd(&sh[key[k]], 1u)] = (uint32_t)(base + k * kPlanThreads + threadIdx.x);
     }
+}
+
+__device__ unsigned g_plan_faults;
+constexpr unsigned kBarrierSpins = 1u << 22;  // x >= 64 ns: about a quarter of a second
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// all blocks of the (cooperative) grid arrive; false if the wait gave up
+__device__ bool grid_barrier(unsigned* bar) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        unsigned spins = 0;
+        while (ld_acquire(bar) < gridDim.x) {
+            if (++spins > kBarrierSpins) {
+                good = 0;
+                atomicAdd(&g_plan_faults, 1u);
+                break;
+            }
+            __nanosleep(64);
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_one(const int64_t* __restrict__ off,
+                                                           const uint8_t* __restrict__ cls, long long n, int nbk,
+                                                           unsigned* __restrict__ totals,
+                                                           unsigned* __restrict__ cursor, unsigned* __restrict__ bar,
+                                                           unsigned* __restrict__ starts,
+                                                           uint32_t* __restrict__ perm, unsigned* __restrict__ queue,
+                                                           long long long_bytes, int mis) {
+    extern __shared__ unsigned sh[];  // [nbk] counts, then [nbk] bucket starts
+    unsigned* sc = sh + nbk;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && queue) *queue = 0;
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kPlanTile;
+    int key[kPlanItems];
+    plan_tile_keys(off, cls, base, n, long_bytes, mis, key);
+#pragma unroll
+    for (int k = 0; k < kPlanItems; k++)
+        if (key[k] >= 0) atomicAdd(&sh[key[k]], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
+        if (sh[b]) atomicAdd(&totals[b], sh[b]);
+    if (!grid_barrier(bar)) {
+#pragma unroll
+        for (int k = 0; k < kPlanItems; k++)
+            if (key[k] >= 0) perm[base + k * kPlanThreads + threadIdx.x] = (uint32_t)(base + k * kPlanThreads + threadIdx.x);
+        return;
+    }
+    plan_block_scan(totals, nbk, sc);
+    if (blockIdx.x == 0)
+        for (int b = threadIdx.x; b < nbk; b += kPlanThreads) starts[b] = sc[b];
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
+        if (sh[b]) sh[b] = sc[b] + atomicAdd(&cursor[b], sh[b]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPlanItems; k++)
+        if (key[k] >= 0) perm[atomicAdd(&sh[key[k]], 1u)] = (uint32_t)(base + k * kPlanThreads + threadIdx.x);
 }
 
 // ------------------------------------------------------------- trace
@@ -427,11 +503,44 @@ int plan_blocks(size_t n) {
     return (int)std::max<long long>(1, std::min<long long>(g, (long long)sm_count() * 64));
 }
 
-// totals and claim cursors (zeroed together), bucket starts, permutation
+// totals, claim cursors and the grid-barrier counter (zeroed together),
+// bucket starts, permutation
 size_t plan_workspace_bytes(size_t n, int nclasses) {
     size_t nbk = (size_t)kLenBuckets * nclasses;
-    return align16(2 * nbk * 4) + align16(nbk * 4) + align16(n * 4);
+    return align16((2 * nbk + 1) * 4) + align16(nbk * 4) + align16(n * 4);
 }
+
+unsigned read_plan_faults(bool reset) {
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_plan_faults, sizeof(v));
+    if (reset) {
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(g_plan_faults, &z, sizeof(z));
+    }
+    return v;
+}
+
+namespace {
+// blocks of k_plan_one that fit on the device at once (per device, cached)
+long long plan_one_capacity(size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, long long> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({dev, smem});
+    if (it != cache.end()) return it->second;
+    int coop = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_one, kPlanThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    const long long cap = coop ? (long long)per_sm * sm_count() : 0;
+    cache[{dev, smem}] = cap;
+    return cap;
+}
+}  // namespace
 
 cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, size_t n, void* ws, uint32_t** perm,
                         unsigned** starts, cudaStream_t st, unsigned* queue, long long long_bytes,
@@ -444,11 +553,37 @@ cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, si
     uint8_t* w = static_cast<uint8_t*>(ws);
     unsigned* totals = reinterpret_cast<unsigned*>(w);
     unsigned* cursor = totals + nbk;
-    unsigned* st_out = reinterpret_cast<unsigned*>(w + align16(2 * (size_t)nbk * 4));
-    *perm = reinterpret_cast<uint32_t*>(w + align16(2 * (size_t)nbk * 4) + align16((size_t)nbk * 4));
+    unsigned* bar = cursor + nbk;
+    const size_t head = align16((2 * (size_t)nbk + 1) * 4);
+    unsigned* st_out = reinterpret_cast<unsigned*>(w + head);
+    *perm = reinterpret_cast<uint32_t*>(w + head + align16((size_t)nbk * 4));
     *starts = st_out;
-    cudaError_t e = cudaMemsetAsync(totals, 0, 2 * (size_t)nbk * 4, st);
+    cudaError_t e = cudaMemsetAsync(totals, 0, (2 * (size_t)nbk + 1) * 4, st);
     if (e != cudaSuccess) return e;
+    // one cooperative launch when every tile gets its own resident block
+    const long long tiles = ((long long)n + kPlanTile - 1) / kPlanTile;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {  // unknown: take the two-launch form
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    const size_t sm1 = 2 * (size_t)nbk * 4;
+    if (cs == cudaStreamCaptureStatusNone && tiles >= 1 && tiles <= plan_one_capacity(sm1)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)tiles);
+        cfg.blockDim = dim3(kPlanThreads);
+        cfg.dynamicSmemBytes = sm1;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_plan_one, off, cls, (long long)n, nbk, totals, cursor, bar, st_out, *perm,
+                               queue, long_bytes, mis);
+        prof_count(1);
+        return e;
+    }
     k_plan_hist<<<G, kPlanThreads, (size_t)nbk * 4, st>>>(off, cls, (long long)n, per, nbk, totals, queue, long_bytes,
                                                                  mis);
     k_plan_scatter<<<G, kPlanThreads, 2 * (size_t)nbk * 4, st>>>(off, cls, (long long)n, per, nbk, totals, cursor,

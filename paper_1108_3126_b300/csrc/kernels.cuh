@@ -138,6 +138,8 @@ cudaError_t paper_match_one(const DevTables& t, const uint8_t* str, int64_t len,
 // Waits of the bulk-copy streaming kernel that gave up (a device-wide
 // counter; optionally cleared).
 unsigned read_wait_faults(bool reset);
+// Grid barriers of the one-launch planner that gave up (likewise).
+unsigned read_plan_faults(bool reset);
 
 // Device properties cached per device.
 int sm_count();

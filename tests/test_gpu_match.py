@@ -343,3 +343,24 @@ def test_host_buffers_edges_and_errors():
         rx.match_host(r, np.zeros(8, np.uint8), bad, np.zeros(2, np.uint8))
     assert ei.value.status == 2
     assert (run(r, synth.pack([b"aa", b"b"])) == np.array([1, 0])).all()
+
+
+def test_planner_one_launch_and_two_launch_forms():
+    """The length planner runs as one cooperative launch when every tile of
+    2048 strings gets a resident block, else as two launches.  1,300,000
+    short strings take the two-launch form, their first 600,000 the one-launch
+    form; both equal the unplanned order on every string and O2 on a sample,
+    with no barrier wait that gave up."""
+    w = synth.cfg_small(n=8)
+    nodes = w.regexes[0]
+    r = rx.Regex.from_nodes(nodes)
+    big = synth.gen_strings(nodes, 1300000, 0, 80, synth.LOWER, synth.item_seed(0xA7, 1), p_lang=0.5)
+    rx.device_faults(reset=True)
+    for n in (600000, 1300000):
+        s = big if n == big.n else synth.Strings(big.data[:big.offsets[n]], big.offsets[:n + 1], big.kind[:n], 0)
+        planned = run(r, s)
+        assert (planned == run(r, s, sort=0)).all(), n
+        idx = np.sort(np.random.default_rng(n).choice(n, 3000, replace=False))
+        sub = synth.pack([s.get(int(i)) for i in idx])
+        assert (planned[idx] == oracle.o2_batch(nodes, sub.data, sub.offsets)).all(), n
+    assert rx.device_faults() == 0
