@@ -45,10 +45,10 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
 # capture, keyed by a hash of that kernel's sources at capture time (null
-# when they have changed since).  k_stream<MemoPairP>: 133.59 MB per launch
+# when they have changed since).  k_stream<MemoPairP>: 132.32 MB per launch
 # on the 262,144-string capture (136.81 MB algorithmic), scaled by
-# algorithmic bytes to the full 1,048,576-string launch (546.80 MB): 533.9 MB.
-TRAFFIC = {("k_stream<MemoPairP>", "9ece4bf1f871035a"): 533.9e6}
+# algorithmic bytes to the full 1,048,576-string launch (546.80 MB): 528.9 MB.
+TRAFFIC = {("k_stream<MemoPairP>", "ac5543bab85b5f67"): 528.9e6}
 
 
 def kernel_source_hash() -> str:

@@ -301,8 +301,7 @@ __device__ bool grid_barrier(unsigned* bar) {
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan_one(const int64_t* __restrict__ off,
                                                            const uint8_t* __restrict__ cls, long long n, int nbk,
-                                                           unsigned* __restrict__ totals,
-                                                           unsigned* __restrict__ cursor, unsigned* __restrict__ bar,
+                                                           unsigned* __restrict__ totals, unsigned* __restrict__ bar,
                                                            unsigned* __restrict__ starts,
                                                            uint32_t* __restrict__ perm, unsigned* __restrict__ queue,
                                                            long long long_bytes, int mis) {
@@ -318,8 +317,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_one(const int64_t* __rest
     for (int k = 0; k < kPlanItems; k++)
         if (key[k] >= 0) atomicAdd(&sh[key[k]], 1u);
     __syncthreads();
+    // adding to the totals also claims this block's range inside each bucket
+    // (the value returned), so only the scan is left after the barrier
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
-        if (sh[b]) atomicAdd(&totals[b], sh[b]);
+        if (sh[b]) sh[b] = atomicAdd(&totals[b], sh[b]);
     if (!grid_barrier(bar)) {
 #pragma unroll
         for (int k = 0; k < kPlanItems; k++)
@@ -329,8 +330,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_one(const int64_t* __rest
     plan_block_scan(totals, nbk, sc);
     if (blockIdx.x == 0)
         for (int b = threadIdx.x; b < nbk; b += kPlanThreads) starts[b] = sc[b];
-    for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
-        if (sh[b]) sh[b] = sc[b] + atomicAdd(&cursor[b], sh[b]);
+    for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] += sc[b];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kPlanItems; k++)
@@ -579,8 +579,8 @@ cudaError_t launch_plan(const int64_t* off, const uint8_t* cls, int nclasses, si
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_plan_one, off, cls, (long long)n, nbk, totals, cursor, bar, st_out, *perm,
-                               queue, long_bytes, mis);
+        e = cudaLaunchKernelEx(&cfg, k_plan_one, off, cls, (long long)n, nbk, totals, bar, st_out, *perm, queue,
+                               long_bytes, mis);
         prof_count(1);
         return e;
     }
