@@ -30,16 +30,27 @@ static_assert(kMemoMaxStates <= 256, "chunk maps hold cache state ids in one byt
 
 // one lane, bytes [s, e) (absolute addresses), cache state st (id * 256),
 // one-byte table T in global memory; stops when the set is empty
+// (the next 16-byte block is loaded while the current one is stepped)
 __device__ uint32_t lane_memo_run(const uint8_t* __restrict__ T, uint32_t st, uint64_t s, uint64_t e) {
     uint64_t blk = s & ~uint64_t(15);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (blk < e && st != 0) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
     while (blk < e && st != 0) {
-        uint4 v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
+        const uint64_t nb = blk + 16;
+        uint4 vn = make_uint4(0, 0, 0, 0);
+        if (nb < e) vn = ld_stream(reinterpret_cast<const uint8_t*>(nb));
+        if (blk >= s && nb <= e) {
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
-            uint64_t p = blk + k;
-            if (p >= s && p < e) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
+            for (int k = 0; k < 16; k++) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const uint64_t q = blk + k;
+                if (q >= s && q < e) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
+            }
         }
-        blk += 16;
+        blk = nb;
+        v = vn;
     }
     return st;
 }
@@ -71,13 +82,26 @@ __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8
     const uint64_t pe = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
     uint8_t* map = wsm + lane * stride;
     uint8_t* dv = wsm + (32 + lane) * stride;
-    // first stage: every incoming state
+    // first stage: every incoming state over the chunk's first (up to) 4
+    // bytes, read once; the states are independent, two in flight
     uint64_t pos = cs + 4 < pe ? cs + 4 : pe;
+    const int nb = (int)(pos - cs);
+    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    if (nb > 0) b0 = __ldg(reinterpret_cast<const uint8_t*>(cs));
+    if (nb > 1) b1 = __ldg(reinterpret_cast<const uint8_t*>(cs + 1));
+    if (nb > 2) b2 = __ldg(reinterpret_cast<const uint8_t*>(cs + 2));
+    if (nb > 3) b3 = __ldg(reinterpret_cast<const uint8_t*>(cs + 3));
     uint32_t bm[kBmWords];
 #pragma unroll
     for (int w = 0; w < kBmWords; w++) bm[w] = 0;
+#pragma unroll 2
     for (int k = 0; k < K; k++) {
-        const uint32_t v = lane_memo_run(T, (uint32_t)k * 256u, cs, pos) >> 8;
+        uint32_t st = (uint32_t)k * 256u;
+        if (nb > 0) st = (uint32_t)__ldg(T + st + b0) << 8;
+        if (nb > 1) st = (uint32_t)__ldg(T + st + b1) << 8;
+        if (nb > 2) st = (uint32_t)__ldg(T + st + b2) << 8;
+        if (nb > 3) st = (uint32_t)__ldg(T + st + b3) << 8;
+        const uint32_t v = st >> 8;
         map[k] = (uint8_t)v;
         bm_set(bm, v);
     }
