@@ -53,8 +53,11 @@ struct BatchTab {
 // the device by the planner from the pair's length), one warp per pair,
 // chunked.
 constexpr int kBatchClasses = 7;
-enum { kClsMemoLong = 0, kClsWarp = 1, kClsSparse8 = 2, kClsSparse4 = 3, kClsThread2 = 4, kClsThread1 = 5,
-       kClsMemo = 6 };
+// Task order (longest serial work per lane first): the classes whose lanes
+// walk a whole string, the cached pairs up to long_bytes, then the long
+// cached pairs, whose lanes walk 1/32 of one.
+enum { kClsWarp = 0, kClsSparse8 = 1, kClsSparse4 = 2, kClsThread2 = 3, kClsThread1 = 4, kClsMemo = 5,
+       kClsMemoLong = 6 };
 struct BatchLaunch {
     int stride = 0;               // chunk-map bytes per lane (largest cache, rounded to 16)
     int block = 256;              // threads per block: 128, 256 or 512
