@@ -242,8 +242,12 @@ rx_status rx_match_static(rx_handle h, size_t n, const uint8_t* strings, const i
  * Device scratch: two staging buffers of the largest piece plus the
  * planner's workspace, from the per-stream scratch buffer rx_match uses.
  * Returns when `out` is written (the stream is synchronised).
+ * Each piece's offsets are checked just before its copy is queued, so the
+ * checks overlap the copies of earlier pieces.
  * Errors: RX_ERR_INVALID_ARG (null handle/pointer, decreasing or negative
- * offsets; nothing copied), RX_ERR_OOM, RX_ERR_CUDA.
+ * offsets: the pieces before the first bad one may already have their
+ * booleans in `out`, the rest of `out` is untouched), RX_ERR_OOM,
+ * RX_ERR_CUDA.
  */
 rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
                         void* stream);

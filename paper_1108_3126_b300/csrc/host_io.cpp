@@ -61,6 +61,30 @@ rx_status copy_stream(CopyStream** out) {
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
+rx_status bad_offsets(size_t i) {
+    rx::set_error("rx_match_host: offsets decrease (or are negative) at " + std::to_string(i));
+    return RX_ERR_INVALID_ARG;
+}
+
+// first i in [i0, i1) with offsets[i + 1] < offsets[i] or < 0 (offsets[i0]
+// >= 0 is known), else -1.  A branch-free pass per block of 4096 (it
+// vectorises): with every offset >= 0 a difference has its sign bit set
+// exactly when it is negative.
+size_t first_decrease(const int64_t* offsets, size_t i0, size_t i1) {
+    for (size_t b = i0; b < i1; b += 4096) {
+        const size_t e = std::min(i1, b + 4096);
+        uint64_t acc = 0;
+        for (size_t i = b; i < e; i++) {
+            const uint64_t hi = (uint64_t)offsets[i + 1], lo = (uint64_t)offsets[i];
+            acc |= hi | (hi - lo);
+        }
+        if (acc >> 63)
+            for (size_t i = b; i < e; i++)
+                if (offsets[i + 1] < 0 || offsets[i + 1] < offsets[i]) return i;
+    }
+    return (size_t)-1;
+}
+
 }  // namespace
 
 extern "C" rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets,
@@ -75,18 +99,21 @@ extern "C" rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings
             rx::set_error("rx_match_host: null argument");
             return RX_ERR_INVALID_ARG;
         }
-        for (size_t i = 0; i < n; i++)
-            if (offsets[i + 1] < offsets[i] || offsets[i] < 0) {
-                rx::set_error("rx_match_host: offsets decrease at " + std::to_string(i));
-                return RX_ERR_INVALID_ARG;
-            }
-        // pieces at string boundaries
+        // pieces at string boundaries, found by binary search on the offsets
+        // (each piece's offsets are checked just before its copy is queued,
+        // so the checks of later pieces overlap the copies of earlier ones;
+        // the cut points themselves are checked here, as they size the
+        // staging buffers)
         std::vector<size_t> cut{0};
         int64_t max_bytes = 0;
         size_t max_n = 0;
+        if (offsets[0] < 0) return bad_offsets(0);
         for (size_t i = 0; i < n;) {
-            size_t j = i + 1;
-            while (j < n && offsets[j + 1] - offsets[i] <= kPieceBytes && (int64_t)(j - i) < kPieceMaxStrings) j++;
+            const size_t hi = std::min(n, i + (size_t)kPieceMaxStrings);
+            size_t j = (size_t)(std::upper_bound(offsets + i + 1, offsets + hi + 1, offsets[i] + kPieceBytes) -
+                                offsets) - 1;
+            if (j <= i) j = i + 1;  // a string longer than a piece is a piece
+            if (offsets[j] < offsets[i]) return bad_offsets(i);
             max_bytes = std::max<int64_t>(max_bytes, offsets[j] - offsets[i]);
             max_n = std::max(max_n, j - i);
             cut.push_back(j);
@@ -120,9 +147,12 @@ extern "C" rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings
         // the copy stream starts after everything already on the caller's stream
         cudaError_t e = cudaEventRecord(cs->freed[0], st);
         if (e == cudaSuccess) e = cudaEventRecord(cs->freed[1], st);
+        size_t bad = (size_t)-1;
         for (size_t k = 0; k + 1 < cut.size() && e == cudaSuccess; k++) {
             const int b = (int)(k & 1);
             const size_t i0 = cut[k], i1 = cut[k + 1];
+            bad = first_decrease(offsets, i0, i1);
+            if (bad != (size_t)-1) break;
             const int64_t o0 = offsets[i0], bytes = offsets[i1] - o0;
             e = cudaStreamWaitEvent(cs->st, cs->freed[b], 0);
             if (e == cudaSuccess && bytes > 0)
@@ -142,10 +172,12 @@ extern "C" rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings
             if (e == cudaSuccess) e = cudaEventRecord(cs->freed[b], st);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs->st);
         if (e != cudaSuccess) {
             rx::set_error(std::string("rx_match_host: ") + cudaGetErrorString(e));
             return RX_ERR_CUDA;
         }
+        if (bad != (size_t)-1) return bad_offsets(bad);
         return RX_OK;
     } catch (...) {
         rx::set_error("rx_match_host: host allocation failed");

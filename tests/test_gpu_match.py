@@ -342,6 +342,21 @@ def test_host_buffers_edges_and_errors():
     with pytest.raises(rx.RxError) as ei:
         rx.match_host(r, np.zeros(8, np.uint8), bad, np.zeros(2, np.uint8))
     assert ei.value.status == 2
+    for neg in (np.array([-1, 0], np.int64), np.array([0, 2, -1], np.int64)):
+        with pytest.raises(rx.RxError) as ei:
+            rx.match_host(r, np.zeros(8, np.uint8), neg, np.zeros(len(neg) - 1, np.uint8))
+        assert ei.value.status == 2
+    # a decrease in the second piece (pieces hold 2^20 strings): the error is
+    # reported after the first piece was queued; the second piece is untouched
+    n = (1 << 20) + 16
+    offs = np.zeros(n + 1, np.int64)
+    offs[(1 << 20) + 5:] = 5
+    offs[(1 << 20) + 6] = 3
+    got = np.full(n, 7, np.uint8)
+    with pytest.raises(rx.RxError) as ei:
+        rx.match_host(r, np.zeros(16, np.uint8), offs, got)
+    assert ei.value.status == 2
+    assert set(np.unique(got[:1 << 20]).tolist()) <= {1, 7} and (got[1 << 20:] == 7).all()
     assert (run(r, synth.pack([b"aa", b"b"])) == np.array([1, 0])).all()
 
 
