@@ -406,7 +406,11 @@ typedef struct {
     int32_t device_payload;      /* 1: submit() bytes are device pointers  */
     int32_t long_threshold;      /* requests longer than this (bytes) run
                                     the chunked mode (rx_match_long) on
-                                    their own streams; 0 = 64 KiB          */
+                                    their own streams; 0 = 32 MiB.  Below
+                                    it, a request with a cache of macro
+                                    steps and more than 2 ticks left takes
+                                    a warp per tick and advances 32 ticks'
+                                    bytes (chunk transfer functions)        */
 } rx_serve_cfg;
 
 typedef struct {

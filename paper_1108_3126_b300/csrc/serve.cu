@@ -11,9 +11,13 @@
 //   3. reads back the slots' done flags and results, completes finished
 //      requests (latency = completion - submission) and frees their memory.
 // Requests arriving while a tick runs join at the next tick, so their work
-// overlaps on the device with requests already in flight.  Requests longer
-// than long_threshold run the exact chunked mode (long.cu) on their own
-// stream and complete when its event fires.
+// overlaps on the device with requests already in flight.  A request with a
+// cache of macro steps and more than 2 ticks of bytes left takes a whole
+// warp in that tick: 32 lanes advance 32 consecutive spans of tick bytes as
+// chunk transfer functions composed from the saved state (exact, Def 5.2
+// acts on states), so long requests move 32 times as far per tick.
+// Requests longer than long_threshold run the exact chunked mode (long.cu)
+// on their own stream and complete when its event fires.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -37,6 +41,7 @@ namespace {
 using namespace rx::dev;
 
 constexpr int kStateWords = kWarpMaxWords;  // saved set per slot (words)
+constexpr int kMapStride = (kMemoMaxStates + 15) & ~15;  // chunk-map row per lane of a long slot
 
 struct ServeSlot {
     const DevTables* tab;
@@ -112,6 +117,26 @@ __device__ void tick_warp(const ServeSlot& sl, int64_t tick, uint32_t* state, ui
     }
 }
 
+// a cached request with many bytes left: the warp advances it by up to 32
+// spans of `tick` bytes (32 chunks) from its saved state; wsm: the slot's
+// chunk-map scratch (64 rows of kMapStride bytes)
+__device__ void tick_memo_long(const ServeSlot& sl, int64_t tick, uint32_t* state, uint8_t* status, uint8_t* wsm) {
+    const DevTables& t = *sl.tab;
+    const int lane = threadIdx.x & 31;
+    const uint32_t x0 = sl.pos > 0 ? state[0] >> 8 : t.memo_start >> 8;
+    const uint64_t base = reinterpret_cast<uint64_t>(sl.data);
+    const int64_t end = min(sl.len, sl.pos + 32 * tick);
+    const uint32_t x = warp_chunked_memo(t.memo_T8, t.memo_K, x0, base + sl.pos, base + end, wsm, kMapStride);
+    if (lane != 0) return;
+    if (end >= sl.len || x == 0) {
+        status[0] = 1;
+        status[1] = end >= sl.len ? t.memo_acc[x] : 0;
+    } else {
+        state[0] = x << 8;
+        status[0] = 0;
+    }
+}
+
 struct Segs {
     int32_t lo[kBatchClasses + 1];   // slot-order segment of each class
     int32_t task[kBatchClasses + 1]; // first task of each class
@@ -120,13 +145,20 @@ struct Segs {
 // one warp per task: a warp-class slot, or up to 32 slots of one class
 __global__ void __launch_bounds__(256) k_serve_tick(const ServeSlot* __restrict__ slots,
                                                     const int32_t* __restrict__ order, Segs sg, int64_t tick,
-                                                    uint32_t* __restrict__ state, uint8_t* __restrict__ status) {
+                                                    uint32_t* __restrict__ state, uint8_t* __restrict__ status,
+                                                    uint8_t* __restrict__ maps) {
     const int lane = threadIdx.x & 31;
     const int task = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     if (task >= sg.task[kBatchClasses]) return;
     int c = 0;
     while (c + 1 < kBatchClasses && task >= sg.task[c + 1]) c++;
     const int g = task - sg.task[c];
+    if (c == kClsMemoLong) {
+        const int slot = order[sg.lo[c] + g];
+        tick_memo_long(slots[slot], tick, state + (size_t)slot * kStateWords, status + 2 * slot,
+                       maps + (size_t)slot * 64 * kMapStride);
+        return;
+    }
     if (c == kClsWarp) {
         const int slot = order[sg.lo[c] + g];
         const ServeSlot sl = slots[slot];
@@ -199,6 +231,7 @@ struct rx_server {
     int32_t* d_order = nullptr;
     int32_t* h_order = nullptr;  // pinned
     uint32_t* d_state = nullptr;
+    uint8_t* d_maps = nullptr;  // chunk maps of the long cached slots
     uint8_t* d_status = nullptr;
     uint8_t* h_status = nullptr;  // pinned
     std::vector<Request*> slots;
@@ -244,6 +277,7 @@ void rx_server::run() {
     const int nslot = cfg.max_inflight;
     std::vector<int> free_slots;
     for (int i = nslot - 1; i >= 0; i--) free_slots.push_back(i);
+    std::vector<int64_t> tick_span(nslot, 0);  // bytes each slot advances this tick
     std::vector<Request*> admitted;
     while (true) {
         admitted.clear();
@@ -337,20 +371,25 @@ void rx_server::run() {
         std::vector<int> cls_slots[kBatchClasses];
         int inflight = 0;
         for (int i = 0; i < nslot; i++)
+            if (slots[i]) inflight++;
+        // a tick advances every request by `tick` bytes; with few requests
+        // in flight the GPU would idle between short ticks, so the tick
+        // grows (up to kTickGrow times) as the in-flight count falls
+        const int64_t grow = std::max<int64_t>(1, std::min<int64_t>(kTickGrow, kTickGrow / std::max(inflight, 1)));
+        const int64_t tick = cfg.tick_bytes * grow;
+        for (int i = 0; i < nslot; i++)
             if (slots[i]) {
-                cls_slots[h_slots[i].cls].push_back(i);
-                inflight++;
+                int c = h_slots[i].cls;
+                // a cached request with more than two ticks left takes a warp
+                if (c == kClsMemo && h_slots[i].len - h_slots[i].pos > 2 * tick) c = kClsMemoLong;
+                cls_slots[c].push_back(i);
+                tick_span[i] = c == kClsMemoLong ? 32 * tick : tick;
             }
         {
             std::lock_guard<std::mutex> lk(mu);
             peak_inflight = std::max<int64_t>(peak_inflight, inflight + (int64_t)longs.size());
         }
         if (inflight > 0) {
-            // a tick advances every request by `tick` bytes; with few requests
-            // in flight the GPU would idle between short ticks, so the tick
-            // grows (up to kTickGrow times) as the in-flight count falls
-            const int64_t grow = std::max<int64_t>(1, std::min<int64_t>(kTickGrow, kTickGrow / inflight));
-            const int64_t tick = cfg.tick_bytes * grow;
             Segs sg{};
             int k = 0, tasks = 0;
             for (int c = 0; c < kBatchClasses; c++) {
@@ -358,7 +397,7 @@ void rx_server::run() {
                 sg.task[c] = tasks;
                 for (int i : cls_slots[c]) h_order[k++] = i;
                 int cnt = (int)cls_slots[c].size();
-                tasks += (c == kClsWarp) ? cnt : (cnt + 31) / 32;
+                tasks += (c == kClsWarp || c == kClsMemoLong) ? cnt : (cnt + 31) / 32;
             }
             sg.lo[kBatchClasses] = k;
             sg.task[kBatchClasses] = tasks;
@@ -367,7 +406,7 @@ void rx_server::run() {
             int blocks = (tasks * 32 + 255) / 256;
             {
                 ProfScope ps(st);
-                k_serve_tick<<<blocks, 256, 0, st>>>(d_slots, d_order, sg, tick, d_state, d_status);
+                k_serve_tick<<<blocks, 256, 0, st>>>(d_slots, d_order, sg, tick, d_state, d_status, d_maps);
             }
             cudaMemcpyAsync(h_status, d_status, 2 * (size_t)nslot, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
@@ -384,7 +423,7 @@ void rx_server::run() {
                     free_slots.push_back(i);
                     complete(r, h_status[2 * i + 1], e == cudaSuccess ? RX_OK : RX_ERR_CUDA);
                 } else {
-                    h_slots[i].pos = std::min(h_slots[i].len, h_slots[i].pos + tick);
+                    h_slots[i].pos = std::min(h_slots[i].len, h_slots[i].pos + tick_span[i]);
                 }
             }
         } else if (!longs.empty()) {
@@ -422,7 +461,7 @@ rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out) {
         if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 1024;
         if (s->cfg.queue_capacity <= 0) s->cfg.queue_capacity = 1 << 16;
         if (s->cfg.tick_bytes <= 0) s->cfg.tick_bytes = 1 << 14;
-        s->long_threshold = s->cfg.long_threshold > 0 ? s->cfg.long_threshold : (1 << 16);
+        s->long_threshold = s->cfg.long_threshold > 0 ? s->cfg.long_threshold : (1 << 25);
         cudaGetDevice(&s->device);
         size_t fr = 0, tot = 0;
         cudaError_t e = cudaMemGetInfo(&fr, &tot);
@@ -441,6 +480,7 @@ rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out) {
                   cudaMalloc(&s->d_slots, sizeof(ServeSlot) * n) == cudaSuccess &&
                   cudaMalloc(&s->d_order, sizeof(int32_t) * n) == cudaSuccess &&
                   cudaMalloc(&s->d_state, sizeof(uint32_t) * (size_t)kStateWords * n) == cudaSuccess &&
+                  cudaMalloc(&s->d_maps, (size_t)64 * kMapStride * n) == cudaSuccess &&
                   cudaMalloc(&s->d_status, 2 * (size_t)n) == cudaSuccess &&
                   cudaMallocHost(&s->h_slots, sizeof(ServeSlot) * n) == cudaSuccess &&
                   cudaMallocHost(&s->h_order, sizeof(int32_t) * n) == cudaSuccess &&
@@ -612,6 +652,7 @@ rx_status rx_serve_destroy(rx_server* s) {
     cudaFree(s->d_slots);
     cudaFree(s->d_order);
     cudaFree(s->d_state);
+    cudaFree(s->d_maps);
     cudaFree(s->d_status);
     cudaFreeHost(s->h_slots);
     cudaFreeHost(s->h_order);

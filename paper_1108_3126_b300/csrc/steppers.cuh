@@ -554,6 +554,149 @@ __device__ __forceinline__ void run_lane(S& st, uint64_t s, uint64_t e, bool val
 }
 
 // ---------------------------------------------------------------------------
+// Chunked transfer functions on cache states for one long string per warp
+// (the batched form's long pairs, the serving tick's long requests).
+static_assert(kMemoMaxStates <= 256, "chunk maps hold cache state ids in one byte");
+
+// one lane, bytes [s, e) (absolute addresses), cache state st (id * 256),
+// one-byte table T in global memory; stops when the set is empty
+// (the next 16-byte block is loaded while the current one is stepped)
+__device__ inline uint32_t lane_memo_run(const uint8_t* __restrict__ T, uint32_t st, uint64_t s, uint64_t e) {
+    uint64_t blk = s & ~uint64_t(15);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (blk < e && st != 0) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
+    while (blk < e && st != 0) {
+        const uint64_t nb = blk + 16;
+        uint4 vn = make_uint4(0, 0, 0, 0);
+        if (nb < e) vn = ld_stream(reinterpret_cast<const uint8_t*>(nb));
+        if (blk >= s && nb <= e) {
+#pragma unroll
+            for (int k = 0; k < 16; k++) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const uint64_t q = blk + k;
+                if (q >= s && q < e) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
+            }
+        }
+        blk = nb;
+        v = vn;
+    }
+    return st;
+}
+
+constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states are merged
+
+// One warp advances the cache state x0 over bytes [s, e) (absolute
+// addresses) and returns the state reached (the same in every lane).  T:
+// the one-byte cache rows in global memory (K x 256).
+// Lane l computes the transfer map of chunk l (of 32) on cache states.
+// Every incoming state advances over the first 4 bytes of the chunk; the
+// states reached are deduplicated (a bitmap; rank = index) into
+// representatives, and each incoming state records its representative.  The
+// representatives then advance in stages of 4, 8, 16, ... bytes (at most
+// kPairPrefix bytes in all) until at most one distinct live state is among
+// them -- the empty set (state 0) stays empty at no cost, and two states that
+// meet stay together (Def 5.2 is a function of the set) -- and each distinct
+// one runs over the rest of the chunk.  wsm holds, per lane, map[K]
+// (incoming state -> representative) and, after the 32 maps, dv[K] (the
+// representatives' states); `stride` >= K bytes each.  Lane 0 composes the
+// 32 maps from x0.
+__device__ inline uint32_t warp_chunked_memo(const uint8_t* __restrict__ T, int K, uint32_t x0, uint64_t s, uint64_t e,
+                                      uint8_t* wsm, int stride) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t L = e - s;
+    const uint64_t C = ((L + 31) / 32 + 15) & ~uint64_t(15);
+    uint64_t cs = s + (uint64_t)lane * C;
+    if (cs > e) cs = e;
+    const uint64_t ce = cs + C < e ? cs + C : e;
+    const uint64_t pe = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
+    uint8_t* map = wsm + lane * stride;
+    uint8_t* dv = wsm + (32 + lane) * stride;
+    // first stage: every incoming state over the chunk's first (up to) 4
+    // bytes, read once; the states are independent, two in flight
+    uint64_t pos = cs + 4 < pe ? cs + 4 : pe;
+    const int nb = (int)(pos - cs);
+    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    if (nb > 0) b0 = __ldg(reinterpret_cast<const uint8_t*>(cs));
+    if (nb > 1) b1 = __ldg(reinterpret_cast<const uint8_t*>(cs + 1));
+    if (nb > 2) b2 = __ldg(reinterpret_cast<const uint8_t*>(cs + 2));
+    if (nb > 3) b3 = __ldg(reinterpret_cast<const uint8_t*>(cs + 3));
+    uint32_t bm[kBmWords];
+#pragma unroll
+    for (int w = 0; w < kBmWords; w++) bm[w] = 0;
+#pragma unroll 2
+    for (int k = 0; k < K; k++) {
+        uint32_t st = (uint32_t)k * 256u;
+        if (nb > 0) st = (uint32_t)__ldg(T + st + b0) << 8;
+        if (nb > 1) st = (uint32_t)__ldg(T + st + b1) << 8;
+        if (nb > 2) st = (uint32_t)__ldg(T + st + b2) << 8;
+        if (nb > 3) st = (uint32_t)__ldg(T + st + b3) << 8;
+        const uint32_t v = st >> 8;
+        map[k] = (uint8_t)v;
+        bm_set(bm, v);
+    }
+    int nr = 0;
+#pragma unroll
+    for (int w = 0; w < kBmWords; w++) {
+        uint32_t x = bm[w];
+        while (x) {
+            dv[nr++] = (uint8_t)(w * 32 + __ffs(x) - 1);
+            x &= x - 1;
+        }
+    }
+    for (int k = 0; k < K; k++) map[k] = (uint8_t)rank_below(bm, map[k]);
+    int live = nr - (int)(bm[0] & 1u);
+    // further stages: the representatives only
+    uint64_t len = 4;
+    while (live > 1 && pos < pe) {
+        const uint64_t end = pos + len < pe ? pos + len : pe;
+#pragma unroll
+        for (int w = 0; w < kBmWords; w++) bm[w] = 0;
+        for (int i = 0; i < nr; i++) {
+            const uint32_t v = lane_memo_run(T, (uint32_t)dv[i] * 256u, pos, end) >> 8;
+            dv[i] = (uint8_t)v;
+            bm_set(bm, v);
+        }
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < kBmWords; w++) cnt += __popc(bm[w]);
+        live = cnt - (int)(bm[0] & 1u);
+        pos = end;
+        len *= 2;
+    }
+    // the rest of the chunk, once per distinct state (a small cache of
+    // (state, result) pairs; a repeat beyond it is run again, same result)
+    uint32_t cv[4], cr[4];
+    int nc = 0;
+    for (int i = 0; i < nr; i++) {
+        const uint32_t v = dv[i];
+        uint32_t r = 0xffffffffu;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (q < nc && cv[q] == v) r = cr[q];
+        if (r == 0xffffffffu) {
+            r = v == 0 ? 0u : lane_memo_run(T, v * 256u, pos, ce) >> 8;
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (q == nc) {
+                    cv[q] = v;
+                    cr[q] = r;
+                }
+            if (nc < 4) nc++;
+        }
+        dv[i] = (uint8_t)r;
+    }
+    for (int k = 0; k < K; k++) map[k] = dv[map[k]];
+    __syncwarp();
+    uint32_t x = x0;
+    if (lane == 0)
+        for (int l = 0; l < 32; l++) x = wsm[l * stride + x];
+    __syncwarp();
+    return __shfl_sync(FULL, x, 0);
+}
+
+// ---------------------------------------------------------------------------
 // One string per warp: lane l owns words l, l+32, ... (K per lane) of the
 // active set.  A step ANDs with B[c], then ORs the follow row of every
 // active bit, found with ballot / shuffle so the loop is warp-uniform.  The

@@ -263,6 +263,14 @@ static void uniform_fill(rng_t* g, uint8_t* dst, int64_t len, const uint8_t* alp
 
 static int64_t draw_len(rng_t* g, int64_t lmin, int64_t lmax, int log_len) {
     if (!log_len) return rint_in(g, lmin, lmax);
+    if (lmin < 1) {
+        /* log-uniform on [1, lmax + 1], shifted down by one: [0, lmax] */
+        const double b = log((double)lmax + 2.0);
+        int64_t L = (int64_t)floor(exp(b * runif(g))) - 1;
+        if (L < 0) L = 0;
+        if (L > lmax) L = lmax;
+        return L;
+    }
     double a = log((double)lmin), b = log((double)lmax + 1.0);
     int64_t L = (int64_t)floor(exp(a + (b - a) * runif(g)));
     if (L < lmin) L = lmin;

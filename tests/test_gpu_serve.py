@@ -88,6 +88,26 @@ def test_mix_equals_alone_equals_oracle():
             assert mixed[k] == oracle.o2(pool[ri], w), (k, len(w))
 
 
+def test_chunked_long_requests_and_warp_ticks_agree():
+    """The three ways a long request can run -- the chunked mode on its own
+    stream (long_threshold low), warp ticks (32 spans per tick composed from
+    the saved state), and lane ticks only (tick larger than any request) --
+    give the same answers, equal to O2."""
+    pool, reqs = workload(seed=0xF8, n_req=160)
+    handles = compile_pool(pool)
+    a, _ = serve_all(handles, reqs, max_inflight=64, tick_bytes=512, long_threshold=8192)
+    b, _ = serve_all(handles, reqs, max_inflight=64, tick_bytes=512)
+    c, _ = serve_all(handles, reqs, max_inflight=64, tick_bytes=1 << 23)
+    assert (a == b).all() and (b == c).all()
+    for k, (ri, w) in enumerate(reqs):
+        if len(w) <= 200000:
+            assert b[k] == oracle.o2(pool[ri], w), (k, len(w))
+    # many requests took warp ticks (more than two 512-byte ticks left), some
+    # more than 32 of them, and some the chunked mode
+    lens = np.array([len(w) for _, w in reqs])
+    assert (lens > 1024).sum() >= 20 and (lens > 8192).sum() >= 8 and (lens > 32 * 512 * 2).sum() >= 5
+
+
 def test_small_budget_admission_is_exact():
     pool, reqs = workload(seed=0xF5, n_req=80)
     handles = compile_pool(pool)
