@@ -45,10 +45,10 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
 # capture, keyed by a hash of that kernel's sources at capture time (null
-# when they have changed since).  k_stream<MemoPairP>: 132.32 MB per launch
+# when they have changed since).  k_stream<MemoPairP>: 131.97 MB per launch
 # on the 262,144-string capture (136.81 MB algorithmic), scaled by
-# algorithmic bytes to the full 1,048,576-string launch (546.80 MB): 528.9 MB.
-TRAFFIC = {("k_stream<MemoPairP>", "ac5543bab85b5f67"): 528.9e6}
+# algorithmic bytes to the full 1,048,576-string launch (546.80 MB): 527.4 MB.
+TRAFFIC = {("k_stream<MemoPairP>", "90f587b869c25e40"): 527.4e6}
 
 
 def kernel_source_hash() -> str:
@@ -151,6 +151,21 @@ def cpu_baseline_streaming(w, seconds_budget: float = 12.0, max_strings: int = 2
     dt = time.perf_counter() - t
     nbytes = int(s.offsets[n])
     return nbytes / dt / 1e9, cores, f"first {n} strings ({nbytes / 1e6:.1f} MB) of the workload, O2 on {cores} threads"
+
+
+def cpu_baseline_o1(w, cores: int, n: int = 300):
+    """The memoised big-step oracle (O1, Fig 2.1) on the first n strings,
+    one thread and all threads; GB/s each."""
+    import oracle
+    nodes, s = w.regexes[0], w.strings
+    n = min(n, s.n)
+    res = {}
+    for th in (1, cores):
+        t = time.perf_counter()
+        oracle.o1_batch(nodes, s.data, s.offsets[:n + 1], threads=th)
+        res[f"GB/s_{th}_threads"] = round(int(s.offsets[n]) / (time.perf_counter() - t) / 1e9, 4)
+    res["sample"] = f"first {n} strings ({int(s.offsets[n]) / 1e6:.1f} MB)"
+    return res
 
 
 def run_reference(args, world, rank):
@@ -334,7 +349,8 @@ def run_streaming(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         v, cores, desc = cpu_baseline_streaming(w)
-        cpu = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "o1_big_step": cpu_baseline_o1(w, cores)}
 
     if rank != 0:
         return
@@ -491,6 +507,15 @@ def run_long(args, world, rank, local):
     rx.match_seq(r, d, pre, out, stream=stream)
     torch.cuda.synchronize(dev)
     assert int(out.item()) == agree_prefix
+    # the mean size of the active set (positions + null) along the first
+    # 256 KiB, from the set trace (one set per byte, GPU)
+    tl = min(n, 256 << 10)
+    W = r.tables()["words"]
+    rows = torch.zeros((tl + 1) * W, dtype=torch.int32, device=dev)
+    rx.trace(r, d, tl, rows, stream=stream)
+    torch.cuda.synchronize(dev)
+    rw = rows.cpu().numpy().view(np.uint32)
+    mean_active = float(np.unpackbits(rw.view(np.uint8)).sum()) / (tl + 1)
     # chunked unanchored search over the same text for a literal planted
     # near its end (the whole text is scanned), informational
     search = None
@@ -514,7 +539,9 @@ def run_long(args, world, rank, local):
             "higher_is_better": True, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "long text: (R)* with 48 positions over a..z, one text of concatenated language "
                                    "samples of R", "bytes": n, "memo_states": r.info()["memo_states"],
-                       "accepted": chunked, "last_whole_sample_end": end},
+                       "accepted": chunked, "last_whole_sample_end": end,
+                       "mean_active_set": round(mean_active, 2),
+                       "mean_active_set_over": f"first {tl} bytes (positions + null, from rx_trace)"},
             "sequential_gpu": {"bytes": pre, "ms": round(seq_ms, 2), "GB/s": round(pre / (seq_ms * 1e-3) / 1e9, 4)},
             "chunked_over_sequential": round((n / ms) / (pre / seq_ms), 1),
             "roofline": {"bound": "hbm", "kernel": "k_chunk_stage + k_span_tasks", "kernel_ms": round(kernel_ms, 4),
