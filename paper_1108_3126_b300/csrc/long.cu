@@ -219,6 +219,21 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
 // first level of the composition, reading the chunk maps straight from the
 // tasks' results: map_j[k] = res[toff[j] + slot[j*K + k]] (0 for the empty
 // set); block b composes chunks [b*G, min((b+1)*G, J)) into out[b]
+// Maps m[0..nmap) of K entries in shared memory, m[0] applied first: leaves
+// their composition in m[0].  Pairwise in log2(nmap) levels: at stride d,
+// m[j] <- m[j + d] o m[j] for j a multiple of 2d (composition is
+// associative, so this bracketing gives the left-to-right result).
+__device__ void compose_tree(uint16_t* m, int nmap, int K) {
+    for (int d = 1; d < nmap; d *= 2) {
+        const int pairs = (nmap - d + 2 * d - 1) / (2 * d);  // j = 0, 2d, ... with j + d < nmap
+        for (int i = threadIdx.x; i < pairs * K; i += blockDim.x) {
+            const int j = (i / K) * 2 * d, k = i % K;
+            m[j * K + k] = m[(j + d) * K + m[j * K + k]];
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_compose_first(const uint16_t* __restrict__ slot, const unsigned* __restrict__ toff,
                                 const uint16_t* __restrict__ res, long long J, int K, int G,
                                 uint16_t* __restrict__ out) {
@@ -235,6 +250,8 @@ __global__ void k_compose_first(const uint16_t* __restrict__ slot, const unsigne
         }
     }
     __syncthreads();
+    // one thread per incoming state walks the maps in order (the gather
+    // above dominates; a pairwise tree here was slower)
     for (int s = threadIdx.x; s < K; s += blockDim.x) {
         int x = s;
         for (int j = 0; j < nmap; j++) x = sm16[j * K + x];
@@ -251,11 +268,8 @@ __global__ void k_compose_maps(const uint16_t* __restrict__ in, long long cnt, i
     int nmap = (int)(hi - lo);
     for (int i = threadIdx.x; i < nmap * K; i += blockDim.x) sm16[i] = in[lo * K + i];
     __syncthreads();
-    for (int s = threadIdx.x; s < K; s += blockDim.x) {
-        int x = s;
-        for (int j = 0; j < nmap; j++) x = sm16[j * K + x];
-        out[(long long)blockIdx.x * K + s] = (uint16_t)x;
-    }
+    compose_tree(sm16, nmap, K);
+    for (int s = threadIdx.x; s < K; s += blockDim.x) out[(long long)blockIdx.x * K + s] = sm16[s];
 }
 
 __global__ void k_finish_memo(const DevTables t, const uint16_t* __restrict__ map, int has_map, uint8_t* out) {
@@ -528,7 +542,7 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         uint16_t* nxt = L.maps_b;
         while (cnt > 1) {
             long long nb = (cnt + G - 1) / G;
-            k_compose_maps<<<(unsigned)nb, 128, (size_t)G * K * 2, st>>>(cur, cnt, K, G, nxt);
+            k_compose_maps<<<(unsigned)nb, 512, (size_t)G * K * 2, st>>>(cur, cnt, K, G, nxt);
             prof_count(1);
             std::swap(cur, nxt);
             cnt = nb;
