@@ -619,15 +619,22 @@ __global__ void __launch_bounds__(256) k_search_stage(const DevTables t, const u
         if (valid) {
             const int64_t cs = j * C, pe = min(cs + kSearchPrefix, min(cs + C, len));
             const int n = (int)(pe - cs);
+            // the prefix, read once into registers (every state walks it)
+            uint32_t wb[kSearchPrefix / 4];
+#pragma unroll
+            for (int i = 0; i < kSearchPrefix / 4; i++) wb[i] = 0;
+#pragma unroll
+            for (int q = 0; q < kSearchPrefix; q++)
+                if (q < n) wb[q >> 2] |= (uint32_t)__ldg(str + cs + q) << (8 * (q & 3));
             for (int k = 0; k < K; k++) {
                 SearchS st = proto;
                 st.set_state((uint32_t)k);
                 int a = -1;
-                for (int q = 0; q < n; q++) {
-                    st.step(__ldg(str + cs + q));
-                    if (st.accepted()) {
-                        a = q + 1;
-                        break;
+#pragma unroll
+                for (int q = 0; q < kSearchPrefix; q++) {
+                    if (q < n && a < 0) {
+                        st.step((wb[q >> 2] >> (8 * (q & 3))) & 0xFFu);
+                        if (st.accepted()) a = q + 1;
                     }
                 }
                 pacc[j * K + k] = a < 0 ? (uint8_t)0xFF : (uint8_t)a;
