@@ -140,11 +140,28 @@ __device__ void tick_memo_long(const ServeSlot& sl, int64_t tick, uint32_t* stat
 struct Segs {
     int32_t lo[kBatchClasses + 1];   // slot-order segment of each class
     int32_t task[kBatchClasses + 1]; // first task of each class
+    int64_t span[kBatchClasses];     // bytes a request of the class advances (per lane / chunk)
 };
+
+// A tick's bytes per class: the classes without a cache of macro steps cost
+// a lane more per byte (a bitset step; the warp class a ballot loop over
+// the active bits), so they take a smaller share, which keeps one slow
+// request from setting the length of the whole tick; a cached request
+// advances `tick` bytes (32 spans of it when it has a warp).
+int64_t class_span(int c, int64_t tick, int64_t base) {
+    switch (c) {
+    case kClsWarp: return std::max<int64_t>(256, base / 16);
+    case kClsSparse8:
+    case kClsSparse4: return std::max<int64_t>(256, base / 2);
+    case kClsThread1:
+    case kClsThread2: return base;
+    default: return tick;
+    }
+}
 
 // one warp per task: a warp-class slot, or up to 32 slots of one class
 __global__ void __launch_bounds__(256) k_serve_tick(const ServeSlot* __restrict__ slots,
-                                                    const int32_t* __restrict__ order, Segs sg, int64_t tick,
+                                                    const int32_t* __restrict__ order, Segs sg,
                                                     uint32_t* __restrict__ state, uint8_t* __restrict__ status,
                                                     uint8_t* __restrict__ maps) {
     const int lane = threadIdx.x & 31;
@@ -153,6 +170,7 @@ __global__ void __launch_bounds__(256) k_serve_tick(const ServeSlot* __restrict_
     int c = 0;
     while (c + 1 < kBatchClasses && task >= sg.task[c + 1]) c++;
     const int g = task - sg.task[c];
+    const int64_t tick = sg.span[c];
     if (c == kClsMemoLong) {
         const int slot = order[sg.lo[c] + g];
         tick_memo_long(slots[slot], tick, state + (size_t)slot * kStateWords, status + 2 * slot,
@@ -377,13 +395,15 @@ void rx_server::run() {
         // grows (up to kTickGrow times) as the in-flight count falls
         const int64_t grow = std::max<int64_t>(1, std::min<int64_t>(kTickGrow, kTickGrow / std::max(inflight, 1)));
         const int64_t tick = cfg.tick_bytes * grow;
+        int64_t span[kBatchClasses];
+        for (int c = 0; c < kBatchClasses; c++) span[c] = class_span(c, tick, cfg.tick_bytes);
         for (int i = 0; i < nslot; i++)
             if (slots[i]) {
                 int c = h_slots[i].cls;
                 // a cached request with more than two ticks left takes a warp
                 if (c == kClsMemo && h_slots[i].len - h_slots[i].pos > 2 * tick) c = kClsMemoLong;
                 cls_slots[c].push_back(i);
-                tick_span[i] = c == kClsMemoLong ? 32 * tick : tick;
+                tick_span[i] = c == kClsMemoLong ? 32 * span[c] : span[c];
             }
         {
             std::lock_guard<std::mutex> lk(mu);
@@ -393,6 +413,7 @@ void rx_server::run() {
             Segs sg{};
             int k = 0, tasks = 0;
             for (int c = 0; c < kBatchClasses; c++) {
+                sg.span[c] = span[c];
                 sg.lo[c] = k;
                 sg.task[c] = tasks;
                 for (int i : cls_slots[c]) h_order[k++] = i;
@@ -406,7 +427,7 @@ void rx_server::run() {
             int blocks = (tasks * 32 + 255) / 256;
             {
                 ProfScope ps(st);
-                k_serve_tick<<<blocks, 256, 0, st>>>(d_slots, d_order, sg, tick, d_state, d_status, d_maps);
+                k_serve_tick<<<blocks, 256, 0, st>>>(d_slots, d_order, sg, d_state, d_status, d_maps);
             }
             cudaMemcpyAsync(h_status, d_status, 2 * (size_t)nslot, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
