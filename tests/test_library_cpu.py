@@ -202,3 +202,14 @@ def test_batch_entry_points_reject_null_arguments():
     assert L.rx_batch_run(None, None, None, None, None) == 2
     assert L.rx_batch_autotune(None, None, None, None, None, None) == 2
     L.rx_batch_free(None)
+
+
+def test_no_cpu_fallback_without_the_library(monkeypatch, tmp_path):
+    """Without librx.so every call raises: there is no other path."""
+    import paper_1108_3126_b300 as rx
+    monkeypatch.setattr(rx, "LIB_PATH", str(tmp_path / "librx.so"))
+    monkeypatch.setattr(rx, "_lib", None)
+    with pytest.raises(RuntimeError):
+        rx.lib()
+    with pytest.raises(RuntimeError):
+        rx.Regex.compile(b"ab", rx.COMPILE_HOST_ONLY)
