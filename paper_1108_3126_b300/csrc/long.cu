@@ -69,16 +69,33 @@ struct IdSet {
 };
 static_assert(kMemoMaxStates <= 192, "IdSet holds 192 ids");
 
+// The cache of macro steps with one-byte entries in shared memory (a
+// quarter of MemoS's rows, so more blocks fit an SM): st = shared address
+// of the state's row of 256 successor ids.
+struct MemoS8 {
+    uint32_t st, base;
+    __host__ __device__ static size_t smem_bytes(const DevTables& t) { return align16((size_t)t.memo_K * 256); }
+    __device__ static void load(const DevTables& t, uint8_t* sm) { copy_to_smem(sm, t.memo_T8, (size_t)t.memo_K * 256); }
+    __device__ void bind(const DevTables& t, uint8_t* sm) {
+        base = smem_addr(sm);
+        st = base + (t.memo_start >> 8) * 256u;
+    }
+    __device__ __forceinline__ void step(uint32_t c) { st = base + (lds8(st + c) << 8); }
+    __device__ __forceinline__ void set_state(uint32_t s) { st = base + s * 256u; }
+    __device__ __forceinline__ uint32_t state_id() const { return (st - base) >> 8; }
+};
+
 // N macro steps over the bytes packed in b (byte q at bits 8*(q%4) of b[q/4])
-template <int N>
-__device__ __forceinline__ void step_bytes(MemoS& st, const uint32_t (&b)[4]) {
+template <int N, class S>
+__device__ __forceinline__ void step_bytes(S& st, const uint32_t (&b)[4]) {
 #pragma unroll
     for (int q = 0; q < N; q++) st.step((b[q >> 2] >> (8 * (q & 3))) & 0xffu);
 }
 
 // the state reached from `s` over the n (<= 16) bytes packed in b
-__device__ __forceinline__ uint32_t step_n(const MemoS& proto, uint32_t s, const uint32_t (&b)[4], int n) {
-    MemoS st = proto;
+template <class S>
+__device__ __forceinline__ uint32_t step_n(const S& proto, uint32_t s, const uint32_t (&b)[4], int n) {
+    S st = proto;
     st.set_state(s);
     if (n == 4) {
         step_bytes<4>(st, b);
@@ -109,13 +126,13 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
                                                      uint16_t* __restrict__ task_state,
                                                      unsigned* __restrict__ ntask) {
     extern __shared__ __align__(16) uint8_t smem[];
-    MemoS::load(t, smem);
+    MemoS8::load(t, smem);
     __syncthreads();
-    MemoS proto;
+    MemoS8 proto;
     proto.bind(t, smem);
     const int K = t.memo_K;
     const int nt = blockDim.x, lane = threadIdx.x & 31;
-    uint8_t* map = smem + align16(MemoS::smem_bytes(t)) + threadIdx.x;
+    uint8_t* map = smem + MemoS8::smem_bytes(t) + threadIdx.x;
     uint8_t* dv = map + (size_t)K * nt;
     uint8_t* rk = dv + (size_t)K * nt;
     // warp-uniform loop over groups of 32 chunks
@@ -507,7 +524,7 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         MemoLongWs L;
         memo_long_layout(J, K, w, &L);
         // phase 1: staged prefixes, distinct states per chunk
-        const size_t tab = align16(MemoS::smem_bytes(t));
+        const size_t tab = MemoS8::smem_bytes(t);
         int dev = 0, optin = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
