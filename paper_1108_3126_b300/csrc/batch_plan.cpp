@@ -150,13 +150,13 @@ rx_status rx_batch_autotune(rx_batch* b, const uint8_t* strings, const int64_t* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rx_batch_tune best{b->L.long_bytes, b->L.block, -1.f};
     if (b->n > 0) {
-        const long long longs[6] = {2048, 4096, 8192, 16384, 32768, (long long)1 << 62};
+        const long long longs[8] = {2048, 3072, 4096, 6144, 8192, 16384, 32768, (long long)1 << 62};
         const int blocks[3] = {128, 256, 512};
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaError_t e = cudaEventCreate(&e0);
         if (e == cudaSuccess) e = cudaEventCreate(&e1);
         for (int bi = 0; bi < 3 && e == cudaSuccess; bi++)
-            for (int li = 0; li < 6 && e == cudaSuccess; li++) {
+            for (int li = 0; li < 8 && e == cudaSuccess; li++) {
                 rx::BatchLaunch L = b->L;
                 L.block = blocks[bi];
                 L.long_bytes = longs[li];

@@ -61,7 +61,7 @@ enum { kClsWarp = 0, kClsSparse8 = 1, kClsSparse4 = 2, kClsThread2 = 3, kClsThre
 struct BatchLaunch {
     int stride = 0;               // chunk-map bytes per lane (largest cache, rounded to 16)
     int block = 256;              // threads per block: 128, 256 or 512
-    long long long_bytes = 4096;  // cached pairs longer than this take a warp
+    long long long_bytes = 6144;  // cached pairs longer than this take a warp
     long long grid_cap = 1;       // resident blocks (set by batch_configure)
 };
 size_t batch_workspace_bytes(size_t n, size_t ntabs);

@@ -591,10 +591,10 @@ constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states a
 // addresses) and returns the state reached (the same in every lane).  T:
 // the one-byte cache rows in global memory (K x 256).
 // Lane l computes the transfer map of chunk l (of 32) on cache states.
-// Every incoming state advances over the first 4 bytes of the chunk; the
+// Every incoming state advances over the first byte of the chunk; the
 // states reached are deduplicated (a bitmap; rank = index) into
 // representatives, and each incoming state records its representative.  The
-// representatives then advance in stages of 4, 8, 16, ... bytes (at most
+// representatives then advance in stages of 3, 6, 12, ... bytes (at most
 // kPairPrefix bytes in all) until at most one distinct live state is among
 // them -- the empty set (state 0) stays empty at no cost, and two states that
 // meet stay together (Def 5.2 is a function of the set) -- and each distinct
@@ -613,26 +613,18 @@ __device__ inline uint32_t warp_chunked_memo(const uint8_t* __restrict__ T, int 
     const uint64_t pe = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
     uint8_t* map = wsm + lane * stride;
     uint8_t* dv = wsm + (32 + lane) * stride;
-    // first stage: every incoming state over the chunk's first (up to) 4
-    // bytes, read once; the states are independent, two in flight
-    uint64_t pos = cs + 4 < pe ? cs + 4 : pe;
-    const int nb = (int)(pos - cs);
-    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-    if (nb > 0) b0 = __ldg(reinterpret_cast<const uint8_t*>(cs));
-    if (nb > 1) b1 = __ldg(reinterpret_cast<const uint8_t*>(cs + 1));
-    if (nb > 2) b2 = __ldg(reinterpret_cast<const uint8_t*>(cs + 2));
-    if (nb > 3) b3 = __ldg(reinterpret_cast<const uint8_t*>(cs + 3));
+    // first stage: every incoming state over the chunk's first byte (the
+    // states are independent, two lookups in flight); a byte's successors
+    // are few distinct states, so the representatives take the rest
+    uint64_t pos = cs + 1 < pe ? cs + 1 : pe;
+    const bool nb = pos > cs;
+    const uint32_t b0 = nb ? __ldg(reinterpret_cast<const uint8_t*>(cs)) : 0u;
     uint32_t bm[kBmWords];
 #pragma unroll
     for (int w = 0; w < kBmWords; w++) bm[w] = 0;
 #pragma unroll 2
     for (int k = 0; k < K; k++) {
-        uint32_t st = (uint32_t)k * 256u;
-        if (nb > 0) st = (uint32_t)__ldg(T + st + b0) << 8;
-        if (nb > 1) st = (uint32_t)__ldg(T + st + b1) << 8;
-        if (nb > 2) st = (uint32_t)__ldg(T + st + b2) << 8;
-        if (nb > 3) st = (uint32_t)__ldg(T + st + b3) << 8;
-        const uint32_t v = st >> 8;
+        const uint32_t v = nb ? (uint32_t)__ldg(T + (uint32_t)k * 256u + b0) : (uint32_t)k;
         map[k] = (uint8_t)v;
         bm_set(bm, v);
     }
@@ -648,7 +640,7 @@ __device__ inline uint32_t warp_chunked_memo(const uint8_t* __restrict__ T, int 
     for (int k = 0; k < K; k++) map[k] = (uint8_t)rank_below(bm, map[k]);
     int live = nr - (int)(bm[0] & 1u);
     // further stages: the representatives only
-    uint64_t len = 4;
+    uint64_t len = 3;
     while (live > 1 && pos < pe) {
         const uint64_t end = pos + len < pe ? pos + len : pe;
 #pragma unroll

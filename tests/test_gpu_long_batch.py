@@ -194,7 +194,7 @@ def test_batched_edges():
 
 
 def test_batched_long_pairs_chunked_per_warp():
-    """Pairs longer than 4 KiB (the default threshold) whose expression has a cache of macro steps run
+    """Pairs longer than 6 KiB (the default threshold) whose expression has a cache of macro steps run
     one warp per pair (32 chunks, exact transfer functions composed by lane
     0).  Mix them with short pairs of the same and other expressions."""
     rng = np.random.default_rng(0xE9)
