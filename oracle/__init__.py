@@ -83,6 +83,8 @@ def _L():
         lib.or_o2_search.restype = I64
         lib.or_o2_search_batch.argtypes = [P, I, I, P, P, I64, P, I]
         lib.or_o2_search_batch.restype = I
+        lib.or_o2_pairs.argtypes = [P, P, P, I64, P, P, P, I64, P, I]
+        lib.or_o2_pairs.restype = I
         _lib = lib
     return _lib
 
@@ -216,6 +218,28 @@ def o2_batch(nodes, data: np.ndarray, offsets: np.ndarray, root: int = 0, thread
         d = np.zeros(1, np.uint8)
     o = np.ascontiguousarray(offsets, np.int64)
     if _L().or_o2_batch(_p(nd), len(nd), root, _p(d), _p(o), n, _p(out), threads) != 0:
+        raise ValueError("malformed tree")
+    return out[:n]
+
+
+def o2_pairs(regexes, regex_of, data: np.ndarray, offsets: np.ndarray, threads: int = 0) -> np.ndarray:
+    """O2 (Fig 6.1) per (expression, string) pair: pair i is string i
+    against regexes[regex_of[i]] (node arrays, root 0).  A plain loop over
+    the pairs on `threads` OpenMP threads (0 = all)."""
+    regs = [_nodes(r) for r in regexes]
+    ns = np.zeros(len(regs) + 1, np.int64)
+    ns[1:] = np.cumsum([len(r) for r in regs])
+    nd = np.ascontiguousarray(np.concatenate(regs)) if regs else np.zeros(1, NODE_DTYPE)
+    roots = np.zeros(max(len(regs), 1), np.int32)
+    pr = np.ascontiguousarray(regex_of, np.int32)
+    n = len(offsets) - 1
+    assert len(pr) == n
+    out = np.zeros(max(n, 1), np.uint8)
+    d = np.ascontiguousarray(data, np.uint8)
+    if d.size == 0:
+        d = np.zeros(1, np.uint8)
+    o = np.ascontiguousarray(offsets, np.int64)
+    if _L().or_o2_pairs(_p(nd), _p(ns), _p(roots), len(regs), _p(pr), _p(d), _p(o), n, _p(out), threads) != 0:
         raise ValueError("malformed tree")
     return out[:n]
 

@@ -212,8 +212,14 @@ int64_t or_o1_search(const or_node* nd, int nn, int root, const uint8_t* w, int6
 
 /* ------------------------------------------------------------------ O2
  * Lists are stacks whose head is the last array element.  NUL is stored as
- * the id nn.  psi(p, l1, l2) = p::l1 if p not in l1@l2, else l1 (Def 6.1),
- * tested by a linear scan of both lists.
+ * the id nn.  psi(p, l1, l2) = p::l1 if p not in l1@l2, else l1 (Def 6.1).
+ * The membership test "p in c@t" is kept as a mark per id: within one macro
+ * step an id only moves from c to t, so it stays in c@t once pushed; the one
+ * exception is null, which the rules drop from c without pushing it to t,
+ * so its mark is cleared when it is popped.  "p in n" is a second mark.
+ * Marks carry the macro-step number, so starting a step invalidates them.
+ * (The lists, their order and every rule are as in the figure; only the
+ * test of Def 6.1 is answered from the marks instead of a scan.)
  *
  * Fig 6.1, rule by rule (c = p::c'):
  *   p = p1|p2 : c := psi(p2, psi(p1, c', t), t);          t := p::t
@@ -243,31 +249,63 @@ typedef struct {
     int len;
 } olist;
 
-static int in_list(const olist* l, int32_t p) {
-    for (int i = 0; i < l->len; i++)
-        if (l->a[i] == p) return 1;
-    return 0;
+/* the lists of the machine and the membership marks of Def 6.1's test */
+typedef struct {
+    olist c, t, n;
+    int64_t* in_ct; /* in_ct[p] == step  iff  p in c@t */
+    int64_t* in_n;  /* in_n[p] == step   iff  p in n   */
+    int64_t step;
+} o2m;
+
+/* c := psi(p, c, t) */
+static void psi_ct(o2m* m, int32_t p) {
+    if (m->in_ct[p] == m->step) return;
+    m->in_ct[p] = m->step;
+    m->c.a[m->c.len++] = p;
 }
-/* l1 := psi(p, l1, l2) */
-static void psi(int32_t p, olist* l1, const olist* l2) {
-    if (in_list(l1, p) || in_list(l2, p)) return;
-    l1->a[l1->len++] = p;
+/* n := psi(p, n, []) */
+static void psi_n(o2m* m, int32_t p) {
+    if (m->in_n[p] == m->step) return;
+    m->in_n[p] = m->step;
+    m->n.a[m->n.len++] = p;
 }
+/* c = [], input a w: c := n; t := []; n := [] (the next macro step) */
+static void next_step(o2m* m) {
+    m->step++;
+    memcpy(m->c.a, m->n.a, sizeof(int32_t) * (size_t)m->n.len);
+    m->c.len = m->n.len;
+    for (int i = 0; i < m->c.len; i++) m->in_ct[m->c.a[i]] = m->step;
+    m->t.len = 0;
+    m->n.len = 0;
+}
+/* machine over buf: 6 (nn+1) int32 for the lists, then 2 (nn+1) int64 marks */
+static void o2m_init(o2m* m, int nn, int32_t* buf) {
+    int cap = 2 * (nn + 1);
+    m->c = (olist){buf, 0};
+    m->t = (olist){buf + cap, 0};
+    m->n = (olist){buf + 2 * cap, 0};
+    m->in_ct = (int64_t*)(buf + 3 * cap);
+    m->in_n = m->in_ct + (nn + 1);
+    for (int i = 0; i <= nn; i++) m->in_ct[i] = m->in_n[i] = -1;
+    m->step = 0;
+}
+#define O2_BUF_BYTES(nn) (sizeof(int32_t) * (size_t)(6 * ((nn) + 1)) + sizeof(int64_t) * (size_t)(2 * ((nn) + 1)))
 
 static int o2_run(const or_node* nd, int nn, int root, const int32_t* cont, const uint8_t* w, int64_t L,
                   uint8_t* trace, uint8_t* ntrace, int32_t* buf) {
     /* every list holds distinct ids from [0, nn]; give each nn+1 slots (plus
      * slack for null, which can be re-pushed after being dropped) */
-    int cap = 2 * (nn + 1);
-    olist c = {buf, 0}, t = {buf + cap, 0}, n = {buf + 2 * cap, 0}, empty = {NULL, 0};
+    o2m m;
+    o2m_init(&m, nn, buf);
     int32_t nul = nn;
     int accept = 0;
     int64_t pos = 0;
-    c.a[c.len++] = root;
+    psi_ct(&m, root);
     for (;;) {
-        if (c.len > 0) {
-            int32_t p = c.a[--c.len];
+        if (m.c.len > 0) {
+            int32_t p = m.c.a[--m.c.len];
             if (p == nul) {
+                m.in_ct[nul] = -1; /* dropped: no longer in c@t */
                 if (trace) trace[pos * (nn + 1) + nn] = 1;
                 if (pos == L) {
                     accept = 1;
@@ -279,35 +317,32 @@ static int o2_run(const or_node* nd, int nn, int root, const int32_t* cont, cons
             int32_t k = cont[p] < 0 ? nul : cont[p];
             switch (x->kind) {
             case ALT:
-                psi(x->l, &c, &t);
-                psi(x->r, &c, &t);
+                psi_ct(&m, x->l);
+                psi_ct(&m, x->r);
                 break;
             case CAT:
-                psi(x->l, &c, &t);
+                psi_ct(&m, x->l);
                 break;
             case STAR:
-                psi(x->l, &c, &t);
-                psi(k, &c, &t);
+                psi_ct(&m, x->l);
+                psi_ct(&m, k);
                 break;
             case EPS:
-                psi(k, &c, &t);
+                psi_ct(&m, k);
                 break;
             case CHAR:
                 if (trace) trace[pos * (nn + 1) + p] = 1;
-                if (pos < L && w[pos] == x->byte) psi(k, &n, &empty);
+                if (pos < L && w[pos] == x->byte) psi_n(&m, k);
                 break;
             }
-            t.a[t.len++] = p;
+            m.t.a[m.t.len++] = p;
             continue;
         }
         /* c = [] */
-        if (pos < L && n.len > 0) {
+        if (pos < L && m.n.len > 0) {
             if (ntrace)
-                for (int i = 0; i < n.len; i++) ntrace[pos * (nn + 1) + n.a[i]] = 1;
-            memcpy(c.a, n.a, sizeof(int32_t) * (size_t)n.len);
-            c.len = n.len;
-            t.len = 0;
-            n.len = 0;
+                for (int i = 0; i < m.n.len; i++) ntrace[pos * (nn + 1) + m.n.a[i]] = 1;
+            next_step(&m);
             pos++;
             continue;
         }
@@ -317,7 +352,7 @@ static int o2_run(const or_node* nd, int nn, int root, const int32_t* cont, cons
 
 int or_o2(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, uint8_t* trace, uint8_t* ntrace) {
     int32_t* cont = (int32_t*)malloc(sizeof(int32_t) * (size_t)nn);
-    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(6 * (nn + 1)));
+    int32_t* buf = (int32_t*)malloc(O2_BUF_BYTES(nn));
     if (!cont || !buf || or_cont(nd, nn, root, cont) != 0) { free(cont); free(buf); return -1; }
     int r = o2_run(nd, nn, root, cont, w, L, trace, ntrace, buf);
     free(cont);
@@ -333,16 +368,16 @@ int or_o2(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L, uint
  * is exhausted without null. */
 int64_t or_o2_search(const or_node* nd, int nn, int root, const uint8_t* w, int64_t L) {
     int32_t* cont = (int32_t*)malloc(sizeof(int32_t) * (size_t)nn);
-    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(6 * (nn + 1)));
+    int32_t* buf = (int32_t*)malloc(O2_BUF_BYTES(nn));
     if (!cont || !buf || or_cont(nd, nn, root, cont) != 0) { free(cont); free(buf); return -2; }
-    int cap = 2 * (nn + 1);
-    olist c = {buf, 0}, t = {buf + cap, 0}, n = {buf + 2 * cap, 0}, empty = {NULL, 0};
+    o2m m;
+    o2m_init(&m, nn, buf);
     int32_t nul = nn;
     int64_t pos = 0, res = -1;
-    c.a[c.len++] = root;
+    psi_ct(&m, root);
     for (;;) {
-        if (c.len > 0) {
-            int32_t p = c.a[--c.len];
+        if (m.c.len > 0) {
+            int32_t p = m.c.a[--m.c.len];
             if (p == nul) {
                 res = pos;
                 break;
@@ -351,34 +386,31 @@ int64_t or_o2_search(const or_node* nd, int nn, int root, const uint8_t* w, int6
             int32_t k = cont[p] < 0 ? nul : cont[p];
             switch (x->kind) {
             case ALT:
-                psi(x->l, &c, &t);
-                psi(x->r, &c, &t);
+                psi_ct(&m, x->l);
+                psi_ct(&m, x->r);
                 break;
             case CAT:
-                psi(x->l, &c, &t);
+                psi_ct(&m, x->l);
                 break;
             case STAR:
-                psi(x->l, &c, &t);
-                psi(k, &c, &t);
+                psi_ct(&m, x->l);
+                psi_ct(&m, k);
                 break;
             case EPS:
-                psi(k, &c, &t);
+                psi_ct(&m, k);
                 break;
             case CHAR:
-                if (pos < L && w[pos] == x->byte) psi(k, &n, &empty);
+                if (pos < L && w[pos] == x->byte) psi_n(&m, k);
                 break;
             }
-            t.a[t.len++] = p;
+            m.t.a[m.t.len++] = p;
             continue;
         }
         /* c = []: the next macro step, with the root added back */
         if (pos >= L) break;
-        memcpy(c.a, n.a, sizeof(int32_t) * (size_t)n.len);
-        c.len = n.len;
-        t.len = 0;
-        n.len = 0;
+        next_step(&m);
         pos++;
-        psi(root, &c, &t);
+        psi_ct(&m, root);
     }
     free(cont);
     free(buf);
@@ -403,7 +435,7 @@ int or_o2_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const
     int failed = 0;
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
     {
-        int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(6 * (nn + 1)));
+        int32_t* buf = (int32_t*)malloc(O2_BUF_BYTES(nn));
         if (!buf) failed = 1;
 #pragma omp for schedule(dynamic, 16)
         for (int64_t i = 0; i < n; i++) {
@@ -431,4 +463,39 @@ int or_o1_batch(const or_node* nd, int nn, int root, const uint8_t* bytes, const
         out[i] = (uint8_t)(r < 0 ? 255 : r);
     }
     return 0;
+}
+
+/* Pairs: n (expression, string) pairs, pair i decided by O2 for expression
+ * pr[i] on string i.  The expressions are concatenated node arrays:
+ * expression r is nd[ns[r] .. ns[r+1]) with its root at index root[r] of
+ * that slice.  A plain loop over the pairs, spread over nthreads OpenMP
+ * threads; out[i] = 0/1.  Returns -1 on a malformed tree. */
+int or_o2_pairs(const or_node* nd, const int64_t* ns, const int32_t* root, int64_t nreg, const int32_t* pr,
+                const uint8_t* bytes, const int64_t* off, int64_t n, uint8_t* out, int nthreads) {
+    int64_t total = ns[nreg];
+    int32_t* cont = (int32_t*)malloc(sizeof(int32_t) * (size_t)(total > 0 ? total : 1));
+    if (!cont) return -1;
+    int failed = 0, maxnn = 0;
+    for (int64_t r = 0; r < nreg; r++) {
+        int nn = (int)(ns[r + 1] - ns[r]);
+        if (nn > maxnn) maxnn = nn;
+        if (or_cont(nd + ns[r], nn, root[r], cont + ns[r]) != 0) failed = 1;
+    }
+    if (failed) { free(cont); return -1; }
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    {
+        int32_t* buf = (int32_t*)malloc(O2_BUF_BYTES(maxnn));
+        if (!buf) failed = 1;
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < n; i++) {
+            if (!buf) continue;
+            int64_t r = pr[i];
+            int nn = (int)(ns[r + 1] - ns[r]);
+            out[i] = (uint8_t)o2_run(nd + ns[r], nn, root[r], cont + ns[r], bytes + off[i], off[i + 1] - off[i],
+                                     NULL, NULL, buf);
+        }
+        free(buf);
+    }
+    free(cont);
+    return failed ? -1 : 0;
 }

@@ -296,3 +296,25 @@ def test_o2_search_equals_o1_search():
     t = bytes(rng.choice(list(b"abc"), size=200000).tolist()) + b"xyz"
     assert oracle.o2_search(oracle.parse(b"xyz"), t) == len(t)
     assert oracle.o2_search(oracle.parse(b"xyzz"), t) == -1
+
+
+def test_o2_pairs_is_o2_per_pair_and_o1():
+    """The pairs loop decides pair i with O2 for its own expression: it
+    equals O2 and O1 called pair by pair, with expressions of different
+    sizes (and epsilon loops) interleaved, empty strings included."""
+    regs, strs, rid = [], [], []
+    for i in range(24):
+        e = synth.gen_regex([3, 8, 20, 60][i % 4], 8, b"abc", synth.item_seed(0x0A, i), eps_loop_p=0.2)
+        regs.append(e)
+        s = synth.gen_strings(e, 12, 0, 40, b"abc", synth.item_seed(0x0B, i), p_lang=0.5)
+        strs += [s.get(k) for k in range(s.n)]
+        rid += [i] * s.n
+    order = np.random.default_rng(3).permutation(len(strs))
+    strs = [strs[k] for k in order]
+    rid = np.array(rid, np.int32)[order]
+    pk = synth.pack(strs)
+    got = oracle.o2_pairs(regs, rid, pk.data, pk.offsets, threads=4)
+    want2 = np.array([oracle.o2(regs[r], w) for r, w in zip(rid, strs)], np.uint8)
+    want1 = np.array([oracle.o1(regs[r], w) for r, w in zip(rid, strs)], np.uint8)
+    assert (got == want2).all() and (want1 == want2).all()
+    assert 0 < got.sum() < len(got)
