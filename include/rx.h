@@ -167,18 +167,46 @@ rx_status rx_tree(rx_handle h, rx_node* out, size_t cap, size_t* n);
 
 /* ---------------------------------------------------------------- matching */
 /*
+ * Device offsets.  String i of a device batch is strings[offsets[i] ..
+ * offsets[i+1]) (the w of the problem e |v w, Section 2).  The kernels check
+ * every pair: it is valid iff 0 <= offsets[i] <= offsets[i+1].  A string
+ * with an invalid pair is not read at all; its result is the marker
+ * RX_RESULT_INVALID (RX_SEARCH_INVALID for rx_search) and it is counted on
+ * the device, and rx_sync_check() returns RX_ERR_INVALID_ARG for it.  The
+ * size of the strings buffer is not passed, so offsets[n] <= that size is
+ * the caller's to guarantee.  (rx_match_host checks its host offsets before
+ * any copy and returns RX_ERR_INVALID_ARG directly.)
+ */
+#define RX_RESULT_INVALID 2
+#define RX_SEARCH_INVALID (-2)
+
+/*
+ * rx_sync_check -- synchronise `stream`, then read and clear the count of
+ * strings with invalid offsets (see above) that the kernels of any call on
+ * the current device have met since the last rx_sync_check.  The count is
+ * kept per device, not per stream or call: work still running on other
+ * streams may add to it.  *bad_strings (optional) receives the count.
+ * The paper has no counterpart (it concerns only the encoding of a batch).
+ * Errors: RX_ERR_INVALID_ARG when the count is > 0; RX_ERR_CUDA.
+ */
+rx_status rx_sync_check(void* stream, int64_t* bad_strings);
+
+/*
  * rx_match -- one expression against n strings (async).  out[i] = 1 iff
- * e |v w_i, else 0, where w_i = strings[offsets[i] .. offsets[i+1]).
+ * e |v w_i (Def 5.3: null in the evolved set after the last byte), else 0,
+ * where w_i = strings[offsets[i] .. offsets[i+1]); RX_RESULT_INVALID for a
+ * string whose offsets are invalid (see "Device offsets").
  *   strings  device, offsets[n] bytes, packed
  *   offsets  device, n+1 int64, non-decreasing, offsets[0] >= 0
  *   out      device, n bytes
+ *   h        compiled on the current device
  * The input bytes are read once; a string whose active set empties is not
- * read further (it is stuck, Fig 6.1).  Offsets are NOT validated on the
- * device: decreasing offsets are undefined behaviour.  Scratch space is
- * library-owned per stream and grows on demand (may synchronise the stream
- * the first time a larger batch is seen).
- * Errors: RX_ERR_INVALID_ARG (NULL pointers with n > 0, host-only handle),
- * RX_ERR_OOM, RX_ERR_CUDA (launch failure).
+ * read further (it is stuck, Fig 6.1).  Scratch space is library-owned per
+ * stream and grows on demand (may synchronise the stream the first time a
+ * larger batch is seen).
+ * Errors: RX_ERR_INVALID_ARG (NULL pointers with n > 0, host-only handle,
+ * handle compiled on another device), RX_ERR_OOM, RX_ERR_CUDA (launch
+ * failure).  Invalid offsets are reported by rx_sync_check.
  */
 rx_status rx_match(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets, uint8_t* out,
                    void* stream);
@@ -212,7 +240,10 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
  * scratch in one fixed 4 MiB array compiled into the library: every GPU that
  * loads the library holds that array until the process exits.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
- *   Arguments, layout and result: as rx_match (async on `stream`).
+ *   Arguments, layout and result: as rx_match (async on `stream`); the
+ *   offsets are checked the same way (RX_RESULT_INVALID, rx_sync_check).
+ *   The handle must have been compiled on the current device (else
+ *   RX_ERR_INVALID_ARG).
  *   Limit: at most 262,144 strings per call; larger n returns
  *   RX_ERR_TOO_LARGE with nothing launched.
  *   The first call on a device looks up the array's device address with
@@ -261,7 +292,8 @@ rx_status rx_match_host(rx_handle h, size_t n, const uint8_t* strings, const int
  * added back after every byte (Defs 5.1-5.3 on the Sigma* e machine), as a
  * cache of macro steps built when the handle is compiled with
  * RX_COMPILE_SEARCH (at most 192 states).
- *   strings/offsets as in rx_match; out_end DEVICE int64[n].
+ *   strings/offsets as in rx_match; out_end DEVICE int64[n]
+ *   (RX_SEARCH_INVALID for a string with invalid offsets).
  * Errors: RX_ERR_INVALID_ARG, RX_ERR_UNSUPPORTED (no search cache: flag
  * missing, or the cache would exceed 192 states), RX_ERR_OOM, RX_ERR_CUDA.
  */
@@ -297,10 +329,17 @@ int64_t rx_device_faults(int32_t reset);
 
 /*
  * rx_match_batch -- n (expression, string) pairs in one persistent launch
- * (async).  handles is a HOST array of n handles (pair i uses handles[i]);
- * strings/offsets/out as in rx_match.  Pairs are bucketed by variant and
- * length, ordered longest first, and drained by a device work queue; the
- * queue and the tables of all distinct handles are uploaded once per call.
+ * (async).  out[i] = 1 iff pair i's own expression matches its string
+ * (e |v w, Fig 2.1, decided by the lockstep machine: null in the evolved
+ * set after the last byte, Def 5.3), else 0; RX_RESULT_INVALID for invalid
+ * offsets.  handles is a HOST array of n handles (pair i uses handles[i]);
+ * strings/offsets/out as in rx_match.  Pairs are bucketed by variant class
+ * and length and ordered by serial work per lane (classes whose lanes walk
+ * a whole string, longest first; then cached pairs up to the long-pair
+ * threshold; then long cached pairs, a warp each, chunked), and drained by
+ * a device work queue; the tables of all distinct handles are uploaded
+ * once per call.  The paper has no counterpart for the batching (its
+ * closing section names persistent threads and task queues as future work).
  * Errors: as rx_match.
  */
 rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
@@ -308,8 +347,9 @@ rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* stri
 
 /*
  * rx_match_pairs -- the plain form: one kernel launch per pair, in order
- * (async).  Same arguments and result as rx_match_batch; kept as the
- * comparison point for the batched form.
+ * (async).  Same arguments and result as rx_match_batch (Def 5.3 for each
+ * pair's own expression, Fig 2.1); kept as the comparison point for the
+ * batched form.
  */
 rx_status rx_match_pairs(const rx_handle* handles, size_t n, const uint8_t* strings, const int64_t* offsets,
                          uint8_t* out, void* stream);
@@ -424,6 +464,13 @@ typedef struct {
 } rx_serve_stats_t;
 
 typedef struct rx_server rx_server;
+
+/* Every request of a server is decided as rx_match decides a string: 1 iff
+ * its expression matches its whole payload (e |v w, Fig 2.1; null in the
+ * evolved set after the last byte, Def 5.3), else 0.  Continuous batching
+ * itself has no counterpart in the paper; a request's saved active set
+ * between ticks is the machine state of Def 5.2 after the bytes read so
+ * far, so resuming it is exact. */
 
 /* rx_serve_create -- start a continuous-batching server on the current
  * device (its own host thread and CUDA stream).  Errors: RX_ERR_INVALID_ARG,

@@ -28,6 +28,8 @@ VARIANT_NAMES = {0: "auto", 1: "memo", 2: "thread", 3: "sparse", 4: "warp", 5: "
 COMPILE_HOST_ONLY = 1
 COMPILE_NO_MEMO = 2
 COMPILE_SEARCH = 4
+RESULT_INVALID = 2      # result byte of a string with invalid offsets
+SEARCH_INVALID = -2     # rx_search result of a string with invalid offsets
 
 STATUS = {0: "RX_OK", 1: "RX_ERR_PARSE", 2: "RX_ERR_INVALID_ARG", 3: "RX_ERR_TOO_LARGE", 4: "RX_ERR_OOM",
           5: "RX_ERR_CUDA", 6: "RX_ERR_TIMEOUT", 7: "RX_ERR_BUSY", 8: "RX_ERR_UNSUPPORTED"}
@@ -88,6 +90,7 @@ SIGNATURES = {
     "rx_match_static": ([P, SZ, P, P, P, P], I32),
     "rx_match_host": ([P, SZ, P, P, P, P], I32),
     "rx_device_faults": ([I32], I64),
+    "rx_sync_check": ([P, ctypes.POINTER(I64)], I32),
     "rx_search": ([P, SZ, P, P, P, P], I32),
     "rx_search_long": ([P, P, I64, I64, P, P], I32),
     "rx_match_batch": ([P, SZ, P, P, P, P], I32),
@@ -269,6 +272,18 @@ def search_long(rx: Regex, text, length: int, out_end, chunk_bytes: int = 0, str
 def device_faults(reset: bool = False) -> int:
     """Bounded device waits that gave up since the last reset (0 normally)."""
     return int(lib().rx_device_faults(1 if reset else 0))
+
+
+def sync_check(stream=None, raise_error: bool = True) -> int:
+    """Synchronise the stream and return (clearing it) the device's count of
+    strings the kernels found with invalid offsets since the last check.
+    A non-zero count raises RxError (RX_ERR_INVALID_ARG) unless
+    raise_error is False."""
+    bad = I64(0)
+    st = lib().rx_sync_check(_stream(stream), ctypes.byref(bad))
+    if st != 0 and (raise_error or st != 2):
+        raise RxError(st, last_error())
+    return int(bad.value)
 
 
 def match_host(rx: Regex, strings, offsets, out, n: int | None = None, stream=None):

@@ -166,6 +166,12 @@ static rx_status upload(rx_regex* h) {
     h->dev_self = reinterpret_cast<const DevTables*>(b + o_self);
     e = cudaMemcpy(b + o_self, &t, sizeof(DevTables), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy table header");
+    // the kernels' counter of invalid offsets is looked up once per device,
+    // here, so that no later call (possibly under stream capture) does it
+    if (!bad_offsets_counter()) {
+        set_error("cudaGetSymbolAddress of the invalid-offsets counter failed");
+        return RX_ERR_CUDA;
+    }
     return RX_OK;
 }
 
@@ -188,6 +194,20 @@ int resolve_variant(const rx_regex* h, int v) {
     return RX_VARIANT_WARP;
 }
 
+// The handle's tables live on the device it was compiled on; a kernel on
+// another device would be given that device's addresses.
+bool on_handle_device(const rx_regex* h, const char* who) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    if (dev == h->device) return true;
+    set_error(std::string(who) + ": handle was compiled on device " + std::to_string(h->device) +
+              ", current device is " + std::to_string(dev));
+    return false;
+}
+
 }  // namespace rx
 
 using namespace rx;
@@ -201,6 +221,11 @@ static rx_status match_paper(rx_handle h, size_t n, const uint8_t* strings, cons
     cudaError_t e = cudaMemcpyAsync(off.data(), offsets, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "rx_match (paper): offsets read-back");
+    for (size_t i = 0; i < n; i++)
+        if (off[i] < 0 || off[i + 1] < off[i]) {
+            set_error("rx_match (paper): invalid offsets at string " + std::to_string(i));
+            return RX_ERR_INVALID_ARG;
+        }
     size_t need = (2 * (size_t)(h->dev.nn + 1) + 4) * sizeof(int);
     void* ws = nullptr;
     rx_status s = get_workspace(st, need, &ws);
@@ -218,22 +243,6 @@ static rx_status match_paper(rx_handle h, size_t n, const uint8_t* strings, cons
     if (e != cudaSuccess) return cuda_fail(e, "rx_match (paper): results");
     return RX_OK;
 }
-
-#define RX_GUARD_BEGIN try {
-#define RX_GUARD_END                                  \
-    }                                                 \
-    catch (const std::bad_alloc&) {                   \
-        set_error("host allocation failed");          \
-        return RX_ERR_OOM;                            \
-    }                                                 \
-    catch (const std::exception& ex) {                \
-        set_error(std::string("internal: ") + ex.what()); \
-        return RX_ERR_INVALID_ARG;                    \
-    }                                                 \
-    catch (...) {                                     \
-        set_error("internal error");                  \
-        return RX_ERR_INVALID_ARG;                    \
-    }
 
 extern "C" {
 
@@ -359,6 +368,7 @@ rx_status rx_match_ex(rx_handle h, size_t n, const uint8_t* strings, const int64
         return RX_ERR_INVALID_ARG;
     }
     if (n == 0) return RX_OK;
+    if (!on_handle_device(h, "rx_match")) return RX_ERR_INVALID_ARG;
     if (!offsets || !out) {
         set_error("rx_match: null offsets or out");
         return RX_ERR_INVALID_ARG;
@@ -442,6 +452,25 @@ rx_status rx_search_long(rx_handle h, const uint8_t* str, int64_t len, int64_t c
     if (s != RX_OK) return s;
     cudaError_t e = rx::launch_search_long(h->dev, str, len, C, out_end, ws, need, st);
     if (e != cudaSuccess) return cuda_fail(e, "rx_search_long launch");
+    return RX_OK;
+    RX_GUARD_END
+}
+
+rx_status rx_sync_check(void* stream, int64_t* bad_strings) {
+    RX_GUARD_BEGIN
+    if (bad_strings) *bad_strings = 0;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rx_sync_check: stream synchronisation");
+    const unsigned long long bad = rx::read_bad_offsets(true);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rx_sync_check: counter read");
+    if (bad_strings) *bad_strings = (int64_t)bad;
+    if (bad) {
+        set_error("rx_sync_check: " + std::to_string(bad) +
+                  " string(s) with invalid offsets (offsets[i] < 0 or offsets[i+1] < offsets[i]); "
+                  "their results hold RX_RESULT_INVALID / RX_SEARCH_INVALID");
+        return RX_ERR_INVALID_ARG;
+    }
     return RX_OK;
     RX_GUARD_END
 }

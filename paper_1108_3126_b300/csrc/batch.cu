@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchTab* __restrict__ t
                                                const uint32_t* __restrict__ perm, const unsigned* __restrict__ starts,
                                                long long n, const uint8_t* __restrict__ str,
                                                const int64_t* __restrict__ off, uint8_t* __restrict__ out,
-                                               unsigned* __restrict__ queue, int stride, uint8_t* __restrict__ maps) {
+                                               unsigned* __restrict__ queue, int stride, uint8_t* __restrict__ maps,
+                                               unsigned long long* __restrict__ bad) {
     __shared__ long long seg[kBatchClasses + 1];
     __shared__ long long tfirst[kBatchClasses + 1];
     if (threadIdx.x == 0) {
@@ -65,6 +66,18 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchTab* __restrict__ t
         int c = 0;
         while (c + 1 < kBatchClasses && (long long)task >= tfirst[c + 1]) c++;
         const long long g = (long long)task - tfirst[c];
+        if (c == kClsMemoLong || c == kClsWarp) {
+            // one pair per warp: an invalid pair is answered by lane 0
+            const uint32_t p = perm[seg[c] + g];
+            uint64_t s, e;
+            if (!string_span(off, p, base, s, e)) {
+                if (lane == 0) {
+                    out[p] = kResultInvalid;
+                    count_bad(bad);
+                }
+                continue;
+            }
+        }
         if (c == kClsMemoLong) {
             const uint32_t p = perm[seg[c] + g];
             const DevTables& t = tabs[pair_tab[p]].t;
@@ -86,14 +99,19 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchTab* __restrict__ t
             continue;
         }
         const long long idx = seg[c] + g * 32 + lane;
-        const bool valid = idx < seg[c + 1];
+        bool valid = idx < seg[c + 1];
         const uint32_t p = valid ? perm[idx] : perm[seg[c]];
         const DevTables& t = tabs[pair_tab[p]].t;
         uint64_t s = base, e = base;
+        bool ok = true;
         if (valid) {
-            s += (uint64_t)off[p];
-            e += (uint64_t)off[p + 1];
+            ok = string_span(off, p, base, s, e);
+            if (!ok) {
+                out[p] = kResultInvalid;
+                count_bad(bad);
+            }
         }
+        valid = valid && ok;
         switch (c) {
         case kClsMemo: {
             MemoStep8 st;
@@ -210,10 +228,10 @@ cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t*
     if (profile) {
         ProfScope ps(st);
         k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
-                                                    b.queue, L.stride, maps);
+                                                    b.queue, L.stride, maps, bad_offsets_counter());
     } else {
         k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
-                                                    b.queue, L.stride, maps);
+                                                    b.queue, L.stride, maps, bad_offsets_counter());
         prof_count(1);
     }
     return cudaGetLastError();

@@ -42,7 +42,8 @@ using namespace rx::dev;
 template <class S>
 __global__ void __launch_bounds__(256) k_thread(const DevTables t, const uint8_t* __restrict__ str,
                                                 const int64_t* __restrict__ off, const uint32_t* __restrict__ perm,
-                                                long long n, uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
+                                                long long n, uint8_t* __restrict__ out, unsigned* __restrict__ queue,
+                                                unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) uint8_t smem[];
     S::load(t, smem);
     __syncthreads();
@@ -62,12 +63,13 @@ __global__ void __launch_bounds__(256) k_thread(const DevTables t, const uint8_t
         // alignment of `str`; a block is read only if it holds string bytes
         const uint64_t base = reinterpret_cast<uint64_t>(str);
         uint64_t s = base, e = base;
-        if (valid) {
-            s += (uint64_t)off[id];
-            e += (uint64_t)off[id + 1];
+        const bool ok = !valid || string_span(off, id, base, s, e);
+        if (!ok) {
+            out[id] = kResultInvalid;
+            count_bad(bad);
         }
         S st = proto;
-        run_lane(st, s, e, valid, out + id);
+        run_lane(st, s, e, valid && ok, out + id);
     }
 }
 
@@ -79,7 +81,8 @@ __global__ void __launch_bounds__(256) k_thread(const DevTables t, const uint8_t
 template <int K>
 __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* __restrict__ str,
                                               const int64_t* __restrict__ off, const uint32_t* __restrict__ perm,
-                                              long long n, uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
+                                              long long n, uint8_t* __restrict__ out, unsigned* __restrict__ queue,
+                                              unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int W = t.W;
     const size_t bw = (size_t)256 * W, fw = (size_t)t.nbits * W;
@@ -101,7 +104,14 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
         if ((long long)task >= n) break;
         long long id = perm ? (long long)perm[task] : (long long)task;
         const uint64_t base = reinterpret_cast<uint64_t>(str);
-        const uint64_t s = base + (uint64_t)off[id], e = base + (uint64_t)off[id + 1];
+        uint64_t s, e;
+        if (!string_span(off, id, base, s, e)) {  // warp-uniform
+            if (lane == 0) {
+                out[id] = kResultInvalid;
+                count_bad(bad);
+            }
+            continue;
+        }
         bool acc = warp_string<K>(t, B, follow, s, e);
         if (lane == 0) out[id] = acc;
     }
@@ -378,7 +388,7 @@ cudaError_t launch_thread_kernel(const DevTables& t, long long n, const uint8_t*
     if (grid < 1) grid = 1;
     {
         ProfScope ps(st);
-        kern<<<(unsigned)grid, block, sm, st>>>(t, str, off, perm, n, out, queue);
+        kern<<<(unsigned)grid, block, sm, st>>>(t, str, off, perm, n, out, queue, bad_offsets_counter());
     }
     return cudaGetLastError();
 }
@@ -399,7 +409,7 @@ cudaError_t launch_warp_kernel(const DevTables& t, long long n, const uint8_t* s
     long long cap = (n * 32 + block - 1) / block;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, block, sm, st>>>(t, str, off, perm, n, out, queue);
+    kern<<<(unsigned)grid, block, sm, st>>>(t, str, off, perm, n, out, queue, bad_offsets_counter());
     return cudaGetLastError();
 }
 
@@ -508,6 +518,36 @@ int plan_blocks(size_t n) {
 size_t plan_workspace_bytes(size_t n, int nclasses) {
     size_t nbk = (size_t)kLenBuckets * nclasses;
     return align16((2 * nbk + 1) * 4) + align16(nbk * 4) + align16(n * 4);
+}
+
+// strings whose offsets the kernels found invalid (rx_sync_check), per device
+__device__ unsigned long long g_bad_offsets;
+
+unsigned long long* bad_offsets_counter() {
+    static std::mutex mu;
+    static unsigned long long* addr[128] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bad_offsets) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        addr[dev] = static_cast<unsigned long long*>(p);
+    }
+    return addr[dev];
+}
+
+unsigned long long read_bad_offsets(bool reset) {
+    unsigned long long v = 0;
+    cudaMemcpyFromSymbol(&v, g_bad_offsets, sizeof(v));
+    if (reset && v) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(g_bad_offsets, &z, sizeof(z));
+    }
+    return v;
 }
 
 unsigned read_plan_faults(bool reset) {

@@ -143,6 +143,11 @@ cudaError_t paper_match_one(const DevTables& t, const uint8_t* str, int64_t len,
 unsigned read_wait_faults(bool reset);
 // Grid barriers of the one-launch planner that gave up (likewise).
 unsigned read_plan_faults(bool reset);
+// Device address (current device) of the counter of strings with invalid
+// offsets, which every kernel that reads offsets receives; and its value,
+// optionally cleared (synchronous).
+unsigned long long* bad_offsets_counter();
+unsigned long long read_bad_offsets(bool reset);
 
 // Device properties cached per device.
 int sm_count();

@@ -14,6 +14,7 @@
 
 namespace rx {
 int resolve_variant(const rx_regex* h, int v);
+bool on_handle_device(const rx_regex* h, const char* who);
 void set_error(const std::string& msg);
 }  // namespace rx
 
@@ -57,6 +58,7 @@ rx_status static_scratch(void** out) {
 
 extern "C" rx_status rx_match_static(rx_handle h, size_t n, const uint8_t* strings, const int64_t* offsets,
                                      uint8_t* out, void* stream) {
+    RX_GUARD_BEGIN
     if (!h || h->host_only) {
         rx::set_error("rx_match_static: null or host-only handle");
         return RX_ERR_INVALID_ARG;
@@ -66,6 +68,9 @@ extern "C" rx_status rx_match_static(rx_handle h, size_t n, const uint8_t* strin
         rx::set_error("rx_match_static: null offsets or out");
         return RX_ERR_INVALID_ARG;
     }
+    // the tables' addresses belong to the compile device, and the array's
+    // address is looked up on the current one: they must be the same
+    if (!rx::on_handle_device(h, "rx_match_static")) return RX_ERR_INVALID_ARG;
     if (n > kStaticMaxStrings) {
         rx::set_error("rx_match_static: " + std::to_string(n) + " strings exceed the limit of " +
                       std::to_string(kStaticMaxStrings) + " per call (use rx_match, which allocates)");
@@ -91,4 +96,5 @@ extern "C" rx_status rx_match_static(rx_handle h, size_t n, const uint8_t* strin
         return RX_ERR_CUDA;
     }
     return RX_OK;
+    RX_GUARD_END
 }

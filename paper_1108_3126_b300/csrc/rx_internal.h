@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -117,6 +119,24 @@ rx_status parse_pattern(const char* pat, size_t len, std::vector<rx_node>& nodes
 void set_error(const std::string& msg);
 
 }  // namespace rx
+
+// Body of every extern "C" entry point: no C++ exception leaves the ABI
+// (an allocation failure is RX_ERR_OOM, anything else an internal error).
+#define RX_GUARD_BEGIN try {
+#define RX_GUARD_END                                      \
+    }                                                     \
+    catch (const std::bad_alloc&) {                       \
+        rx::set_error("host allocation failed");          \
+        return RX_ERR_OOM;                                \
+    }                                                     \
+    catch (const std::exception& ex) {                    \
+        rx::set_error(std::string("internal: ") + ex.what()); \
+        return RX_ERR_INVALID_ARG;                        \
+    }                                                     \
+    catch (...) {                                         \
+        rx::set_error("internal error");                  \
+        return RX_ERR_INVALID_ARG;                        \
+    }
 
 struct rx_regex {
     rx::Compiled host;

@@ -32,6 +32,28 @@ __device__ inline void copy_to_smem(void* dst, const void* src, size_t bytes) {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// ------------------------------------------------------------- offsets
+// String id of a batch is w = bytes[off[id] .. off[id+1]) (the problem
+// statement e |v w of Section 2, one string per pair of offsets).  The pair
+// is valid iff 0 <= off[id] <= off[id+1]; the kernels do not know the size
+// of the bytes buffer, so off[n] is the caller's to keep inside it.  On a
+// valid pair [s, e) are the absolute addresses of its bytes; on an invalid
+// one s = e = base, so the lane reads nothing, and the kernel writes the
+// marker result and counts the string in *bad (one atomic per bad string).
+__device__ __forceinline__ bool string_span(const int64_t* __restrict__ off, long long id, uint64_t base,
+                                            uint64_t& s, uint64_t& e) {
+    const int64_t a = off[id], b = off[id + 1];
+    const bool ok = a >= 0 && b >= a;
+    s = base + (ok ? (uint64_t)a : 0ull);
+    e = base + (ok ? (uint64_t)b : 0ull);
+    return ok;
+}
+// result byte of a string with invalid offsets (RX_RESULT_INVALID of rx.h)
+constexpr uint8_t kResultInvalid = 2;
+// search result of a string with invalid offsets (RX_SEARCH_INVALID of rx.h)
+constexpr int64_t kSearchInvalid = -2;
+__device__ __forceinline__ void count_bad(unsigned long long* bad) { atomicAdd(bad, 1ull); }
+
 // ------------------------------------------------------------- steppers
 // A stepper holds one active set and advances it by one byte.  Interface:
 //   smem_bytes(t) / load(t, smem) / bind(t, smem)   tables in shared memory

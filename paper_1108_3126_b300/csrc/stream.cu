@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK, has_pairs<S>::value ? 3 : 1)
     k_stream(const DevTables t, const uint8_t* __restrict__ str,
                                                          const int64_t* __restrict__ off,
                                                          const uint32_t* __restrict__ perm, long long n,
-                                                         uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
+                                                         uint8_t* __restrict__ out, unsigned* __restrict__ queue,
+                                                         unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) uint8_t smem[];
     S::load(t, smem);
     __syncthreads();
@@ -187,13 +188,11 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK, has_pairs<S>::value ? 3 : 1)
         const bool valid = k < n;
         const long long id = valid ? (perm ? (long long)perm[k] : k) : 0;
         uint64_t s = base, e = base;
-        if (valid) {
-            s += (uint64_t)off[id];
-            e += (uint64_t)off[id + 1];
-        }
+        const bool ok = !valid || string_span(off, id, base, s, e);
         S st = proto;
-        bool active = valid && s < e;
-        if (valid && !active) out[id] = st.accept();
+        bool active = valid && ok && s < e;
+        if (valid && !active) out[id] = ok ? (uint8_t)st.accept() : kResultInvalid;
+        if (!ok) count_bad(bad);
         if (!active) st.kill();
         uint64_t blk = s & ~uint64_t(31);
         Blk32 va = ld_blk(blk, active);
@@ -290,7 +289,8 @@ template <class S, int CH, int NST>
 __global__ void __launch_bounds__(1024, 1) k_stream_tma(const DevTables t, const uint8_t* __restrict__ str,
                                                      const int64_t* __restrict__ off,
                                                      const uint32_t* __restrict__ perm, long long n,
-                                                     uint8_t* __restrict__ out, unsigned* __restrict__ queue) {
+                                                     uint8_t* __restrict__ out, unsigned* __restrict__ queue,
+                                                     unsigned long long* __restrict__ bad) {
     static_assert(CH % 32 == 0, "steps of whole 32-byte blocks");
     using Lay = TmaLayout<CH, NST>;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -320,13 +320,11 @@ __global__ void __launch_bounds__(1024, 1) k_stream_tma(const DevTables t, const
         const bool valid = k < n;
         const long long id = valid ? (perm ? (long long)perm[k] : k) : 0;
         uint64_t s = base, e = base;
-        if (valid) {
-            s += (uint64_t)off[id];
-            e += (uint64_t)off[id + 1];
-        }
+        const bool ok = !valid || string_span(off, id, base, s, e);
         S st = proto;
-        bool active = valid && s < e;
-        if (valid && !active) out[id] = st.accept();
+        bool active = valid && ok && s < e;
+        if (valid && !active) out[id] = ok ? (uint8_t)st.accept() : kResultInvalid;
+        if (!ok) count_bad(bad);
         if (!active) st.kill();
         const uint64_t blk0 = s & ~uint64_t(31);
         // steps of CH bytes this lane needs, and the round's
@@ -422,7 +420,8 @@ __device__ __forceinline__ int search32(SearchS& st, const Blk32& v, uint32_t ma
 __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_search(const DevTables t, const uint8_t* __restrict__ str,
                                                            const int64_t* __restrict__ off,
                                                            const uint32_t* __restrict__ perm, long long n,
-                                                           int64_t* __restrict__ out, unsigned* __restrict__ queue) {
+                                                           int64_t* __restrict__ out, unsigned* __restrict__ queue,
+                                                           unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) uint8_t smem[];
     SearchS::load(t, smem);
     __syncthreads();
@@ -440,14 +439,12 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_search(const DevTables t, 
         const bool valid = k < n;
         const long long id = valid ? (perm ? (long long)perm[k] : k) : 0;
         uint64_t s = base, e = base;
-        if (valid) {
-            s += (uint64_t)off[id];
-            e += (uint64_t)off[id + 1];
-        }
+        const bool ok = !valid || string_span(off, id, base, s, e);
+        if (!ok) count_bad(bad);
         SearchS st = proto;
-        int64_t found = -1;
-        if (valid && st.accepted()) found = 0;  // the empty substring at 0
-        bool active = valid && found < 0 && s < e;
+        int64_t found = ok ? -1 : kSearchInvalid;
+        if (valid && ok && st.accepted()) found = 0;  // the empty substring at 0
+        bool active = valid && found == -1 && s < e;
         uint64_t blk = s & ~uint64_t(31);
         Blk32 va = ld_blk(blk, active);
         Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
@@ -649,7 +646,8 @@ cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str,
     long long grid = std::min<long long>((rounds * 32 + block - 1) / block, (long long)per_sm * sm_count());
     {
         ProfScope ps(st);
-        kern<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, off, perm, n, out, queue);
+        kern<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, off, perm, n, out, queue,
+                                                                        bad_offsets_counter());
     }
     return cudaGetLastError();
 }
@@ -667,7 +665,8 @@ cudaError_t launch_search_k(const DevTables& t, long long n, const uint8_t* str,
     long long grid = std::min<long long>((rounds * 32 + block - 1) / block, (long long)per_sm * sm_count());
     {
         ProfScope ps(st);
-        k_search<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, off, perm, n, out, queue);
+        k_search<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, off, perm, n, out, queue,
+                                                                             bad_offsets_counter());
     }
     return cudaGetLastError();
 }
@@ -694,7 +693,8 @@ cudaError_t launch_stream_tma_t(const DevTables& t, long long n, const uint8_t* 
     long long grid = std::min<long long>((rounds + nw - 1) / nw, (long long)per_sm * sm_count());
     {
         ProfScope ps(st);
-        kern<<<(unsigned)std::max<long long>(grid, 1), nw * 32, sm, st>>>(t, str, off, perm, n, out, queue);
+        kern<<<(unsigned)std::max<long long>(grid, 1), nw * 32, sm, st>>>(t, str, off, perm, n, out, queue,
+                                                                          bad_offsets_counter());
     }
     return cudaGetLastError();
 }

@@ -137,7 +137,7 @@ def test_device_payload_mode():
     srv.close()
 
 
-def test_serving_full_scale_replay_sampled():
+def test_serving_full_scale_replay_vs_o2():
     """The serving workload at its full scale: 2000 pool expressions plus
     expressions compiled on arrival (20% of requests), 20,000 requests at
     200k req/s through native paced replay, device-resident payloads drawn
