@@ -1,18 +1,27 @@
 """Benchmark: matched input GB/s of the lockstep matcher on B300.
 
-Default workload (N=1): one random 64-node expression over a..z against
+Headline workload (N=1): one random 64-node expression over a..z against
 1,048,576 strings with lengths uniform in [1, 1024] (~537 MB packed, int64
 offsets), half language samples and half edited language samples, seeded.
 A step is one call of the public batch entry point (rx_match: length-sort
 planner + lockstep kernel + accept) over the whole batch, inputs resident in
 HBM (537 MB, larger than the 126 MB L2, so no flush is needed between steps).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload streaming|small|batched|long|serving]
+At N=1 the same JSON line also carries, under "configs", the other four
+workloads: small (16 nodes, 4096 strings; with Section 8's machine timed on
+a sample), batched (10,000 expressions, 148,077 pairs, prepared batch against
+one launch per pair), long (1 GiB text, chunked against sequential) and
+serving (Poisson sweep, device and host payloads, against one synchronous
+call per request), each with its roofline fraction, the oracle on the host
+cores and the clocks seen.  --workload runs one of them alone.
 
-Under torchrun each rank runs the same workload on its own GPU (replicas,
-weak scaling); rank 0 prints one JSON line.  --impl reference times the CPU
-oracle (the Fig 6.1 machine) on a bounded sample of the same workload.
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload streaming|small|batched|long|serving] [--no-extra]
+
+Under torchrun each rank runs the headline workload on its own GPU
+(replicas, weak scaling); rank 0 prints one JSON line.  --impl reference
+times the CPU oracle (the Fig 6.1 machine) on a bounded sample of the
+headline workload.
 """
 from __future__ import annotations
 
@@ -45,15 +54,13 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
 # capture, keyed by a hash of that kernel's sources at capture time (null
-# when they have changed since).  k_stream<MemoPairP>: 132.16 MB per launch
-# on the 262,144-string capture (136.81 MB algorithmic), scaled by
-# algorithmic bytes to the full 1,048,576-string launch (546.80 MB): 528.2 MB.
-TRAFFIC = {("k_stream<MemoPairP>", "fd4d133c8e539c5c"): 528.2e6}
+# when they have changed since).
+TRAFFIC = {}
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("stream.cu", "steppers.cuh", "rx_internal.h"):
+    for f in ("stream.cu", "steppers.cuh", "rx_internal.h", "plan.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1108_3126_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -240,13 +247,18 @@ def run_streaming(args, world, rank, local):
     def step():
         rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=variant)
 
+    step()
+    torch.cuda.synchronize(dev)
+    # the clock sampler starts first; the warm-up steps then run right before
+    # the timed region, so the GPU is busy (not ramping up from idle) when
+    # timing begins
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
     rx.profile_read()
-    clocks = Clocks(local)
-    clocks.start()
-    time.sleep(0.3)
     rx.profile_enable(True)
     if world > 1:
         dist.barrier()
@@ -265,8 +277,8 @@ def run_streaming(args, world, rank, local):
     clk = clocks.stop()
     ms = max_over_ranks(ms, world, dev)
     value = world * total_bytes / (ms * 1e-3) / 1e9
-    # the two timed kernels of a step: phase 1 (k_chunk_stage) and phase 2
-    # (k_span_tasks); composition and launch gaps are the rest of the step
+    # the timed kernel of a step is the streaming kernel (one launch per
+    # step); the planner and the launch gaps are the rest of the step
     kernel_ms = kms / max(args.steps, 1)
     alg_bytes = total_bytes + 8 * (n + 1) + n
     peak, peak_kind = peaks()
@@ -275,19 +287,21 @@ def run_streaming(args, world, rank, local):
 
     # the other kernel variants on the same batch (informational)
     variants = {}
-    for name, v, blk in ((("memo_pair", 1, 0), ("memo_pair_tma32x3", 1, 4),
-                          ("memo_pair_tma64x2", 1, 12), ("memo_pair_tma64x3", 1, 20), ("memo_single", 1, 257),
-                          ("thread", 2, 0), ("sparse", 3, 0), ("warp", 4, 0)) if not args.quick else ()):
+    for name, v, blk, srt in ((("memo_pair", 1, 0, -1), ("memo_pair_planner_apart", 1, 0, 2),
+                               ("memo_pair_tma32x3", 1, 4, -1), ("memo_pair_tma64x2", 1, 12, -1),
+                               ("memo_pair_tma64x3", 1, 20, -1), ("memo_single", 1, 257, -1),
+                               ("thread", 2, 0, -1), ("sparse", 3, 0, -1), ("warp", 4, 0, -1))
+                              if not args.quick else ()):
         if not (info["variants"] >> v) & 1:
             continue
         reps = max(3, min(50, args.steps // 20))
         for _ in range(2):
-            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v, block=blk)
+            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v, block=blk, sort=srt)
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(reps):
-            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v, block=blk)
+            rx.match(r, d_str, d_off, d_out, n=n, stream=stream, variant=v, block=blk, sort=srt)
         b.record(stream)
         torch.cuda.synchronize(dev)
         vms = a.elapsed_time(b) / reps
@@ -357,7 +371,8 @@ def run_streaming(args, world, rank, local):
     chosen_v = tuned["variant"] if tuned else (variant or (1 if info["memo_states"] else 2))
     chosen_b = tuned["block"] if tuned else 0
     kname = {1: ("k_stream<MemoS>" if (chosen_b & 1) or not info.get("pair", True) else
-                 "k_stream_tma<MemoPairP>" if chosen_b & 28 else "k_stream<MemoPairP>"),
+                 "k_stream_tma<MemoPairP>" if chosen_b & 28 else
+                 "k_stream_local<MemoPairP>" if chosen_b in (0, 768) and n >= 4096 else "k_stream<MemoPairP>"),
              2: "k_stream<Thread1S|Thread2S>", 3: "k_thread<SparseStep>", 4: "k_warp"}[chosen_v]
     src_hash = kernel_source_hash()
     traffic = TRAFFIC.get((kname, src_hash))
@@ -390,6 +405,15 @@ def run_streaming(args, world, rank, local):
         "accepted": accepted,
         "kernel_src": src_hash,
     }
+    # the other four configurations (N=1 only), each with its forms, roofline
+    # fraction, oracle baseline and clocks, as extra keys of this line
+    if world == 1 and not args.quick and not args.no_extra:
+        extra = {}
+        for name, fn in CONFIG_RESULTS.items():
+            t0 = time.perf_counter()
+            extra[name] = fn(args, dev)
+            extra[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        line["configs"] = extra
     print(json.dumps(line))
 
 
@@ -413,13 +437,152 @@ def _time(fn, reps, stream, dev):
     return a.elapsed_time(b) / reps
 
 
-def run_batched(args, world, rank, local):
-    """10,000 expressions x 1-64 strings each, one persistent launch
-    (rx_match_batch) against one launch per pair (rx_match_pairs)."""
+def _timed(fn, stream, dev, min_s: float = 0.3, max_reps: int = 2000, min_reps: int = 3):
+    """Mean ms of fn over enough repetitions to last about min_s (CUDA
+    events on `stream`), and the number of repetitions."""
+    one = _time(fn, 1, stream, dev)
+    reps = int(max(min_reps, min(max_reps, (min_s * 1e3) / max(one, 1e-3))))
+    return _time(fn, reps, stream, dev), reps
+
+
+def _roofline(alg_bytes, kernel_ms, kernel, step_ms=None):
+    peak, kind = peaks()
+    ach = alg_bytes / (kernel_ms * 1e-3) / 1e9 if kernel_ms else None
+    d = {"bound": "hbm", "kernel": kernel, "kernel_ms": round(kernel_ms, 5) if kernel_ms else None,
+         "algorithmic_bytes_per_launch": int(alg_bytes), "achieved": round(ach, 1) if ach else None,
+         "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None,
+         "peak_source": f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else "fallback 6.4 TB/s"}
+    if step_ms:
+        d["step_frac"] = round(alg_bytes / (step_ms * 1e-3) / 1e9 / peak, 4)
+    return d
+
+
+def _cpu_o2(fn_sample, budget_s: float, k0: int = 1):
+    """Time the oracle's O2 (as it stands) on a bounded sample: fn_sample(k)
+    runs O2 on the first k units and returns (bytes, description, all units
+    done); k grows until one run takes about budget_s.  Returns (GB/s,
+    description) of the last run."""
+    k = k0
+    while True:
+        t = time.perf_counter()
+        nbytes, desc, done = fn_sample(k)
+        dt = time.perf_counter() - t
+        if dt >= 0.5 * budget_s or done:
+            return nbytes / max(dt, 1e-9) / 1e9, desc
+        k = max(k + 1, int(k * min(16.0, budget_s / max(dt, 1e-3))))
+
+
+def cfg_small_result(args, dev):
+    """Config 1 (plain method, small): one 16-node expression over {a,b,c},
+    4096 strings of 0-256 bytes.  The streaming form (rx_match), the batched
+    form (rx_match_batch and a prepared batch), the plain form (one launch
+    per pair), Section 8's machine (one launch per micro-step, a sample of
+    strings), the oracle on the host cores; plus the plain form's per-launch
+    cost on 1-byte strings."""
     import torch
+    import oracle
     import paper_1108_3126_b300 as rx
     import synth
-    dev = _dev_setup(local)
+    w = synth.cfg_small()
+    nodes, s = w.regexes[0], w.strings
+    n, total = s.n, int(s.offsets[-1])
+    r = rx.Regex.from_nodes(nodes)
+    d_str = torch.from_numpy(s.data).to(dev)
+    d_off = torch.from_numpy(s.offsets).to(dev)
+    out = torch.zeros(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    want = oracle.o2_batch(nodes, s.data, s.offsets)
+    clocks = Clocks(dev.index)
+    clocks.start()
+    forms = {}
+
+    def check(name):
+        torch.cuda.synchronize(dev)
+        if not (out.cpu().numpy() == want).all():
+            raise SystemExit(f"config 1: {name} disagrees with O2")
+
+    for _ in range(3):
+        rx.match(r, d_str, d_off, out, n=n, stream=stream)
+    check("rx_match")
+    rx.profile_read()
+    rx.profile_enable(True)
+    ms, reps = _timed(lambda: rx.match(r, d_str, d_off, out, n=n, stream=stream), stream, dev)
+    rx.profile_enable(False)
+    launches, timed, kms = rx.profile_read()
+    kernel_ms = kms / max(timed, 1)
+    forms["streaming"] = {"ms": round(ms, 5), "GB/s": round(total / (ms * 1e-3) / 1e9, 3),
+                          "launches_per_call": round(launches / reps, 2)}
+    hs = rx.handle_array([r] * n)
+    rx.match_batch(hs, d_str, d_off, out, stream=stream)
+    check("rx_match_batch")
+    ms_b, _ = _timed(lambda: rx.match_batch(hs, d_str, d_off, out, stream=stream), stream, dev)
+    forms["batched_call"] = {"ms": round(ms_b, 5), "GB/s": round(total / (ms_b * 1e-3) / 1e9, 3)}
+    plan = rx.Batch(hs)
+    plan.run(d_str, d_off, out, stream=stream)
+    check("prepared batch")
+    ms_p, _ = _timed(lambda: plan.run(d_str, d_off, out, stream=stream), stream, dev)
+    plan.free()
+    forms["batched_prepared"] = {"ms": round(ms_p, 5), "GB/s": round(total / (ms_p * 1e-3) / 1e9, 3)}
+    out.fill_(7)
+    rx.match_pairs(hs, d_str, d_off, out, stream=stream)
+    check("rx_match_pairs")
+    ms_pl = _time(lambda: rx.match_pairs(hs, d_str, d_off, out, stream=stream), 2, stream, dev)
+    forms["plain_per_pair"] = {"ms": round(ms_pl, 3), "GB/s": round(total / (ms_pl * 1e-3) / 1e9, 4),
+                               "launches": n, "us_per_pair": round(1e3 * ms_pl / n, 2)}
+    # the plain form's fixed cost per pair: the same number of 1-byte strings
+    one = synth.pack([b"a"] * n)
+    o_str, o_off = torch.from_numpy(one.data).to(dev), torch.from_numpy(one.offsets).to(dev)
+    ms_1 = _time(lambda: rx.match_pairs(hs, o_str, o_off, out, stream=stream), 2, stream, dev)
+    forms["plain_per_pair"]["us_per_pair_1_byte"] = round(1e3 * ms_1 / n, 2)
+    # Section 8's machine: one launch per micro-step, flags read back by the
+    # host; timed on the first strings of the batch
+    k = args.paper_strings
+    sub = synth.Strings(s.data[:s.offsets[k]], s.offsets[:k + 1], s.kind[:k], 0)
+    p_str, p_off = torch.from_numpy(sub.data).to(dev), torch.from_numpy(sub.offsets).to(dev)
+    pout = torch.zeros(k, dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    rx.match(r, p_str, p_off, pout, n=k, stream=stream, variant=rx.VARIANT_PAPER)
+    torch.cuda.synchronize(dev)
+    pdt = time.perf_counter() - t0
+    if not (pout.cpu().numpy() == want[:k]).all():
+        raise SystemExit("config 1: Section 8 machine disagrees with O2")
+    pbytes = int(sub.offsets[-1])
+    forms["paper_section8"] = {"strings": k, "bytes": pbytes, "s": round(pdt, 3),
+                               "GB/s": round(pbytes / pdt / 1e9, 6), "ms_per_string": round(1e3 * pdt / k, 2)}
+    clk = clocks.stop()
+    # the oracle on the host cores, the whole batch repeated to ~2 s
+    cores = len(os.sched_getaffinity(0))
+
+    def o2_rep(kk):
+        for _ in range(kk):
+            oracle.o2_batch(nodes, s.data, s.offsets, threads=cores)
+        return kk * total, f"the whole batch x{kk}, O2 on {cores} threads", False
+
+    cpu_v, cpu_desc = _cpu_o2(o2_rep, 2.0)
+    t = time.perf_counter()
+    oracle.o1_batch(nodes, s.data, s.offsets, threads=cores)
+    o1_gbs = total / (time.perf_counter() - t) / 1e9
+    st = forms["streaming"]
+    return {"workload": "small: 1 regex x 16 AST nodes (depth<=6) over {a,b,c}; 4096 strings L~U[0,256], "
+                        "half language samples, half uniform random",
+            "value": st["GB/s"], "unit": "GB/s", "ms_per_step": st["ms"], "strings": n, "total_bytes": total,
+            "accepted": int(want.sum()), "forms": forms,
+            "roofline": _roofline(total + 8 * (n + 1) + n, kernel_ms, "k_stream (rx_match)", st["ms"]),
+            "batched_over_plain": round(ms_pl / ms_p, 1), "streaming_over_paper_section8":
+                round(st["GB/s"] / max(forms["paper_section8"]["GB/s"], 1e-12), 1),
+            "cpu_baseline": {"value": cpu_v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": cpu_desc,
+                             "o1_big_step_GB/s": round(o1_gbs, 5)},
+            "clocks": clk, "parity": "every string equal to O2 (each form)"}
+
+
+def cfg_batched_result(args, dev):
+    """Config 3: 10,000 expressions x 1-64 strings each, one persistent
+    launch (prepared batch replayed from its captured graph, after the
+    launch-shape autotuner), against one launch per pair."""
+    import torch
+    import oracle
+    import paper_1108_3126_b300 as rx
+    import synth
     t0 = time.perf_counter()
     w = synth.cfg_batched(n_regex=args.regexes)
     gen_s = time.perf_counter() - t0
@@ -433,69 +596,92 @@ def run_batched(args, world, rank, local):
     d_off = torch.from_numpy(s.offsets).to(dev)
     out = torch.zeros(n, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    # one call per step, nothing prepared (tables and classes uploaded, the
-    # launches issued one by one)
-    for _ in range(args.warmup):
+    clocks = Clocks(dev.index)
+    clocks.start()
+    # one call per step, nothing prepared
+    for _ in range(3):
         rx.match_batch(hs, d_str, d_off, out, stream=stream)
     rx.profile_read()
     rx.profile_enable(True)
-    ms_call = _time(lambda: rx.match_batch(hs, d_str, d_off, out, stream=stream), args.steps, stream, dev)
+    ms_call, _ = _timed(lambda: rx.match_batch(hs, d_str, d_off, out, stream=stream), stream, dev)
     rx.profile_enable(False)
     launches, timed, kms = rx.profile_read()
+    kernel_ms = kms / max(timed, 1)
     res_batch = out.cpu().numpy().copy()
     # prepared batch: expressions fixed once, every step a replay of the
-    # captured graph (after the launch-shape autotuner with --autotune)
+    # captured graph, after the launch-shape autotuner
     plan = rx.Batch(hs)
-    tuned = plan.autotune(d_str, d_off, out, stream=stream) if args.autotune else None
-    for _ in range(args.warmup):
+    tuned = plan.autotune(d_str, d_off, out, stream=stream) if not args.no_autotune else None
+    for _ in range(3):
         plan.run(d_str, d_off, out, stream=stream)
-    ms = _time(lambda: plan.run(d_str, d_off, out, stream=stream), args.steps, stream, dev)
+    ms, reps = _timed(lambda: plan.run(d_str, d_off, out, stream=stream), stream, dev)
     if not (out.cpu().numpy() == res_batch).all():
         raise SystemExit("prepared batch disagrees with rx_match_batch")
     plan.free()
-    plain_ms = None
-    if not args.quick:
-        out.fill_(7)
-        rx.match_pairs(hs, d_str, d_off, out, stream=stream)  # warm
-        plain_ms = _time(lambda: rx.match_pairs(hs, d_str, d_off, out, stream=stream), 1, stream, dev)
-        assert (out.cpu().numpy() == res_batch).all(), "batched and plain forms disagree"
+    out.fill_(7)
+    rx.match_pairs(hs, d_str, d_off, out, stream=stream)  # warm
+    plain_ms = _time(lambda: rx.match_pairs(hs, d_str, d_off, out, stream=stream), 1, stream, dev)
+    if not (out.cpu().numpy() == res_batch).all():
+        raise SystemExit("batched and plain forms disagree")
+    clk = clocks.stop()
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(0x5EED0003)
+    perm = rng.permutation(n)
+
+    def o2_pairs(kk):
+        kk = min(kk, n)
+        idx = np.sort(perm[:kk])
+        sub = synth.pack([s.get(int(i)) for i in idx])
+        got = oracle.o2_pairs(w.regexes, w.regex_of[idx], sub.data, sub.offsets, threads=cores)
+        if not (got == res_batch[idx]).all():
+            raise SystemExit("batched form disagrees with O2")
+        mb = int(sub.offsets[-1]) / 1e6
+        return int(sub.offsets[-1]), f"{kk} random pairs ({mb:.1f} MB), O2 on {cores} threads, equal to the GPU", \
+            kk >= n
+
+    cpu_v, cpu_desc = _cpu_o2(o2_pairs, args.cpu_seconds, 2000)
     infos = [h.info() for h in handles]
-    line = {"metric": METRIC, "workload": "batched", "value": round(total / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"batched uneven: {len(handles)} regexes 8-512 AST nodes (log-uniform, depth<=12, "
-                                   "5% (eps*|e)* loops) over 256 bytes; 1-64 strings each, L log-uniform 1 B-64 KiB",
-                       "pairs": n, "total_bytes": total, "positions_max": max(i["positions"] for i in infos),
-                       "memo_share": sum(1 for i in infos if i["memo_states"]) / len(infos),
-                       "gen_s": round(gen_s, 1), "compile_s": round(compile_s, 2)},
-            "plain_per_pair": None if plain_ms is None else
-            {"ms": round(plain_ms, 2), "GB/s": round(total / (plain_ms * 1e-3) / 1e9, 3), "launches": n},
-            "batched_over_plain": None if plain_ms is None else round(plain_ms / ms, 1),
-            "kernel_ms": round(kms / max(timed, 1), 4), "gpu_launches_per_step": launches / args.steps,
+    for h in handles:
+        h.free()
+    value = total / (ms * 1e-3) / 1e9
+    return {"workload": f"batched uneven: {len(handles)} regexes 8-512 AST nodes (log-uniform, depth<=12, "
+                        "5% (eps*|e)* loops) over 256 bytes; 1-64 strings each, L log-uniform 1 B-64 KiB",
+            "value": round(value, 2), "unit": "GB/s", "ms_per_step": round(ms, 4), "steps": reps,
+            "pairs": n, "total_bytes": total, "positions_max": max(i["positions"] for i in infos),
+            "memo_share": round(sum(1 for i in infos if i["memo_states"]) / len(infos), 3),
+            "gen_s": round(gen_s, 1), "compile_s": round(compile_s, 2),
             "form": "prepared batch, graph replay" + (" (autotuned)" if tuned else ""), "autotune": tuned,
-            "unprepared_call": {"ms": round(ms_call, 4), "GB/s": round(total / (ms_call * 1e-3) / 1e9, 2)}}
-    if rank == 0:
-        print(json.dumps(line))
+            "unprepared_call": {"ms": round(ms_call, 4), "GB/s": round(total / (ms_call * 1e-3) / 1e9, 2),
+                                "gpu_launches_per_call": launches / max(timed, 1)},
+            "plain_per_pair": {"ms": round(plain_ms, 2), "GB/s": round(total / (plain_ms * 1e-3) / 1e9, 3),
+                               "launches": n, "us_per_pair": round(1e3 * plain_ms / n, 2)},
+            "batched_over_plain": round(plain_ms / ms, 1),
+            "roofline": _roofline(total + 8 * (n + 1) + n, kernel_ms, "k_batch (unprepared call)", ms),
+            "cpu_baseline": {"value": cpu_v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": cpu_desc},
+            "clocks": clk, "accepted": int(res_batch.sum())}
 
 
-def run_long(args, world, rank, local):
-    """One 1 GiB text against (R)* with 48 positions: exact chunked mode
-    (rx_match_long) against the one-thread sequential run (rx_match_seq)."""
+def cfg_long_result(args, dev):
+    """Config 4: one 1 GiB text against (R)* with 48 positions: exact
+    chunked mode (rx_match_long) against the one-thread sequential run
+    (rx_match_seq), the oracle on one host core."""
     import torch
+    import oracle
     import paper_1108_3126_b300 as rx
     import synth
-    dev = _dev_setup(local)
     nodes, text, end = synth.cfg_long(total=args.long_bytes, with_end=True)
     r = rx.Regex.from_nodes(nodes)
     d = torch.from_numpy(text).to(dev)
     n = len(text)
     out = torch.zeros(1, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    clocks = Clocks(dev.index)
+    clocks.start()
+    for _ in range(3):
         rx.match_long(r, d, n, out, stream=stream)
     rx.profile_read()
     rx.profile_enable(True)
-    ms = _time(lambda: rx.match_long(r, d, n, out, stream=stream), args.steps, stream, dev)
+    ms, reps = _timed(lambda: rx.match_long(r, d, n, out, stream=stream), stream, dev)
     rx.profile_enable(False)
     launches, timed, kms = rx.profile_read()
     chunked = int(out.item())
@@ -506,9 +692,10 @@ def run_long(args, world, rank, local):
     agree_prefix = int(out.item())
     rx.match_seq(r, d, pre, out, stream=stream)
     torch.cuda.synchronize(dev)
-    assert int(out.item()) == agree_prefix
-    # the mean size of the active set (positions + null) along the first
-    # 256 KiB, from the set trace (one set per byte, GPU)
+    if int(out.item()) != agree_prefix:
+        raise SystemExit("chunked and sequential runs disagree")
+    clk = clocks.stop()
+    # mean size of the active set along the first 256 KiB (GPU set trace)
     tl = min(n, 256 << 10)
     W = r.tables()["words"]
     rows = torch.zeros((tl + 1) * W, dtype=torch.int32, device=dev)
@@ -516,52 +703,80 @@ def run_long(args, world, rank, local):
     torch.cuda.synchronize(dev)
     rw = rows.cpu().numpy().view(np.uint32)
     mean_active = float(np.unpackbits(rw.view(np.uint8)).sum()) / (tl + 1)
-    # chunked unanchored search over the same text for a literal planted
-    # near its end (the whole text is scanned), informational
-    search = None
-    lit = b"zqzqzq"
-    rs = rx.Regex.compile(lit, rx.COMPILE_SEARCH)
-    if rs.info()["search_states"]:
-        p = n - 1000
-        d[p:p + len(lit)] = torch.tensor(list(lit), dtype=torch.uint8, device=dev)
-        d_end = torch.empty(1, dtype=torch.int64, device=dev)
-        rx.search_long(rs, d, n, d_end, stream=stream)
-        sms = _time(lambda: rx.search_long(rs, d, n, d_end, stream=stream), max(3, args.steps), stream, dev)
-        search = {"GB/s": round(n / (sms * 1e-3) / 1e9, 1), "ms": round(sms, 4), "found_end": int(d_end.item()),
-                  "planted_end": p + len(lit)}
-    rs.free()
-    peak, _ = peaks()
-    # the two timed kernels of a step: phase 1 (k_chunk_stage) and phase 2
-    # (k_span_tasks); composition and launch gaps are the rest of the step
-    kernel_ms = kms / max(args.steps, 1)
-    line = {"metric": METRIC, "workload": "long", "value": round(n / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "long text: (R)* with 48 positions over a..z, one text of concatenated language "
-                                   "samples of R", "bytes": n, "memo_states": r.info()["memo_states"],
-                       "accepted": chunked, "last_whole_sample_end": end,
-                       "mean_active_set": round(mean_active, 2),
-                       "mean_active_set_over": f"first {tl} bytes (positions + null, from rx_trace)"},
+
+    def o2_prefix(kk):
+        nb = min(n, kk << 20)
+        want = oracle.o2(nodes, text[:nb])
+        rx.match_long(r, d, nb, out, stream=stream)
+        torch.cuda.synchronize(dev)
+        if int(out.item()) != int(want):
+            raise SystemExit("chunked mode disagrees with O2 on a prefix")
+        return nb, f"first {nb >> 20} MiB of the text, O2 on 1 thread (equal to the chunked GPU result)", nb >= n
+
+    cpu_v, cpu_desc = _cpu_o2(o2_prefix, args.cpu_seconds, 4)
+    kernel_ms = kms / max(reps, 1)
+    return {"workload": "long text: (R)* with 48 positions over a..z, one 1 GiB text of concatenated language "
+                        "samples of R", "value": round(n / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms, 4), "steps": reps, "bytes": n, "memo_states": r.info()["memo_states"],
+            "accepted": chunked, "last_whole_sample_end": end, "mean_active_set": round(mean_active, 2),
             "sequential_gpu": {"bytes": pre, "ms": round(seq_ms, 2), "GB/s": round(pre / (seq_ms * 1e-3) / 1e9, 4)},
             "chunked_over_sequential": round((n / ms) / (pre / seq_ms), 1),
-            "roofline": {"bound": "hbm", "kernel": "k_chunk_stage + k_span_tasks", "kernel_ms": round(kernel_ms, 4),
-                         "achieved": round(n / (kernel_ms * 1e-3) / 1e9, 1), "peak": peak,
-                         "frac": round(n / (kernel_ms * 1e-3) / 1e9 / peak, 4),
-                         "step_frac": round(n / (ms * 1e-3) / 1e9 / peak, 4)},
-            "gpu_launches_per_step": launches / args.steps, "search_long": search}
-    if rank == 0:
-        print(json.dumps(line))
+            "roofline": _roofline(n, kernel_ms, "k_chunk_stage + k_span_tasks (timed kernels of a step)", ms),
+            "gpu_launches_per_step": launches / max(reps, 1),
+            "cpu_baseline": {"value": cpu_v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": cpu_desc},
+            "clocks": clk}
 
 
-def run_serving(args, world, rank, local):
-    """Poisson arrivals of (regex, string) requests over a pool of 2000
-    compiled expressions (80% reuse; 20% compiled on arrival), payloads
-    resident on the device, swept over arrival rates; p50/p99 latency and
-    throughput, against the plain per-request form."""
+def _serving_sweep(rx, pool, owners, datas, bufs, fresh_nodes, rates, args, payload_mode, rng):
+    """One Poisson replay per arrival rate through a new server; bufs are the
+    payloads as the mode takes them (device tensors for mode 1, page-locked
+    host tensors for mode 2)."""
+    points, compile_us, fresh_all = [], [], []
+    for rate in rates:
+        nreq = int(min(args.max_requests, max(200, rate * args.seconds)))
+        arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        pick = rng.integers(0, len(datas), nreq)
+        reuse = rng.random(nreq) < 0.8
+        handles = np.zeros(nreq, np.uint64)
+        for k in range(nreq):
+            if reuse[k]:
+                handles[k] = pool[int(owners[int(pick[k])])].handle
+            else:
+                # an expression outside the pool: compiled on arrival (cost reported separately)
+                t0 = time.perf_counter()
+                h = rx.Regex.from_nodes(fresh_nodes[k % len(fresh_nodes)])
+                compile_us.append((time.perf_counter() - t0) * 1e6)
+                fresh_all.append(h)
+                handles[k] = h.handle
+        payloads = np.array([bufs[int(p)].data_ptr() for p in pick], np.uint64)
+        lens = np.array([len(datas[int(p)]) for p in pick], np.int64)
+        srv = rx.Server(max_inflight=8192, device_payload=payload_mode)
+        _, late = srv.replay(handles, payloads, lens, (arrive * 1e9).astype(np.int64))
+        srv.drain(600000)
+        st = srv.stats()
+        srv.close()
+        points.append({"rate_target": rate, "requests": nreq, "submit_late_ms": round(late / 1e6, 3),
+                       "req_per_s": round(st["req_per_s"], 1), "GB/s": round(st["gb_per_s"], 2),
+                       "offered_GB/s": round(rate * float(lens.mean()) / 1e9, 2),
+                       "p50_ms": round(st["p50_ns"] / 1e6, 3), "p99_ms": round(st["p99_ns"] / 1e6, 3),
+                       "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
+                       "mean_bytes": int(lens.mean())})
+    for h in fresh_all:
+        h.free()
+    return points, compile_us
+
+
+def cfg_serving_result(args, dev):
+    """Config 5: Poisson arrivals of (regex, string) requests over a pool of
+    2000 compiled expressions (80% reuse; 20% compiled on arrival), swept
+    over arrival rates, with payloads resident on the device and with
+    payloads in page-locked host memory (read by the server when it admits a
+    request, payload mode 2); p50/p99 latency and throughput, against the
+    plain per-request form."""
     import torch
+    import oracle
     import paper_1108_3126_b300 as rx
     import synth
-    dev = _dev_setup(local)
     pool_nodes = synth.serving_pool(pool=args.pool)
     pool = [rx.Regex.from_nodes(nd) for nd in pool_nodes]
     rng = np.random.default_rng(0x5EED0005)
@@ -573,71 +788,95 @@ def run_serving(args, world, rank, local):
     for k in range(npay):
         s = synth.gen_strings(pool_nodes[owners[k]], 1, int(lens[k]), int(lens[k]), synth.ALL_BYTES,
                               synth.item_seed(0x5EED0005, 10 + k), p_lang=0.5)
-        datas.append(s.data)
+        datas.append(np.ascontiguousarray(s.data))
     dbufs = [torch.from_numpy(np.concatenate([x, np.zeros(16, np.uint8)])).to(dev) for x in datas]
+    hbufs = [torch.from_numpy(x).pin_memory() for x in datas]
     torch.cuda.synchronize(dev)
     fresh_nodes = [synth.gen_regex(int(np.exp(rng.uniform(np.log(8), np.log(1025)))), 14, synth.ALL_BYTES,
                                    synth.item_seed(0x5EED0005, 100000 + k)) for k in range(4096)]
-    points = []
-    fresh_all = []
-    compile_us = []
-    for rate in args.rates:
-        nreq = int(min(args.max_requests, max(200, rate * args.seconds)))
-        arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
-        pick = rng.integers(0, npay, nreq)
-        reuse = rng.random(nreq) < 0.8
-        handles = np.zeros(nreq, np.uint64)
-        for k in range(nreq):
-            if reuse[k]:
-                handles[k] = pool[int(owners[int(pick[k])])].handle
-            else:
-                # a regex outside the pool: compiled on arrival (cost reported separately)
-                t0 = time.perf_counter()
-                h = rx.Regex.from_nodes(fresh_nodes[k % len(fresh_nodes)])
-                compile_us.append((time.perf_counter() - t0) * 1e6)
-                fresh_all.append(h)
-                handles[k] = h.handle
-        payloads = np.array([dbufs[int(p)].data_ptr() for p in pick], np.uint64)
-        lens = np.array([len(datas[int(p)]) for p in pick], np.int64)
-        srv = rx.Server(max_inflight=8192, device_payload=True)
-        _, late = srv.replay(handles, payloads, lens, (arrive * 1e9).astype(np.int64))
-        srv.drain(600000)
-        st = srv.stats()
-        srv.close()
-        points.append({"rate_target": rate, "requests": nreq, "submit_late_ms": round(late / 1e6, 3),
-                       "req_per_s": round(st["req_per_s"], 1), "GB/s": round(st["gb_per_s"], 2),
-                       "p50_ms": round(st["p50_ns"] / 1e6, 3), "p99_ms": round(st["p99_ns"] / 1e6, 3),
-                       "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
-                       "mean_bytes": int(lens.mean())})
+    clocks = Clocks(dev.index)
+    clocks.start()
+    dev_points, compile_us = _serving_sweep(rx, pool, owners, datas, dbufs, fresh_nodes, args.rates, args, 1,
+                                            np.random.default_rng(0x5EED0015))
+    host_points, _ = _serving_sweep(rx, pool, owners, datas, hbufs, fresh_nodes, args.rates, args, 2,
+                                    np.random.default_rng(0x5EED0015))
     # plain per-request form: one synchronous call per request
     out = torch.zeros(1, dtype=torch.uint8, device=dev)
-    off = torch.zeros(2, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
     lat = []
     nb = 0
+    prng = np.random.default_rng(0x5EED0025)
     t0 = time.perf_counter()
     for k in range(args.plain_requests):
-        p = int(rng.integers(0, npay))
+        p = int(prng.integers(0, npay))
         ts = time.perf_counter()
-        rx.match_long(pool[int(owners[p])], dbufs[p], len(datas[p]), out, stream=stream) \
-            if len(datas[p]) > (1 << 20) else rx.match_seq(pool[int(owners[p])], dbufs[p], len(datas[p]), out,
-                                                           stream=stream)
+        if len(datas[p]) > (1 << 20):
+            rx.match_long(pool[int(owners[p])], dbufs[p], len(datas[p]), out, stream=stream)
+        else:
+            rx.match_seq(pool[int(owners[p])], dbufs[p], len(datas[p]), out, stream=stream)
         torch.cuda.synchronize(dev)
         lat.append(time.perf_counter() - ts)
         nb += len(datas[p])
     el = time.perf_counter() - t0
-    best = max(points, key=lambda q: q["req_per_s"])
-    line = {"metric": METRIC, "workload": "serving", "value": best["GB/s"], "unit": "GB/s", "n_gpus": world,
-            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"serving: Poisson arrivals, pool of {len(pool)} regexes 8-1024 nodes, 80% reuse, "
-                                   f"payloads log-uniform 16 B-16 MiB ({npay} device-resident payloads)"},
-            "sweep": points,
-            "plain_per_request": {"requests": args.plain_requests, "req_per_s": round(args.plain_requests / el, 1),
+    clk = clocks.stop()
+    # the host-to-device link (a 256 MiB page-locked copy), the ceiling of
+    # the host-payload mode's input rate
+    hp = torch.empty(256 << 20, dtype=torch.uint8).pin_memory()
+    dp = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    dp.copy_(hp, non_blocking=True)
+    link_ms = _time(lambda: dp.copy_(hp, non_blocking=True), 5, stream, dev)
+    link_gbs = (256 << 20) / (link_ms * 1e-3) / 1e9
+    del hp, dp
+    # the oracle on the host cores: O2 on random requests' (expression, payload)
+    cores = len(os.sched_getaffinity(0))
+    order = np.random.default_rng(0x5EED0035).permutation(npay)
+
+    def o2_req(kk):
+        kk = min(kk, npay)
+        idx = order[:kk]
+        sub = synth.pack([datas[int(i)].tobytes() for i in idx])
+        oracle.o2_pairs([pool_nodes[int(owners[int(i)])] for i in idx], np.arange(kk, dtype=np.int32), sub.data,
+                        sub.offsets, threads=cores)
+        mb = int(sub.offsets[-1]) / 1e6
+        return int(sub.offsets[-1]), f"{kk} random payloads with their expressions ({mb:.1f} MB), O2 on {cores} " \
+                                     "threads", kk >= npay
+
+    cpu_v, cpu_desc = _cpu_o2(o2_req, args.cpu_seconds, 16)
+    best = max(dev_points, key=lambda q: q["req_per_s"])
+    best_h = max(host_points, key=lambda q: q["req_per_s"])
+    plain_rps = args.plain_requests / el
+    for h in pool:
+        h.free()
+    return {"workload": f"serving: Poisson arrivals, pool of {len(pool)} regexes 8-1024 nodes, 80% reuse, "
+                        f"payloads log-uniform 16 B-16 MiB ({npay} payloads)",
+            "value": best["GB/s"], "unit": "GB/s", "req_per_s": best["req_per_s"],
+            "sweep_device_payloads": dev_points, "sweep_host_payloads": host_points,
+            "host_link_GB/s": round(link_gbs, 1),
+            "link_note": "host payloads (mode 2, page-locked, borrowed until polled): every payload crosses the "
+                         "host link once, so the offered input exceeds the link above about link / mean bytes "
+                         "requests per second",
+            "plain_per_request": {"requests": args.plain_requests, "req_per_s": round(plain_rps, 1),
                                   "GB/s": round(nb / el / 1e9, 3),
                                   "p50_ms": round(1e3 * float(np.median(lat)), 3),
                                   "p99_ms": round(1e3 * float(np.quantile(lat, 0.99)), 3)},
-            "served_over_plain_req_per_s": round(best["req_per_s"] / (args.plain_requests / el), 1),
-            "compile_on_miss_us_mean": round(float(np.mean(compile_us)), 1) if compile_us else None}
+            "served_over_plain_req_per_s": round(best["req_per_s"] / plain_rps, 1),
+            "served_host_over_plain_req_per_s": round(best_h["req_per_s"] / plain_rps, 1),
+            "compile_on_miss_us_mean": round(float(np.mean(compile_us)), 1) if compile_us else None,
+            "cpu_baseline": {"value": cpu_v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": cpu_desc},
+            "clocks": clk}
+
+
+CONFIG_RESULTS = {"small": cfg_small_result, "batched": cfg_batched_result, "long": cfg_long_result,
+                  "serving": cfg_serving_result}
+
+
+def run_config(args, world, rank, local):
+    """One of the other configs alone: its own JSON line."""
+    dev = _dev_setup(local)
+    r = CONFIG_RESULTS[args.workload](args, dev)
+    line = {"metric": METRIC, "n_gpus": world, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "config": {"workload": r.pop("workload")}}
+    line.update(r)
     if rank == 0:
         print(json.dumps(line))
 
@@ -648,20 +887,26 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="streaming", choices=["streaming", "batched", "long", "serving"])
+    ap.add_argument("--workload", default="streaming", choices=["streaming", "small", "batched", "long", "serving"])
     ap.add_argument("--regexes", type=int, default=10000, help="batched: number of expressions")
     ap.add_argument("--long-bytes", type=int, default=1 << 30, help="long: text length")
     ap.add_argument("--seq-bytes", type=int, default=64 << 20, help="long: prefix timed sequentially")
     ap.add_argument("--pool", type=int, default=2000, help="serving: compiled expressions")
-    ap.add_argument("--payloads", type=int, default=768, help="serving: device-resident payloads")
+    ap.add_argument("--payloads", type=int, default=768, help="serving: payloads (device and host copies)")
     ap.add_argument("--rates", type=float, nargs="+", default=[1000, 3000, 10000, 30000, 100000, 200000])
     ap.add_argument("--seconds", type=float, default=0.5, help="serving: arrival window per rate")
     ap.add_argument("--max-requests", type=int, default=20000)
     ap.add_argument("--plain-requests", type=int, default=300)
+    ap.add_argument("--paper-strings", type=int, default=48, help="small: strings timed on Section 8's machine")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="CPU-baseline budget per config")
     ap.add_argument("--variant", default="auto", choices=["auto", "memo", "thread", "sparse", "warp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batched: skip the launch-shape autotuner")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="streaming: skip the other four configs (run by default at N=1)")
     ap.add_argument("--strings", type=int, default=1 << 20, help="batch size (default: the full workload)")
-    ap.add_argument("--quick", action="store_true", help="skip the variant sweep, e2e repeats and CPU baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the variant sweep, e2e repeats, CPU baseline and the other configs")
     ap.add_argument("--autotune", action="store_true", help="run the autotuner on the batch before timing")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -674,8 +919,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        {"streaming": run_streaming, "batched": run_batched, "long": run_long,
-         "serving": run_serving}[args.workload](args, world, rank, local)
+        if args.workload == "streaming":
+            run_streaming(args, world, rank, local)
+        else:
+            run_config(args, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -218,7 +218,12 @@ typedef struct {
                            one-byte-per-lookup kernel (block - 1 threads)    */
     int32_t sort;       /* -1 = auto, 0 = input order, 1 = length order +
                            per-variant kernel, 2 = length order + streaming
-                           kernel, 3 = streaming kernel in input order       */
+                           kernel, 3 = streaming kernel in input order, 4 =
+                           streaming kernel with a length order per block
+                           (one launch, no planner; memo variant with the
+                           two-byte cache, else as 2).  Auto: 4 for the memo
+                           variant and 2 for the thread variant from 4096
+                           strings, 3 below; 1 / 0 for the others          */
     int32_t len_hint;   /* mean string length if known (selects the tuned
                            entry of that length bucket), 0 = unknown         */
 } rx_match_opts;
@@ -444,7 +449,12 @@ typedef struct {
                                     per device tick (0 = 16 KiB); with k
                                     short requests in flight a tick covers
                                     tick_bytes * max(1, min(8, 8 / k))     */
-    int32_t device_payload;      /* 1: submit() bytes are device pointers  */
+    int32_t device_payload;      /* where submit()'s bytes live: 0 = host,
+                                    copied before submit returns; 1 = device,
+                                    valid until the result is polled; 2 =
+                                    host, borrowed until the result is
+                                    polled (no copy at submit; page-locked
+                                    memory is copied at full link speed)  */
     int32_t long_threshold;      /* requests longer than this (bytes) run
                                     the chunked mode (rx_match_long) on
                                     their own streams; 0 = 32 MiB.  Below
@@ -473,14 +483,15 @@ typedef struct rx_server rx_server;
  * far, so resuming it is exact. */
 
 /* rx_serve_create -- start a continuous-batching server on the current
- * device (its own host thread and CUDA stream).  Errors: RX_ERR_INVALID_ARG,
- * RX_ERR_OOM, RX_ERR_CUDA. */
+ * device (its own host thread and CUDA stream).  Errors: RX_ERR_INVALID_ARG
+ * (device_payload not 0, 1 or 2), RX_ERR_OOM, RX_ERR_CUDA. */
 rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out);
 
-/* rx_serve_submit -- enqueue one match (thread-safe).  `bytes` is host
- * memory (copied before the call returns) unless cfg.device_payload, in
- * which case it is a device pointer that must stay valid until the result
- * is polled.  The handle must outlive the request.  *ticket identifies the
+/* rx_serve_submit -- enqueue one match (thread-safe).  `bytes` is, by
+ * cfg.device_payload: 0, host memory copied before the call returns; 1, a
+ * device pointer; 2, host memory the server reads when it admits the
+ * request.  In modes 1 and 2 the bytes must stay valid until the result is
+ * polled.  The handle must outlive the request.  *ticket identifies the
  * result.  Errors: RX_ERR_BUSY (queue full), RX_ERR_INVALID_ARG, RX_ERR_OOM. */
 rx_status rx_serve_submit(rx_server* s, rx_handle h, const uint8_t* bytes, int64_t len, uint64_t* ticket);
 

@@ -414,7 +414,9 @@ class Server:
     """Continuous-batching matcher (rx_serve_*)."""
 
     def __init__(self, device_budget_bytes: int = 0, max_inflight: int = 256, queue_capacity: int = 65536,
-                 tick_bytes: int = 0, device_payload: bool = False, long_threshold: int = 0):
+                 tick_bytes: int = 0, device_payload=False, long_threshold: int = 0):
+        """device_payload: False/0 host bytes copied at submit, True/1 device
+        pointers, 2 host bytes borrowed until polled (pin them)."""
         cfg = ServeCfg(device_budget_bytes, max_inflight, queue_capacity, tick_bytes, int(device_payload),
                        long_threshold)
         h = P()

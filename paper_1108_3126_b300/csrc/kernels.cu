@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "plan.cuh"
 #include "steppers.cuh"
 
 namespace rx {
@@ -90,8 +91,8 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
     const uint32_t* B = t.B;
     const uint32_t* follow = t.follow;
     if (in_smem) {
-        copy_to_smem(smem, t.B, bw * 4);
-        copy_to_smem(smem + align16(bw * 4), t.follow, fw * 4);
+        copy_to_smem_serial(smem, t.B, bw * 4);
+        copy_to_smem_serial(smem + align16(bw * 4), t.follow, fw * 4);
         __syncthreads();
         B = reinterpret_cast<const uint32_t*>(smem);
         follow = reinterpret_cast<const uint32_t*>(smem + align16(bw * 4));
@@ -138,52 +139,7 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
 // of a tile are in flight together.  Within a bucket the order depends on
 // which block claims first; the kernels only need equal lengths within a
 // round of 32.
-constexpr int kPlanThreads = 512;
-constexpr int kPlanItems = 4;
-constexpr int kPlanTile = kPlanThreads * kPlanItems;
-
-// span = the string's length plus its start's offset in its 32-byte block:
-// below 2 KiB the bucket is the number of 32-byte blocks the string
-// touches, so the lanes of a round start and end their strings in the same
-// iteration of the kernels' block loops
-__device__ __forceinline__ int len_bucket(int64_t len) {
-    if (len < 2048) return (int)((len + 31) >> 5);
-    int lg = 63 - __clzll(len);  // >= 11
-    int b = 128 + 4 * (lg - 11) + (int)((len >> (lg - 2)) & 3);
-    return b < kLenBuckets ? b : kLenBuckets - 1;
-}
-
-// long_bytes: cached pairs longer than this go to kClsMemoLong
-// mis: the strings buffer's address mod 32
-__device__ __forceinline__ int plan_key(const int64_t* off, const uint8_t* cls, long long i, long long long_bytes,
-                                        int mis) {
-    const int64_t o = off[i], len = off[i + 1] - o;
-    int lb = len_bucket(len > 0 ? len + ((o + mis) & 31) : 0);
-    int c = cls ? (int)cls[i] : 0;
-    if (cls && c == kClsMemo && len > long_bytes) c = kClsMemoLong;
-    return c * kLenBuckets + (kLenBuckets - 1 - lb);
-}
-
-// keys of the tile at `base` (-1 past hi)
-__device__ __forceinline__ void plan_tile_keys(const int64_t* off, const uint8_t* cls, long long base, long long hi,
-                                               long long long_bytes, int mis, int (&key)[kPlanItems]) {
-#pragma unroll
-    for (int k = 0; k < kPlanItems; k++) {
-        const long long i = base + k * kPlanThreads + threadIdx.x;
-        key[k] = i < hi ? plan_key(off, cls, i, long_bytes, mis) : -1;
-    }
-}
-
-__device__ void plan_count(const int64_t* off, const uint8_t* cls, long long lo, long long hi, long long long_bytes,
-                           int mis, unsigned* sh) {
-    for (long long base = lo; base < hi; base += kPlanTile) {
-        int key[kPlanItems];
-        plan_tile_keys(off, cls, base, hi, long_bytes, mis, key);
-#pragma unroll
-        for (int k = 0; k < kPlanItems; k++)
-            if (key[k] >= 0) atomicAdd(&sh[key[k]], 1u);
-    }
-}
+using namespace rx::plan;
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __restrict__ off,
                                                             const uint8_t* __restrict__ cls, long long n,
@@ -199,50 +155,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_hist(const int64_t* __res
     __syncthreads();
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
         if (sh[b]) atomicAdd(&totals[b], sh[b]);
-}
-
-// exclusive scan of in[0..nbk) into out (shared), by the whole block
-__device__ void plan_block_scan(const unsigned* __restrict__ in, int nbk, unsigned* out) {
-    __shared__ unsigned wsum[kPlanThreads / 32];
-    const int per_t = (nbk + kPlanThreads - 1) / kPlanThreads;
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    unsigned sum = 0;
-    for (int j = 0; j < per_t; j++) {
-        const int b = t * per_t + j;
-        if (b < nbk) {
-            const unsigned v = __ldcg(in + b);
-            out[b] = v;
-            sum += v;
-        }
-    }
-    unsigned incl = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        unsigned w = lane < kPlanThreads / 32 ? wsum[lane] : 0u, wi = w;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned v = __shfl_up_sync(0xffffffffu, wi, d);
-            if (lane >= d) wi += v;
-        }
-        if (lane < kPlanThreads / 32) wsum[lane] = wi - w;
-    }
-    __syncthreads();
-    unsigned run = wsum[wid] + incl - sum;
-    for (int j = 0; j < per_t; j++) {
-        const int b = t * per_t + j;
-        if (b < nbk) {
-            const unsigned v = out[b];
-            out[b] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
 }
 
 // every block scans the totals itself (bucket starts), claims a range per
@@ -262,7 +174,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __
     __syncthreads();
     const long long lo = (long long)blockIdx.x * per, hi = min(lo + per, n);
     plan_count(off, cls, lo, hi, long_bytes, mis, sh);
-    plan_block_scan(totals, nbk, sc);
+    block_scan(totals, nbk, sc);
     if (blockIdx.x == 0)
         for (int b = threadIdx.x; b < nbk; b += kPlanThreads) starts[b] = sc[b];
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
@@ -278,36 +190,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_scatter(const int64_t* __
 }
 
 __device__ unsigned g_plan_faults;
-constexpr unsigned kBarrierSpins = 1u << 22;  // x >= 64 ns: about a quarter of a second
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// all blocks of the (cooperative) grid arrive; false if the wait gave up
-__device__ bool grid_barrier(unsigned* bar) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        int good = 1;
-        unsigned spins = 0;
-        while (ld_acquire(bar) < gridDim.x) {
-            if (++spins > kBarrierSpins) {
-                good = 0;
-                atomicAdd(&g_plan_faults, 1u);
-                break;
-            }
-            __nanosleep(64);
-        }
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan_one(const int64_t* __restrict__ off,
                                                            const uint8_t* __restrict__ cls, long long n, int nbk,
@@ -331,13 +213,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_one(const int64_t* __rest
     // (the value returned), so only the scan is left after the barrier
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads)
         if (sh[b]) sh[b] = atomicAdd(&totals[b], sh[b]);
-    if (!grid_barrier(bar)) {
+    if (!grid_barrier(bar, gridDim.x, &g_plan_faults)) {
 #pragma unroll
         for (int k = 0; k < kPlanItems; k++)
             if (key[k] >= 0) perm[base + k * kPlanThreads + threadIdx.x] = (uint32_t)(base + k * kPlanThreads + threadIdx.x);
         return;
     }
-    plan_block_scan(totals, nbk, sc);
+    block_scan(totals, nbk, sc);
     if (blockIdx.x == 0)
         for (int b = threadIdx.x; b < nbk; b += kPlanThreads) starts[b] = sc[b];
     for (int b = threadIdx.x; b < nbk; b += kPlanThreads) sh[b] += sc[b];
@@ -640,12 +522,14 @@ size_t match_workspace_bytes(size_t n, int sort) {
 
 int resolve_sort(int variant, int sort, size_t n) {
     const bool streams = variant == RX_VARIANT_MEMO || variant == RX_VARIANT_THREAD;
-    if (sort >= 0) {
-        if (sort >= 2 && !streams) return sort == 2 ? 1 : 0;
-        return sort;
+    if (sort < 0) {
+        if (variant == RX_VARIANT_MEMO) sort = n >= 4096 ? 4 : 3;
+        else if (variant == RX_VARIANT_THREAD) sort = n >= 4096 ? 2 : 3;
+        else sort = n >= 4096 ? 1 : 0;
     }
-    if (variant == RX_VARIANT_MEMO || variant == RX_VARIANT_THREAD) return n >= 4096 ? 2 : 3;
-    return n >= 4096 ? 1 : 0;
+    if (sort == 4 && variant != RX_VARIANT_MEMO) sort = 2;
+    if (sort >= 2 && !streams) return sort == 3 ? 0 : 1;
+    return sort;
 }
 
 cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_t* str, const int64_t* off,
@@ -656,7 +540,15 @@ cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_
     unsigned* queue = reinterpret_cast<unsigned*>(w);
     uint32_t* perm = nullptr;
     cudaError_t err = cudaSuccess;
-    if (sort != 1 && sort != 2) {  // with the planner, its scan kernel clears the counter
+    if (sort == 4) {  // block-local length order in the streaming kernel, else sort 2
+        bool launched = false;
+        if (block == 0 || block == 768) {
+            err = launch_stream_local(t, (long long)n, str, off, out, st, &launched);
+            if (err != cudaSuccess || launched) return err;
+        }
+        sort = 2;
+    }
+    if (sort != 1 && sort != 2) {  // with the planner, its first kernel clears the counter
         err = cudaMemsetAsync(w, 0, 256, st);
         if (err != cudaSuccess) return err;
     }

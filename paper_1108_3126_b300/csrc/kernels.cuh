@@ -20,7 +20,9 @@ struct Workspace {
 
 // Work order of rx_match: 0 = input order, 1 = global sort by length
 // (planner kernels) + the per-variant kernel, 2 = global sort + the
-// streaming kernel (memo and thread variants).
+// streaming kernel (memo and thread variants), 3 = the streaming kernel in
+// input order, 4 = the two-byte streaming kernel with a block-local length
+// order (memo variant; 2 where that kernel cannot run).
 int resolve_sort(int variant, int sort, size_t n);
 
 // Bytes of scratch rx_match needs for n strings.
@@ -29,6 +31,13 @@ size_t match_workspace_bytes(size_t n, int sort);
 // Single expression, n strings.  variant and sort are resolved.
 cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_t* str, const int64_t* off,
                          uint8_t* out, int sort, int block, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+// The two-byte streaming kernel with a block-local length order (memo
+// variant with the two-byte cache): one launch, no planner, no scratch.
+// *launched = false (nothing enqueued) when two of its blocks do not fit on
+// an SM beside the tables.
+cudaError_t launch_stream_local(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
+                                uint8_t* out, cudaStream_t st, bool* launched);
 
 // Streaming kernel (memo and thread variants); perm may be NULL.
 cudaError_t launch_stream(const DevTables& t, int variant, long long n, const uint8_t* str, const int64_t* off,

@@ -217,7 +217,8 @@ using namespace rx;
 struct Request {
     uint64_t ticket;
     rx_regex* h;
-    std::vector<uint8_t> host;  // host payload copy
+    std::vector<uint8_t> host;  // host payload copy (payload mode 0)
+    const uint8_t* hsrc = nullptr;  // caller's host payload (mode 2, borrowed)
     const uint8_t* dptr;        // device payload (caller's or ours)
     uint8_t* owned;             // device payload we allocated
     int64_t len;
@@ -309,7 +310,7 @@ void rx_server::run() {
             while (!pending.empty()) {
                 Request* r = pending.front();
                 bool lng = r->len > long_threshold && long_supported(r->h->dev);
-                int64_t need = (cfg.device_payload ? 0 : r->len);
+                int64_t need = (cfg.device_payload == 1 ? 0 : r->len);
                 if (lng) need += (int64_t)long_workspace_bytes(r->h->dev, r->len, long_chunk_auto(r->h->dev, r->len));
                 bool room = lng ? longs.size() < kMaxLong : !free_slots.empty();
                 if (!room || (inflight_bytes + need > budget && inflight_bytes > 0)) break;
@@ -327,7 +328,7 @@ void rx_server::run() {
         }
         // payload copies (copy stream) and long launches
         for (Request* r : admitted) {
-            if (!cfg.device_payload && r->len > 0) {
+            if (cfg.device_payload != 1 && r->len > 0) {
                 cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&r->owned), (size_t)r->len, copy_st);
                 if (e != cudaSuccess) {
                     cudaGetLastError();
@@ -336,7 +337,10 @@ void rx_server::run() {
                     complete(r, 0, RX_ERR_OOM);
                     continue;
                 }
-                cudaMemcpyAsync(r->owned, r->host.data(), (size_t)r->len, cudaMemcpyHostToDevice, copy_st);
+                // mode 0: our pageable copy (staged by the driver); mode 2:
+                // the caller's buffer, a direct DMA when it is page-locked
+                cudaMemcpyAsync(r->owned, cfg.device_payload == 2 ? r->hsrc : r->host.data(), (size_t)r->len,
+                                cudaMemcpyHostToDevice, copy_st);
                 r->dptr = r->owned;
             }
             if (r->is_long) {
@@ -477,6 +481,10 @@ rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out) {
             return RX_ERR_INVALID_ARG;
         }
         *out = nullptr;
+        if (cfg && (cfg->device_payload < 0 || cfg->device_payload > 2)) {
+            set_error("rx_serve_create: device_payload must be 0, 1 or 2");
+            return RX_ERR_INVALID_ARG;
+        }
         rx_server* s = new rx_server();
         if (cfg) s->cfg = *cfg;
         if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 1024;
@@ -533,8 +541,9 @@ rx_status rx_serve_submit(rx_server* s, rx_handle h, const uint8_t* bytes, int64
         r->h = h;
         r->len = len;
         r->owned = nullptr;
-        r->dptr = s->cfg.device_payload ? bytes : nullptr;
-        if (!s->cfg.device_payload && len > 0) r->host.assign(bytes, bytes + len);
+        r->dptr = s->cfg.device_payload == 1 ? bytes : nullptr;
+        r->hsrc = s->cfg.device_payload == 2 ? bytes : nullptr;
+        if (s->cfg.device_payload == 0 && len > 0) r->host.assign(bytes, bytes + len);
         r->t_submit = now_ns();
         uint64_t tk = 0;
         {

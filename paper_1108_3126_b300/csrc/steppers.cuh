@@ -22,11 +22,29 @@ __device__ __forceinline__ uint32_t byte_of(const uint4& v, int k) {
     return (w >> (8 * (k & 3))) & 0xffu;
 }
 
-// cooperative copy global -> shared (16-byte granules; sizes rounded up)
+// cooperative copy global -> shared (16-byte granules; sizes rounded up);
+// each thread issues four loads before it stores, so a table arrives in
+// about one memory latency per 64 bytes a thread copies
 __device__ inline void copy_to_smem(void* dst, const void* src, size_t bytes) {
+    const uint4* __restrict__ s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    const size_t n = (bytes + 15) / 16, stride = blockDim.x;
+    size_t i = threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        uint4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = __ldg(s + i + k * stride);
+#pragma unroll
+        for (int k = 0; k < 4; k++) d[i + k * stride] = v[k];
+    }
+    for (; i < n; i += stride) d[i] = __ldg(s + i);
+}
+// the same, one load at a time (for kernels whose register budget is
+// better spent elsewhere)
+__device__ inline void copy_to_smem_serial(void* dst, const void* src, size_t bytes) {
     const uint4* s = reinterpret_cast<const uint4*>(src);
     uint4* d = reinterpret_cast<uint4*>(dst);
-    size_t n = (bytes + 15) / 16;
+    const size_t n = (bytes + 15) / 16;
     for (size_t i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
 }
 

@@ -10,8 +10,12 @@
 // Input: every lane reads its string in aligned 32-byte blocks (one full
 // sector, two 16-byte loads) with loads issued two blocks ahead.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "kernels.cuh"
+#include "plan.cuh"
 #include "steppers.cuh"
 
 namespace rx {
@@ -162,20 +166,59 @@ __device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
     }
 }
 
-// the two-byte stepper is held to 40 registers: three 512-thread blocks
+// One round: lane l walks string `id` (valid: the lane has a string) from
+// its first 32-byte block to its end, or until its set empties (stuck), and
+// writes its result; the warp steps while any lane is active.
+template <class S>
+__device__ __forceinline__ void stream_round(const S& proto, uint64_t base, const int64_t* __restrict__ off,
+                                             long long id, bool valid, uint8_t* __restrict__ out,
+                                             unsigned long long* __restrict__ bad) {
+    uint64_t s = base, e = base;
+    const bool ok = !valid || string_span(off, id, base, s, e);
+    S st = proto;
+    bool active = valid && ok && s < e;
+    if (valid && !active) out[id] = ok ? (uint8_t)st.accept() : kResultInvalid;
+    if (!ok) count_bad(bad);
+    if (!active) st.kill();
+    uint64_t blk = s & ~uint64_t(31);
+    Blk32 va = ld_blk(blk, active);
+    Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
+    while (__any_sync(FULL, active)) {
+        // block A at blk, then block B at blk + 32; each buffer is
+        // refilled two blocks ahead right after it is consumed
+        block32(st, va, valid_mask(blk, s, e, active));
+        if (active && (blk + 32 >= e || st.dead())) {
+            out[id] = st.accept();
+            st.kill();
+            active = false;
+        }
+        va = ld_blk(blk + 64, active && blk + 64 < e);
+        if (!__any_sync(FULL, active)) break;
+        block32(st, vb, valid_mask(blk + 32, s, e, active));
+        if (active && (blk + 64 >= e || st.dead())) {
+            out[id] = st.accept();
+            st.kill();
+            active = false;
+        }
+        vb = ld_blk(blk + 96, active && blk + 96 < e);
+        blk += 64;
+    }
+}
+
+// the two-byte stepper is held to 40 registers: three 512-thread blocks// the two-byte stepper is held to 40 registers: three 512-thread blocks
 // (48 warps) per SM, which its shared memory (up to 3 planes) also allows
 template <class S>
 __global__ void __launch_bounds__(STREAM_MAX_BLOCK, has_pairs<S>::value ? 3 : 1)
-    k_stream(const DevTables t, const uint8_t* __restrict__ str,
-                                                         const int64_t* __restrict__ off,
-                                                         const uint32_t* __restrict__ perm, long long n,
-                                                         uint8_t* __restrict__ out, unsigned* __restrict__ queue,
-                                                         unsigned long long* __restrict__ bad) {
+    k_stream(const DevTables t, const uint8_t* __restrict__ str, const int64_t* __restrict__ off,
+             const uint32_t* __restrict__ perm, long long n, uint8_t* __restrict__ out,
+             unsigned* __restrict__ queue, unsigned long long* __restrict__ bad) {
     extern __shared__ __align__(16) uint8_t smem[];
     S::load(t, smem);
     __syncthreads();
     S proto;
     proto.bind(t, smem);
+    // a warp takes round r (entries 32r .. 32r+31 of the order) from the
+    // work counter; lane l walks string perm[32r + l] (32r + l without one)
     const int lane = threadIdx.x & 31;
     const uint64_t base = reinterpret_cast<uint64_t>(str);
     const long long nround = (n + 31) / 32;
@@ -187,36 +230,105 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK, has_pairs<S>::value ? 3 : 1)
         const long long k = (long long)r * 32 + lane;
         const bool valid = k < n;
         const long long id = valid ? (perm ? (long long)perm[k] : k) : 0;
-        uint64_t s = base, e = base;
-        const bool ok = !valid || string_span(off, id, base, s, e);
-        S st = proto;
-        bool active = valid && ok && s < e;
-        if (valid && !active) out[id] = ok ? (uint8_t)st.accept() : kResultInvalid;
-        if (!ok) count_bad(bad);
-        if (!active) st.kill();
-        uint64_t blk = s & ~uint64_t(31);
-        Blk32 va = ld_blk(blk, active);
-        Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
-        while (__any_sync(FULL, active)) {
-            // block A at blk, then block B at blk + 32; each buffer is
-            // refilled two blocks ahead right after it is consumed
-            block32(st, va, valid_mask(blk, s, e, active));
-            if (active && (blk + 32 >= e || st.dead())) {
-                out[id] = st.accept();
-                st.kill();
-                active = false;
-            }
-            va = ld_blk(blk + 64, active && blk + 64 < e);
-            if (!__any_sync(FULL, active)) break;
-            block32(st, vb, valid_mask(blk + 32, s, e, active));
-            if (active && (blk + 64 >= e || st.dead())) {
-                out[id] = st.accept();
-                st.kill();
-                active = false;
-            }
-            vb = ld_blk(blk + 96, active && blk + 96 < e);
-            blk += 64;
+        stream_round(proto, base, off, id, valid, out, bad);
+    }
+}
+
+__device__ unsigned g_wait_faults;
+
+// ------------------------------------------------ block-local length order
+// One launch, no global planner and no scratch.  Block b owns the
+// contiguous range of strings [b * per_block, (b + 1) * per_block) and walks
+// it in tiles of up to kLocalTile strings.  For a tile it counts the length
+// keys of its strings (the planner's buckets) in shared memory, scans the
+// counts, and places the tile's strings into a shared order, longest first
+// (each thread keeps its strings' keys in registers across the scan); its warps
+// then take rounds of 32 consecutive entries from a shared counter, so the
+// lanes of a round walk strings of (nearly) the same length, as with the
+// global order: a range of a few thousand random strings has the length mix
+// of the whole batch.  Nothing waits on another block.  Two 768-thread
+// blocks per SM (48 warps, 40 registers) leave room in shared memory for
+// the order beside the tables without changing the plain kernel's
+// shared-memory carveout.
+constexpr int kLocalThreads = 768;
+constexpr int kLocalTile = 4096;
+
+// exclusive scan of a[0..nbk) in shared memory, in place, by the block
+__device__ inline void block_scan_smem(unsigned* a, int nbk) {
+    __shared__ unsigned wsum[32];
+    const int nt = blockDim.x, nw = nt >> 5;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const unsigned v = t < nbk ? a[t] : 0u;  // nbk <= blockDim.x
+    unsigned incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned u = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += u;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned w = lane < nw ? wsum[lane] : 0u, wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned u = __shfl_up_sync(FULL, wi, d);
+            if (lane >= d) wi += u;
         }
+        if (lane < nw) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    if (t < nbk) a[t] = wsum[wid] + incl - v;
+    __syncthreads();
+}
+
+constexpr int kLocalKeys = (kLocalTile + kLocalThreads - 1) / kLocalThreads;
+
+template <class S>
+__global__ void __launch_bounds__(kLocalThreads, has_pairs<S>::value ? 2 : 1)
+    k_stream_local(const DevTables t, const uint8_t* __restrict__ str, const int64_t* __restrict__ off, long long n,
+                   uint8_t* __restrict__ out, long long per_block, int mis, unsigned long long* __restrict__ bad) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    unsigned* cnt = reinterpret_cast<unsigned*>(smem + align16(S::smem_bytes(t)));
+    uint16_t* ord = reinterpret_cast<uint16_t*>(cnt + kLenBuckets);
+    __shared__ unsigned next_round;
+    S::load(t, smem);
+    S proto;
+    proto.bind(t, smem);
+    const int lane = threadIdx.x & 31;
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    const long long lo = min((long long)blockIdx.x * per_block, n), hi = min(lo + per_block, n);
+    for (long long t0 = lo; t0 < hi; t0 += kLocalTile) {
+        const int m = (int)min((long long)kLocalTile, hi - t0);
+        for (int b = threadIdx.x; b < kLenBuckets; b += blockDim.x) cnt[b] = 0;
+        if (threadIdx.x == 0) next_round = 0;
+        __syncthreads();  // also orders the table copy before the rounds
+        int key[kLocalKeys];  // loads of a thread's keys in flight together
+#pragma unroll
+        for (int q = 0; q < kLocalKeys; q++) {
+            const int j = q * kLocalThreads + (int)threadIdx.x;
+            key[q] = j < m ? plan::plan_key(off, nullptr, t0 + j, 0, mis) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < kLocalKeys; q++)
+            if (key[q] >= 0) atomicAdd(&cnt[key[q]], 1u);
+        __syncthreads();
+        block_scan_smem(cnt, kLenBuckets);
+#pragma unroll
+        for (int q = 0; q < kLocalKeys; q++)
+            if (key[q] >= 0) ord[atomicAdd(&cnt[key[q]], 1u)] = (uint16_t)(q * kLocalThreads + (int)threadIdx.x);
+        __syncthreads();
+        const int nround = (m + 31) / 32;
+        for (;;) {
+            unsigned r = 0;
+            if (lane == 0) r = atomicAdd(&next_round, 1u);
+            r = __shfl_sync(FULL, r, 0);
+            if ((int)r >= nround) break;
+            const int k = (int)r * 32 + lane;
+            const bool valid = k < m;
+            const long long id = valid ? t0 + ord[k] : 0;
+            stream_round(proto, base, off, id, valid, out, bad);
+        }
+        __syncthreads();  // the order and the counts are reused by the next tile
     }
 }
 
@@ -232,8 +344,6 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK, has_pairs<S>::value ? 3 : 1)
 // cover all 32 banks in four wavefronts.  Every wait is bounded: a warp
 // whose stage does not complete counts a fault (rx_device_faults), waits a
 // bounded time for its copies in flight and leaves.
-
-__device__ unsigned g_wait_faults;
 
 // each try_wait suspends for at most about kWaitHintNs; a wait gives up
 // after kWaitSpins of them (about 0.2 s)
@@ -631,6 +741,54 @@ cudaError_t launch_span_t(const DevTables& t, const uint8_t* str, int64_t len, i
     return cudaGetLastError();
 }
 
+// blocks of `kern` resident per SM with `smem` bytes of dynamic shared
+// memory (cached per device)
+int resident_blocks(const void* kern, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(dev, kern, block, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    if (allow_smem_raw(kern, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    cache[key] = per_sm;
+    return per_sm;
+}
+
+// The block-local order: launched (*launched = true) when two blocks of
+// the kernel fit on an SM beside the tables (else nothing is launched).
+template <class S>
+cudaError_t launch_stream_local_t(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
+                                  uint8_t* out, cudaStream_t st, bool* launched) {
+    static_assert(kLocalThreads >= kLenBuckets, "one bucket per thread in the scan");
+    static_assert(kLocalTile <= 65536, "tile indices in 16 bits");
+    *launched = false;
+    if (n <= 0) return cudaSuccess;
+    auto kern = k_stream_local<S>;
+    const size_t sm = align16(S::smem_bytes(t)) + (size_t)kLenBuckets * 4 + (size_t)kLocalTile * 2;
+    const int per_sm = resident_blocks(reinterpret_cast<const void*>(kern), kLocalThreads, sm);
+    if (per_sm < 2) return cudaSuccess;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    const long long grid = std::min<long long>((long long)per_sm * sm_count(), (n + 31) / 32);
+    const long long per_block = (n + grid - 1) / grid;
+    const int mis = (int)(reinterpret_cast<uintptr_t>(str) & 31);
+    {
+        ProfScope ps(st);
+        kern<<<(unsigned)grid, kLocalThreads, sm, st>>>(t, str, off, n, out, per_block, mis, bad_offsets_counter());
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) *launched = true;
+    return e;
+}
+
 template <class S>
 cudaError_t launch_stream_t(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
                             const uint32_t* perm, uint8_t* out, unsigned* queue, int block, cudaStream_t st) {
@@ -759,6 +917,13 @@ cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t le
                                         max_tasks, st);
     return launch_span_t<MemoS>(t, str, len, C, P, task_chunk, task_state, ntask_p, pstart, res, queue, max_tasks,
                                 st);
+}
+
+cudaError_t launch_stream_local(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
+                                uint8_t* out, cudaStream_t st, bool* launched) {
+    *launched = false;
+    if (!t.bgp_T) return cudaSuccess;
+    return launch_stream_local_t<MemoPairP>(t, n, str, off, out, st, launched);
 }
 
 bool stream_supported(const DevTables& t, int variant) {

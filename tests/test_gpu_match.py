@@ -48,7 +48,7 @@ def test_small_config_all_variants_vs_o1_o2():
     vs = variants_of(r)
     assert rx.VARIANT_MEMO in vs and rx.VARIANT_WARP in vs
     for v in [0] + vs:
-        for sort in (0, 1, 2, 3):
+        for sort in (0, 1, 2, 3, 4):
             for block in ((0, 257, 128, 512, 130, 4, 12, 20) if v == rx.VARIANT_MEMO else (0,)):
                 got = run(r, w.strings, v, sort, block)
                 assert (got == want2).all(), (v, sort, block, np.nonzero(got != want2)[0][:10])
@@ -177,7 +177,7 @@ def test_invalid_offsets_marked_counted_and_reported():
     d, o = dev(s.data), dev(off)
     out = torch.full((s.n,), 7, dtype=torch.uint8, device="cuda")
     rx.sync_check(raise_error=False)
-    shapes = [(v, sort, block) for v in [0] + variants_of(r) for sort in (0, 1, 2, 3)
+    shapes = [(v, sort, block) for v in [0] + variants_of(r) for sort in (0, 1, 2, 3, 4)
               for block in ((0, 257, 4, 12, 20) if v == rx.VARIANT_MEMO else (0,))]
     for v, sort, block in shapes:
         out.fill_(7)
@@ -454,18 +454,22 @@ def test_host_buffers_edges_and_errors():
 
 def test_planner_one_launch_and_two_launch_forms():
     """The length planner runs as one cooperative launch when every tile of
-    2048 strings gets a resident block, else as two launches.  1,300,000
-    short strings take the two-launch form, their first 600,000 the one-launch
-    form; both equal the unplanned order and O2 on every string, with no
-    barrier wait that gave up."""
+    2048 strings gets a resident block, else as two launches; by default
+    (order 4) planner and streaming kernel share one cooperative launch
+    when the planner's keys fit beside the tables.  1,300,000 short strings
+    take the two-launch planner, their first 600,000 the one-launch
+    planner; 4,500,000 take the separate planner (the keys no longer fit
+    the shared one).  Every form equals the unplanned order and O2 on every
+    string, with no barrier wait that gave up."""
     w = synth.cfg_small(n=8)
     nodes = w.regexes[0]
     r = rx.Regex.from_nodes(nodes)
-    big = synth.gen_strings(nodes, 1300000, 0, 80, synth.LOWER, synth.item_seed(0xA7, 1), p_lang=0.5)
+    big = synth.gen_strings(nodes, 4500000, 0, 80, synth.LOWER, synth.item_seed(0xA7, 1), p_lang=0.5)
     rx.device_faults(reset=True)
-    for n in (600000, 1300000):
+    for n in (600000, 1300000, 4500000):
         s = big if n == big.n else synth.Strings(big.data[:big.offsets[n]], big.offsets[:n + 1], big.kind[:n], 0)
-        planned = run(r, s)
-        assert (planned == run(r, s, sort=0)).all(), n
-        assert (planned == oracle.o2_batch(nodes, s.data, s.offsets)).all(), n
+        want = oracle.o2_batch(nodes, s.data, s.offsets)
+        assert (run(r, s, sort=0) == want).all(), n
+        for sort in (2, 4, -1):
+            assert (run(r, s, sort=sort) == want).all(), (n, sort)
     assert rx.device_faults() == 0

@@ -137,6 +137,31 @@ def test_device_payload_mode():
     srv.close()
 
 
+def test_borrowed_host_payload_mode():
+    """Payload mode 2: host bytes (page-locked) read by the server when it
+    admits a request, with no copy at submit.  Results equal the copying
+    mode's, which equal O2 (want); an invalid mode is rejected."""
+    pool, reqs = workload(seed=0xF8, n_req=80)
+    handles = compile_pool(pool)
+    want, _ = serve_all(handles, reqs, max_inflight=32)
+    srv = rx.Server(max_inflight=32, device_payload=2)
+    bufs = [torch.from_numpy(np.frombuffer(w + b"\0", np.uint8).copy()).pin_memory() for _, w in reqs]
+    tickets = {}
+    for k, (ri, w) in enumerate(reqs):
+        tickets[srv.submit(handles[ri], bufs[k], len(w))] = k
+    srv.drain(60000)
+    got = np.full(len(reqs), 9, np.uint8)
+    tk, r, st = srv.poll(1000)
+    assert (st == 0).all()
+    for a, b in zip(tk, r):
+        got[tickets[int(a)]] = b
+    assert (got == want).all()
+    assert (want == np.array([oracle.o2(pool[ri], w) for ri, w in reqs], np.uint8)).all()
+    srv.close()
+    with pytest.raises(rx.RxError):
+        rx.Server(device_payload=3)
+
+
 def test_serving_full_scale_replay_vs_o2():
     """The serving workload at its full scale: 2000 pool expressions plus
     expressions compiled on arrival (20% of requests), 20,000 requests at
