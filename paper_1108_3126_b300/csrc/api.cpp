@@ -82,6 +82,7 @@ static rx_status upload(rx_regex* h) {
     size_t o_desc = take(256 * sizeof(uint2)), o_tt = take(std::max<size_t>(C.gl_tt.size(), 1) * 4);
     size_t o_T = take(std::max<size_t>(C.memo_T.size(), 1) * 4), o_acc = take(std::max<size_t>(C.memo_acc.size(), 1));
     size_t o_T8 = take(std::max<size_t>(C.memo_T.size(), 1));
+    size_t o_imo = take(std::max<size_t>(C.memo_img_off.size(), 1) * 2), o_img = take(std::max<size_t>(C.memo_img.size(), 1));
     size_t o_sT = take(std::max<size_t>(C.srch_T.size(), 1) * 4);
     size_t o_nd = take(C.nodes.size() * sizeof(int4));
     const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
@@ -103,6 +104,8 @@ static rx_status upload(rx_regex* h) {
     put(o_sT, C.srch_T.data(), C.srch_T.size() * 4);
     for (size_t i = 0; i < C.memo_T.size(); i++) blob[o_T8 + i] = (uint8_t)(C.memo_T[i] / 256u);  // ids < 192
     put(o_acc, C.memo_acc.data(), C.memo_acc.size());
+    put(o_imo, C.memo_img_off.data(), C.memo_img_off.size() * 2);
+    put(o_img, C.memo_img.data(), C.memo_img.size());
     std::vector<int4> pn(C.nodes.size());
     for (size_t i = 0; i < C.nodes.size(); i++)
         pn[i] = make_int4((int)C.nodes[i].kind | ((int)C.nodes[i].byte << 8), C.nodes[i].l, C.nodes[i].r, C.cont[i]);
@@ -155,6 +158,8 @@ static rx_status upload(rx_regex* h) {
     t.srch_start = C.srch_start;
     t.srch_acc0 = C.srch_acc0;
     t.memo_acc = b + o_acc;
+    t.memo_img_off = reinterpret_cast<const uint16_t*>(b + o_imo);
+    t.memo_img = b + o_img;
     t.memo_start = C.memo_start;
     t.bgp_T = C.bgp_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bgp);
     t.bg_lo = C.bg_lo;
@@ -627,12 +632,17 @@ rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* stri
     L.stride = rx::batch_stride(tabs.data(), tabs.size());
     cudaError_t e = rx::batch_configure(L);
     if (e != cudaSuccess) return cuda_fail(e, "rx_match_batch configure");
-    size_t need = rx::batch_workspace_bytes(n, tabs.size()) + rx::batch_maps_bytes(L, n);
+    rx::BatchPlan P;
+    P.n = n;
+    P.ntabs = tabs.size();
+    const size_t maps = rx::batch_maps_bytes(L, n);
+    const size_t need = rx::batch_plan_bytes(P, maps);
     void* ws = nullptr;
     s = rx::get_workspace(st, need, &ws);
     if (s != RX_OK) return s;
-    e = rx::launch_batch(tabs.data(), tabs.size(), pair_tab.data(), cls.data(), n, strings, offsets, out, ws, need, L,
-                         st);
+    rx::batch_plan_place(P, maps, ws);
+    e = rx::batch_plan_upload(P, tabs.data(), pair_tab.data(), cls.data(), st);
+    if (e == cudaSuccess) e = rx::batch_run(P, strings, offsets, out, L, st, true);
     if (e != cudaSuccess) return cuda_fail(e, "rx_match_batch launch");
     return RX_OK;
     RX_GUARD_END

@@ -28,7 +28,7 @@ using namespace rx::dev;
 
 // one warp, one long pair: whether the pair matches (all lanes)
 __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
-    const uint32_t x = warp_chunked_memo(t.memo_T8, t.memo_K, t.memo_start >> 8, s, e, wsm, stride);
+    const uint32_t x = warp_chunked_memo(t, t.memo_start >> 8, s, e, wsm, stride);
     return t.memo_acc[x] != 0;
 }
 
@@ -176,11 +176,13 @@ size_t batch_workspace_bytes(size_t n, size_t ntabs) {
     return 256 + a256(ntabs * sizeof(BatchTab)) + a256(n * 4) + a256(n) + plan_workspace_bytes(n, kBatchClasses);
 }
 
-// chunk maps of long pairs: 32 lanes x (largest cache over the batch's
-// expressions, rounded to 16) bytes per warp; none without a cache
+// chunk functions of long pairs: a row of 2 + K bytes per lane (K the
+// largest cache over the batch's expressions), rounded to 16; none without
+// a cache
 int batch_stride(const BatchTab* h_tabs, size_t ntabs) {
     int stride = 0;
-    for (size_t i = 0; i < ntabs; i++) stride = std::max(stride, (int)((h_tabs[i].t.memo_K + 15) & ~15));
+    for (size_t i = 0; i < ntabs; i++)
+        if (h_tabs[i].t.memo_K > 0) stride = std::max(stride, (int)((h_tabs[i].t.memo_K + 2 + 15) & ~15));
     return stride;
 }
 
@@ -212,40 +214,44 @@ size_t batch_maps_bytes(const BatchLaunch& L, size_t n) {
     return (size_t)batch_grid(L, n) * (L.block / 32) * 64 * (size_t)std::max(L.stride, 1);
 }
 
-// counter reset, planner, persistent kernel: every launch of one batched
-// run, all on `st` (capturable into a graph)
-cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws,
-                      const BatchLaunch& L, cudaStream_t st, bool profile, uint8_t* maps) {
-    if (n == 0) return cudaSuccess;
-    BatchWs b = batch_ws(ws, n, ntabs);
+size_t batch_plan_bytes(const BatchPlan& P, size_t maps_bytes) {
+    return align16(batch_workspace_bytes(P.n, P.ntabs)) + align16(maps_bytes);
+}
+
+void batch_plan_place(BatchPlan& P, size_t maps_bytes, void* base) {
+    uint8_t* w = static_cast<uint8_t*>(base);
+    P.ws = w;
+    P.maps = maps_bytes ? w + align16(batch_workspace_bytes(P.n, P.ntabs)) : nullptr;
+}
+
+cudaError_t batch_plan_upload(const BatchPlan& P, const BatchTab* h_tabs, const uint32_t* h_pair_tab,
+                              const uint8_t* h_cls, cudaStream_t st) {
+    return batch_upload(h_tabs, P.ntabs, h_pair_tab, h_cls, P.n, P.ws, st);
+}
+
+// Every launch of one batched run, all on `st` (capturable into a graph):
+// counter reset, planner, persistent kernel.
+cudaError_t batch_run(const BatchPlan& P, const uint8_t* str, const int64_t* off, uint8_t* out, const BatchLaunch& L,
+                      cudaStream_t st, bool profile) {
+    if (P.n == 0) return cudaSuccess;
+    BatchWs b = batch_ws(P.ws, P.n, P.ntabs);
     cudaError_t e = cudaMemsetAsync(b.queue, 0, 256, st);
     if (e != cudaSuccess) return e;
     uint32_t* perm = nullptr;
     unsigned* starts = nullptr;
-    e = launch_plan(off, b.cls, kBatchClasses, n, b.plan_ws, &perm, &starts, st, nullptr, L.long_bytes, str);
+    e = launch_plan(off, b.cls, kBatchClasses, P.n, b.plan_ws, &perm, &starts, st, nullptr, L.long_bytes, str);
     if (e != cudaSuccess) return e;
-    const long long grid = batch_grid(L, n);
+    const long long grid = batch_grid(L, P.n);
     if (profile) {
         ProfScope ps(st);
-        k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
-                                                    b.queue, L.stride, maps, bad_offsets_counter());
+        k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)P.n, str, off, out,
+                                                    b.queue, L.stride, P.maps, bad_offsets_counter());
     } else {
-        k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)n, str, off, out,
-                                                    b.queue, L.stride, maps, bad_offsets_counter());
+        k_batch<<<(unsigned)grid, L.block, 0, st>>>(b.tabs, b.pair_tab, perm, starts, (long long)P.n, str, off, out,
+                                                    b.queue, L.stride, P.maps, bad_offsets_counter());
         prof_count(1);
     }
     return cudaGetLastError();
-}
-
-cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
-                         size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
-                         const BatchLaunch& L, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    const size_t base = batch_workspace_bytes(n, ntabs);
-    if (ws_bytes < base + batch_maps_bytes(L, n)) return cudaErrorInvalidValue;
-    cudaError_t e = batch_upload(h_tabs, ntabs, h_pair_tab, h_cls, n, ws, st);
-    if (e == cudaSuccess) e = batch_run(n, ntabs, str, off, out, ws, L, st, true, static_cast<uint8_t*>(ws) + base);
-    return e;
 }
 
 }  // namespace rx

@@ -24,9 +24,9 @@ void set_error(const std::string& msg);
 
 struct rx_batch {
     int device = -1;
-    size_t n = 0, ntabs = 0;
-    void* ws = nullptr;
-    uint8_t* maps = nullptr;  // chunk-map scratch, after the batch workspace in ws
+    size_t n = 0;
+    void* ws = nullptr;  // one allocation: the workspace and the chunk-function scratch
+    rx::BatchPlan P;     // its parts
     rx::BatchLaunch L;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -55,7 +55,7 @@ cudaError_t capture(rx_batch* b, const uint8_t* str, const int64_t* off, uint8_t
     drop_graph(b);
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t er = rx::batch_run(b->n, b->ntabs, str, off, out, b->ws, b->L, b->cap, false, b->maps);
+    cudaError_t er = rx::batch_run(b->P, str, off, out, b->L, b->cap, false);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->cap, &g);
     if (er != cudaSuccess) e = er;
@@ -90,11 +90,12 @@ rx_status rx_batch_prepare(const rx_handle* handles, size_t n, rx_batch** out) {
         rx_batch* b = new rx_batch();
         cudaGetDevice(&b->device);
         b->n = n;
-        b->ntabs = tabs.size();
         b->L.stride = rx::batch_stride(tabs.data(), tabs.size());
+        b->P.n = n;
+        b->P.ntabs = tabs.size();
         cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-        // chunk-map scratch for the largest resident grid of any block size
-        // the autotuner may pick
+        // chunk-function scratch for the largest resident grid of any block
+        // size the autotuner may pick
         size_t maps = 0;
         const int blocks[3] = {128, 256, 512};
         for (int i = 0; i < 3 && e == cudaSuccess; i++) {
@@ -103,11 +104,10 @@ rx_status rx_batch_prepare(const rx_handle* handles, size_t n, rx_batch** out) {
             e = rx::batch_configure(Lb);
             if (e == cudaSuccess) maps = std::max(maps, rx::batch_maps_bytes(Lb, n));
         }
-        const size_t base = rx::batch_workspace_bytes(n, tabs.size());
-        if (e == cudaSuccess && n > 0) e = cudaMalloc(&b->ws, base + maps);
-        if (e == cudaSuccess && n > 0) b->maps = static_cast<uint8_t*>(b->ws) + base;
+        if (e == cudaSuccess && n > 0) e = cudaMalloc(&b->ws, rx::batch_plan_bytes(b->P, maps));
+        if (e == cudaSuccess && n > 0) rx::batch_plan_place(b->P, maps, b->ws);
         if (e == cudaSuccess && n > 0)
-            e = rx::batch_upload(tabs.data(), tabs.size(), pair_tab.data(), cls.data(), n, b->ws, b->cap);
+            e = rx::batch_plan_upload(b->P, tabs.data(), pair_tab.data(), cls.data(), b->cap);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
         if (e == cudaSuccess) e = rx::batch_configure(b->L);
         if (e != cudaSuccess) {
@@ -136,7 +136,7 @@ rx_status rx_batch_run(rx_batch* b, const uint8_t* strings, const int64_t* offse
     if (!b->exec || b->g_str != strings || b->g_off != offsets || b->g_out != out) e = capture(b, strings, offsets, out);
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "rx_batch_run");
-    rx::prof_count(3);
+    rx::prof_count(3);  // kernels in the graph: the planner's two launches (under capture) and k_batch
     return RX_OK;
 }
 
@@ -150,7 +150,7 @@ rx_status rx_batch_autotune(rx_batch* b, const uint8_t* strings, const int64_t* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rx_batch_tune best{b->L.long_bytes, b->L.block, -1.f};
     if (b->n > 0) {
-        const long long longs[8] = {2048, 3072, 4096, 6144, 8192, 16384, 32768, (long long)1 << 62};
+        const long long longs[8] = {512, 1024, 2048, 3072, 4096, 6144, 8192, (long long)1 << 62};
         const int blocks[3] = {128, 256, 512};
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaError_t e = cudaEventCreate(&e0);
@@ -166,12 +166,10 @@ rx_status rx_batch_autotune(rx_batch* b, const uint8_t* strings, const int64_t* 
                     e = cudaSuccess;
                     continue;
                 }
-                if (e == cudaSuccess)
-                    e = rx::batch_run(b->n, b->ntabs, strings, offsets, out, b->ws, L, st, false, b->maps);
+                if (e == cudaSuccess) e = rx::batch_run(b->P, strings, offsets, out, L, st, false);
                 const int reps = 3;
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-                for (int r = 0; r < reps && e == cudaSuccess; r++)
-                    e = rx::batch_run(b->n, b->ntabs, strings, offsets, out, b->ws, L, st, false, b->maps);
+                for (int r = 0; r < reps && e == cudaSuccess; r++) e = rx::batch_run(b->P, strings, offsets, out, L, st, false);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;

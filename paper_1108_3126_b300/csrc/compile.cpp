@@ -467,6 +467,19 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
             for (int k = 0; k < C.memo_K; k++)
                 C.memo_acc[k] = (states[k][C.null_bit >> 5] >> (C.null_bit & 31)) & 1u;
             C.memo_start = (uint32_t)s0 * 256u;
+            // 8a. the image of every byte's column: after one byte c every
+            // incoming state is one of these few states, so the effect of a
+            // chunk starting with c is fixed by its effect on them
+            C.memo_img_off.assign(257, 0);
+            C.memo_img.clear();
+            std::vector<uint8_t> seen(C.memo_K);
+            for (int c = 0; c < 256; c++) {
+                std::fill(seen.begin(), seen.end(), 0);
+                for (int k = 0; k < C.memo_K; k++) seen[C.memo_T[(size_t)k * 256 + c] / 256u] = 1;
+                for (int k = 0; k < C.memo_K; k++)
+                    if (seen[k]) C.memo_img.push_back((uint8_t)k);
+                C.memo_img_off[c + 1] = (uint16_t)C.memo_img.size();
+            }
         }
     }
     // ---- 8c. cache for unanchored search (a match may start at any

@@ -2,6 +2,8 @@
 // C ABI layer (api.cpp).  All launchers are asynchronous on `stream`.
 #pragma once
 
+#include <vector>
+
 #include "rx_internal.h"
 
 namespace rx {
@@ -68,26 +70,35 @@ constexpr int kBatchClasses = 7;
 enum { kClsWarp = 0, kClsSparse8 = 1, kClsSparse4 = 2, kClsThread2 = 3, kClsThread1 = 4, kClsMemo = 5,
        kClsMemoLong = 6 };
 struct BatchLaunch {
-    int stride = 0;               // chunk-map bytes per lane (largest cache, rounded to 16)
+    int stride = 0;               // chunk-function row bytes per lane (batch_stride)
     int block = 256;              // threads per block: 128, 256 or 512
-    long long long_bytes = 6144;  // cached pairs longer than this take a warp
+    long long long_bytes = 2048;  // cached pairs longer than this take a warp
     long long grid_cap = 1;       // resident blocks (set by batch_configure)
 };
+
+// Everything one batched run needs beside the pairs themselves: sizes and
+// the places of its device scratch.
+struct BatchPlan {
+    size_t n = 0, ntabs = 0;
+    void* ws = nullptr;       // batch_workspace_bytes
+    uint8_t* maps = nullptr;  // batch_maps_bytes (chunk functions of long cached pairs)
+};
+// device bytes of a plan whose chunk-function scratch takes maps_bytes,
+// and the placement of its parts in one allocation
+size_t batch_plan_bytes(const BatchPlan& P, size_t maps_bytes);
+void batch_plan_place(BatchPlan& P, size_t maps_bytes, void* base);
 size_t batch_workspace_bytes(size_t n, size_t ntabs);
+// bytes of a chunk-function row (2 + the largest cache, rounded to 16)
 int batch_stride(const BatchTab* h_tabs, size_t ntabs);
-cudaError_t batch_upload(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
-                         size_t n, void* ws, cudaStream_t st);
 cudaError_t batch_configure(BatchLaunch& L);
 long long batch_grid(const BatchLaunch& L, size_t n);
-// scratch for the chunk maps of long pairs, after batch_workspace_bytes
+// scratch for the chunk functions of long pairs (64 rows per resident warp)
 size_t batch_maps_bytes(const BatchLaunch& L, size_t n);
-cudaError_t batch_run(size_t n, size_t ntabs, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws,
-                      const BatchLaunch& L, cudaStream_t st, bool profile, uint8_t* maps);
-// L: stride set and batch_configure'd; ws: batch_workspace_bytes +
-// batch_maps_bytes
-cudaError_t launch_batch(const BatchTab* h_tabs, size_t ntabs, const uint32_t* h_pair_tab, const uint8_t* h_cls,
-                         size_t n, const uint8_t* str, const int64_t* off, uint8_t* out, void* ws, size_t ws_bytes,
-                         const BatchLaunch& L, cudaStream_t st);
+cudaError_t batch_run(const BatchPlan& P, const uint8_t* str, const int64_t* off, uint8_t* out, const BatchLaunch& L,
+                      cudaStream_t st, bool profile);
+// uploads of a batch: tables, per-pair table and class
+cudaError_t batch_plan_upload(const BatchPlan& P, const BatchTab* h_tabs, const uint32_t* h_pair_tab,
+                              const uint8_t* h_cls, cudaStream_t st);
 // host arrays of a batch: distinct tables, table index and class per pair
 // (api.cpp); `who` prefixes error messages
 rx_status collect_pairs(const rx_handle* handles, size_t n, const char* who, std::vector<BatchTab>& tabs,

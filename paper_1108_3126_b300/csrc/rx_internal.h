@@ -49,6 +49,11 @@ struct DevTables {
     const uint32_t* memo_T;  // [K*256] next state * 256 (row start, in words)
     const uint8_t* memo_T8;  // [K*256] next state id (the same table, one byte per entry, for global reads)
     const uint8_t* memo_acc; // [K] 1 iff the state's set holds null
+    // image of each byte's column of the cache: the distinct successor ids
+    // of byte c, ascending, are memo_img[memo_img_off[c] .. memo_img_off[c+1])
+    // (state 0, the empty set, is always among them: it stays empty)
+    const uint16_t* memo_img_off;  // [257]
+    const uint8_t* memo_img;
     uint32_t memo_start;     // start state * 256
     // cache for unanchored search (start set added after every byte);
     // states >= srch_acc0 hold null (a match ends there)
@@ -99,6 +104,8 @@ struct Compiled {
     uint32_t srch_start = 0;
     std::vector<uint32_t> srch_T;
     std::vector<uint8_t> memo_acc;
+    std::vector<uint16_t> memo_img_off;  // 257 (see DevTables::memo_img)
+    std::vector<uint8_t> memo_img;
     uint32_t memo_start = 0;
     // two-byte cache: per state a row of 1024 pair successors (entry
     // 32*j + i after bytes lo+i, lo+j) then 256 byte successors, u16 ids

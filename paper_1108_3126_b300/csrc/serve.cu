@@ -41,7 +41,7 @@ namespace {
 using namespace rx::dev;
 
 constexpr int kStateWords = kWarpMaxWords;  // saved set per slot (words)
-constexpr int kMapStride = (kMemoMaxStates + 15) & ~15;  // chunk-map row per lane of a long slot
+constexpr int kMapStride = (kMemoMaxStates + 2 + 15) & ~15;  // chunk-function row per lane of a long slot
 
 struct ServeSlot {
     const DevTables* tab;
@@ -126,7 +126,7 @@ __device__ void tick_memo_long(const ServeSlot& sl, int64_t tick, uint32_t* stat
     const uint32_t x0 = sl.pos > 0 ? state[0] >> 8 : t.memo_start >> 8;
     const uint64_t base = reinterpret_cast<uint64_t>(sl.data);
     const int64_t end = min(sl.len, sl.pos + 32 * tick);
-    const uint32_t x = warp_chunked_memo(t.memo_T8, t.memo_K, x0, base + sl.pos, base + end, wsm, kMapStride);
+    const uint32_t x = warp_chunked_memo(t, x0, base + sl.pos, base + end, wsm, kMapStride);
     if (lane != 0) return;
     if (end >= sl.len || x == 0) {
         status[0] = 1;

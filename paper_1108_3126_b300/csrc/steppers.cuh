@@ -598,95 +598,89 @@ __device__ __forceinline__ void run_lane(S& st, uint64_t s, uint64_t e, bool val
 // (the batched form's long pairs, the serving tick's long requests).
 static_assert(kMemoMaxStates <= 256, "chunk maps hold cache state ids in one byte");
 
-// one lane, bytes [s, e) (absolute addresses), cache state st (id * 256),
-// one-byte table T in global memory; stops when the set is empty
-// (the next 16-byte block is loaded while the current one is stepped)
-__device__ inline uint32_t lane_memo_run(const uint8_t* __restrict__ T, uint32_t st, uint64_t s, uint64_t e) {
+// Readers of the cache with one-byte entries (K rows of 256 successor
+// ids): in global memory (L1/L2) or copied into shared memory.  Both also
+// carry the column images (DevTables::memo_img) from global memory.
+struct GlobalT8 {
+    const uint8_t* __restrict__ T;
+    const uint16_t* __restrict__ img_off;
+    const uint8_t* __restrict__ img;
+    __device__ __forceinline__ uint32_t next(uint32_t x, uint32_t c) const { return __ldg(T + x * 256u + c); }
+};
+struct SharedT8 {
+    uint32_t base;  // shared address of row 0
+    const uint16_t* __restrict__ img_off;
+    const uint8_t* __restrict__ img;
+    __device__ __forceinline__ uint32_t next(uint32_t x, uint32_t c) const { return lds8(base + x * 256u + c); }
+};
+
+// one lane, bytes [s, e) (absolute addresses), from cache state id x;
+// returns the state id reached; stops when the set is empty (state 0).
+// The next 16-byte block is loaded while the current one is stepped.
+template <class R>
+__device__ inline uint32_t run_t8(const R& rd, uint32_t x, uint64_t s, uint64_t e) {
     uint64_t blk = s & ~uint64_t(15);
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (blk < e && st != 0) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
-    while (blk < e && st != 0) {
+    if (blk < e && x != 0) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
+    while (blk < e && x != 0) {
         const uint64_t nb = blk + 16;
         uint4 vn = make_uint4(0, 0, 0, 0);
         if (nb < e) vn = ld_stream(reinterpret_cast<const uint8_t*>(nb));
         if (blk >= s && nb <= e) {
 #pragma unroll
-            for (int k = 0; k < 16; k++) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
+            for (int k = 0; k < 16; k++) x = rd.next(x, byte_of(v, k));
         } else {
 #pragma unroll
             for (int k = 0; k < 16; k++) {
                 const uint64_t q = blk + k;
-                if (q >= s && q < e) st = (uint32_t)__ldg(T + st + byte_of(v, k)) << 8;
+                if (q >= s && q < e) x = rd.next(x, byte_of(v, k));
             }
         }
         blk = nb;
         v = vn;
     }
-    return st;
+    return x;
 }
 
 constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states are merged
 
-// One warp advances the cache state x0 over bytes [s, e) (absolute
-// addresses) and returns the state reached (the same in every lane).  T:
-// the one-byte cache rows in global memory (K x 256).
-// Lane l computes the transfer map of chunk l (of 32) on cache states.
-// Every incoming state advances over the first byte of the chunk; the
-// states reached are deduplicated (a bitmap; rank = index) into
-// representatives, and each incoming state records its representative.  The
-// representatives then advance in stages of 3, 6, 12, ... bytes (at most
-// kPairPrefix bytes in all) until at most one distinct live state is among
-// them -- the empty set (state 0) stays empty at no cost, and two states that
-// meet stay together (Def 5.2 is a function of the set) -- and each distinct
-// one runs over the rest of the chunk.  wsm holds, per lane, map[K]
-// (incoming state -> representative) and, after the 32 maps, dv[K] (the
-// representatives' states); `stride` >= K bytes each.  Lane 0 composes the
-// 32 maps from x0.
-__device__ inline uint32_t warp_chunked_memo(const uint8_t* __restrict__ T, int K, uint32_t x0, uint64_t s, uint64_t e,
-                                      uint8_t* wsm, int stride) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t L = e - s;
-    const uint64_t C = ((L + 31) / 32 + 15) & ~uint64_t(15);
-    uint64_t cs = s + (uint64_t)lane * C;
-    if (cs > e) cs = e;
-    const uint64_t ce = cs + C < e ? cs + C : e;
+// One lane computes the transfer function of bytes [cs, ce) (absolute
+// addresses) on cache states, as a row:
+//   row[0] = the chunk's first byte c, row[1] = n = the size of the image
+//   of column c (the distinct states any incoming state reaches on c),
+//   row[2 + i] = the state reached from image entry i over the rest.
+// An incoming state k then ends in row[2 + i] with img[i] = T[k][c] (exact:
+// a macro step is a function of the set, Def 5.2, so k's path after c is
+// that of T[k][c]).  The image is usually a few states, so no incoming
+// state is stepped on its own.  They advance in stages of 3, 6, 12, ...
+// bytes (at most kPairPrefix bytes in all) until at most one distinct live
+// state is among them -- the empty set (state 0, always entry 0) stays
+// empty at no cost, and two states that meet stay together -- and each
+// distinct one then runs over the rest.  row holds 2 + K bytes; n = 0
+// marks an empty chunk (the identity).
+template <class R>
+__device__ inline void chunk_fn_t8(const R& rd, uint64_t cs, uint64_t ce, uint8_t* row) {
+    if (ce <= cs) {
+        row[1] = 0;
+        return;
+    }
+    const uint32_t c = __ldg(reinterpret_cast<const uint8_t*>(cs));
+    const int lo = rd.img_off[c], n = (int)rd.img_off[c + 1] - lo;
+    uint8_t* dv = row + 2;
+    row[0] = (uint8_t)c;
+    row[1] = (uint8_t)n;
+    for (int i = 0; i < n; i++) dv[i] = rd.img[lo + i];
     const uint64_t pe = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
-    uint8_t* map = wsm + lane * stride;
-    uint8_t* dv = wsm + (32 + lane) * stride;
-    // first stage: every incoming state over the chunk's first byte (the
-    // states are independent, two lookups in flight); a byte's successors
-    // are few distinct states, so the representatives take the rest
-    uint64_t pos = cs + 1 < pe ? cs + 1 : pe;
-    const bool nb = pos > cs;
-    const uint32_t b0 = nb ? __ldg(reinterpret_cast<const uint8_t*>(cs)) : 0u;
-    uint32_t bm[kBmWords];
-#pragma unroll
-    for (int w = 0; w < kBmWords; w++) bm[w] = 0;
-#pragma unroll 2
-    for (int k = 0; k < K; k++) {
-        const uint32_t v = nb ? (uint32_t)__ldg(T + (uint32_t)k * 256u + b0) : (uint32_t)k;
-        map[k] = (uint8_t)v;
-        bm_set(bm, v);
-    }
-    int nr = 0;
-#pragma unroll
-    for (int w = 0; w < kBmWords; w++) {
-        uint32_t x = bm[w];
-        while (x) {
-            dv[nr++] = (uint8_t)(w * 32 + __ffs(x) - 1);
-            x &= x - 1;
-        }
-    }
-    for (int k = 0; k < K; k++) map[k] = (uint8_t)rank_below(bm, map[k]);
-    int live = nr - (int)(bm[0] & 1u);
-    // further stages: the representatives only
+    uint64_t pos = cs + 1;
+    int live = n - 1;  // entry 0 is the empty set
     uint64_t len = 3;
+    uint32_t bm[kBmWords];
     while (live > 1 && pos < pe) {
         const uint64_t end = pos + len < pe ? pos + len : pe;
 #pragma unroll
         for (int w = 0; w < kBmWords; w++) bm[w] = 0;
-        for (int i = 0; i < nr; i++) {
-            const uint32_t v = lane_memo_run(T, (uint32_t)dv[i] * 256u, pos, end) >> 8;
+        for (int i = 0; i < n; i++) {
+            const uint32_t v = run_t8(rd, (uint32_t)dv[i], pos, end);
             dv[i] = (uint8_t)v;
             bm_set(bm, v);
         }
@@ -701,14 +695,14 @@ __device__ inline uint32_t warp_chunked_memo(const uint8_t* __restrict__ T, int 
     // (state, result) pairs; a repeat beyond it is run again, same result)
     uint32_t cv[4], cr[4];
     int nc = 0;
-    for (int i = 0; i < nr; i++) {
+    for (int i = 0; i < n; i++) {
         const uint32_t v = dv[i];
         uint32_t r = 0xffffffffu;
 #pragma unroll
         for (int q = 0; q < 4; q++)
             if (q < nc && cv[q] == v) r = cr[q];
         if (r == 0xffffffffu) {
-            r = v == 0 ? 0u : lane_memo_run(T, v * 256u, pos, ce) >> 8;
+            r = v == 0 ? 0u : run_t8(rd, v, pos, ce);
 #pragma unroll
             for (int q = 0; q < 4; q++)
                 if (q == nc) {
@@ -719,13 +713,49 @@ __device__ inline uint32_t warp_chunked_memo(const uint8_t* __restrict__ T, int 
         }
         dv[i] = (uint8_t)r;
     }
-    for (int k = 0; k < K; k++) map[k] = dv[map[k]];
+}
+
+// The state a chunk's row (chunk_fn_t8) leads state x to.
+template <class R>
+__device__ __forceinline__ uint32_t chunk_apply(const R& rd, const uint8_t* row, uint32_t x) {
+    const int n = row[1];
+    if (n == 0) return x;
+    const uint32_t c = row[0], y = rd.next(x, c);
+    int lo = rd.img_off[c], hi = lo + n - 1;  // the image is ascending and holds y
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rd.img[mid] < y) lo = mid + 1;
+        else hi = mid;
+    }
+    return row[2 + (lo - rd.img_off[c])];
+}
+
+// One warp advances the cache state x0 over bytes [s, e) (absolute
+// addresses) and returns the state reached (the same in every lane).  rd
+// reads the one-byte cache rows.  Lane l computes the transfer function of
+// chunk l (of 32) with chunk_fn_t8 into row l of wsm (`stride` >= K + 2
+// bytes each); lane 0 applies the 32 rows to x0 in order.
+template <class R>
+__device__ inline uint32_t warp_chunked_t8(const R& rd, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t L = e - s;
+    const uint64_t C = ((L + 31) / 32 + 15) & ~uint64_t(15);
+    uint64_t cs = s + (uint64_t)lane * C;
+    if (cs > e) cs = e;
+    const uint64_t ce = cs + C < e ? cs + C : e;
+    chunk_fn_t8(rd, cs, ce, wsm + lane * stride);
     __syncwarp();
     uint32_t x = x0;
     if (lane == 0)
-        for (int l = 0; l < 32; l++) x = wsm[l * stride + x];
+        for (int l = 0; l < 32; l++) x = chunk_apply(rd, wsm + l * stride, x);
     __syncwarp();
     return __shfl_sync(FULL, x, 0);
+}
+
+// the same with the rows in global memory (the batched and serving forms)
+__device__ inline uint32_t warp_chunked_memo(const DevTables& t, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm,
+                                             int stride) {
+    return warp_chunked_t8(GlobalT8{t.memo_T8, t.memo_img_off, t.memo_img}, x0, s, e, wsm, stride);
 }
 
 // ---------------------------------------------------------------------------
