@@ -83,6 +83,7 @@ static rx_status upload(rx_regex* h) {
     size_t o_T = take(std::max<size_t>(C.memo_T.size(), 1) * 4), o_acc = take(std::max<size_t>(C.memo_acc.size(), 1));
     size_t o_T8 = take(std::max<size_t>(C.memo_T.size(), 1));
     size_t o_imo = take(std::max<size_t>(C.memo_img_off.size(), 1) * 2), o_img = take(std::max<size_t>(C.memo_img.size(), 1));
+    size_t o_imp = take(std::max<size_t>(C.memo_imgpos.size(), 1));
     size_t o_sT = take(std::max<size_t>(C.srch_T.size(), 1) * 4);
     size_t o_nd = take(C.nodes.size() * sizeof(int4));
     const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
@@ -106,6 +107,7 @@ static rx_status upload(rx_regex* h) {
     put(o_acc, C.memo_acc.data(), C.memo_acc.size());
     put(o_imo, C.memo_img_off.data(), C.memo_img_off.size() * 2);
     put(o_img, C.memo_img.data(), C.memo_img.size());
+    put(o_imp, C.memo_imgpos.data(), C.memo_imgpos.size());
     std::vector<int4> pn(C.nodes.size());
     for (size_t i = 0; i < C.nodes.size(); i++)
         pn[i] = make_int4((int)C.nodes[i].kind | ((int)C.nodes[i].byte << 8), C.nodes[i].l, C.nodes[i].r, C.cont[i]);
@@ -160,6 +162,7 @@ static rx_status upload(rx_regex* h) {
     t.memo_acc = b + o_acc;
     t.memo_img_off = reinterpret_cast<const uint16_t*>(b + o_imo);
     t.memo_img = b + o_img;
+    t.memo_imgpos = b + o_imp;
     t.memo_start = C.memo_start;
     t.bgp_T = C.bgp_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bgp);
     t.bg_lo = C.bg_lo;

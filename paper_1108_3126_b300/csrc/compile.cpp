@@ -472,12 +472,19 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
             // chunk starting with c is fixed by its effect on them
             C.memo_img_off.assign(257, 0);
             C.memo_img.clear();
-            std::vector<uint8_t> seen(C.memo_K);
+            C.memo_imgpos.assign((size_t)C.memo_K * 256, 0);
+            std::vector<int> at(C.memo_K);
             for (int c = 0; c < 256; c++) {
-                std::fill(seen.begin(), seen.end(), 0);
-                for (int k = 0; k < C.memo_K; k++) seen[C.memo_T[(size_t)k * 256 + c] / 256u] = 1;
+                std::fill(at.begin(), at.end(), -1);
+                for (int k = 0; k < C.memo_K; k++) at[C.memo_T[(size_t)k * 256 + c] / 256u] = 0;
+                int n = 0;
                 for (int k = 0; k < C.memo_K; k++)
-                    if (seen[k]) C.memo_img.push_back((uint8_t)k);
+                    if (at[k] >= 0) {
+                        at[k] = n++;
+                        C.memo_img.push_back((uint8_t)k);
+                    }
+                for (int k = 0; k < C.memo_K; k++)
+                    C.memo_imgpos[(size_t)k * 256 + c] = (uint8_t)at[C.memo_T[(size_t)k * 256 + c] / 256u];
                 C.memo_img_off[c + 1] = (uint16_t)C.memo_img.size();
             }
         }

@@ -27,25 +27,26 @@ namespace {
 
 using namespace rx::dev;
 
-// Phase 1: one thread per chunk.  The K incoming cache states advance over
-// the first 4 bytes of the chunk; the states reached are deduplicated (a
-// bitmap of state ids) into a list of representatives, and each incoming
-// state records its representative.  The representatives then advance
-// through further stages (4, 8, 16, ... bytes, kMaxPrefix in all) until at
-// most one distinct live state is among them (the empty set, state 0, stays
-// empty at no cost) -- two states that meet stay together, since a macro
-// step is a function of the set (Def 5.2).  Each distinct live state left is
-// one task of phase 2 (the rest of the chunk from that state); the tasks of
-// a warp's 32 chunks are allotted with one atomic add.  Per chunk j:
-// slot[j*K + k] = task index (relative to toff[j]) of the state incoming
-// state k has reached, 0xFFFF if it is the empty set; toff[j] = first task;
-// pstart[j] = prefix bytes consumed.  The prefix is kept short because a
-// warp's 32 chunks go through it together.  Each thread keeps map[K]
-// (representative of each incoming state), dv[K] (the representatives'
-// states) and rk[K] (index of a state id in the current list) as bytes in
-// shared memory after the table, interleaved across the block's threads
-// (entry k of thread x at k * blockDim + x) so that a warp's accesses fall
-// in distinct banks.
+// Phase 1: one thread per chunk.  After the chunk's first byte c every
+// incoming cache state is in the image of column c (the distinct
+// successors on c, usually a few states; DevTables::memo_img), so those
+// states are the chunk's representatives and no incoming state is stepped
+// on its own.  The representatives advance in stages (3, 4, 8, 16, ...
+// bytes, kMaxPrefix in all) until at most one distinct live state is among
+// them (the empty set, state 0, stays empty at no cost) -- two states that
+// meet stay together, since a macro step is a function of the set (Def
+// 5.2).  Each distinct live state left is one task of phase 2 (the rest of
+// the chunk from that state); the tasks of a warp's 32 chunks are allotted
+// with one atomic add.  Per chunk j: cb0[j] = c; slot[j*K + i] = task index
+// (relative to toff[j]) of the state image entry i has reached, 0xFFFF if
+// it is the empty set; toff[j] = first task; pstart[j] = prefix bytes
+// consumed.  An incoming state k is then mapped through entry
+// memo_imgpos[k][c].  The prefix is kept short because a warp's 32 chunks
+// go through it together.  Each thread keeps dv[K] (the representatives'
+// states) and rk[K] (task number of a state id) as bytes in shared memory
+// after the table, interleaved across the block's threads (entry k of
+// thread x at k * blockDim + x) so that a warp's accesses fall in distinct
+// banks.
 constexpr int kMaxPrefix = 128;
 
 // a set of cache state ids (< 192) in six registers
@@ -121,8 +122,8 @@ __device__ __forceinline__ void load_bytes(const uint8_t* p, int n, uint32_t (&b
 
 __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const uint8_t* __restrict__ str, int64_t len,
                                                      int64_t C, long long J, uint16_t* __restrict__ slot,
-                                                     uint16_t* __restrict__ pstart, unsigned* __restrict__ toff,
-                                                     uint32_t* __restrict__ task_chunk,
+                                                     uint8_t* __restrict__ cb0, uint16_t* __restrict__ pstart,
+                                                     unsigned* __restrict__ toff, uint32_t* __restrict__ task_chunk,
                                                      uint16_t* __restrict__ task_state,
                                                      unsigned* __restrict__ ntask) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -132,8 +133,7 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
     proto.bind(t, smem);
     const int K = t.memo_K;
     const int nt = blockDim.x, lane = threadIdx.x & 31;
-    uint8_t* map = smem + MemoS8::smem_bytes(t) + threadIdx.x;
-    uint8_t* dv = map + (size_t)K * nt;
+    uint8_t* dv = smem + MemoS8::smem_bytes(t) + threadIdx.x;
     uint8_t* rk = dv + (size_t)K * nt;
     // warp-uniform loop over groups of 32 chunks
     const long long wstride = (long long)gridDim.x * blockDim.x;
@@ -142,37 +142,24 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
         const bool valid = j < J;
         int nr = 0, nl = 0;
         int64_t cs = 0, pos = 0;
+        uint32_t c0 = 0;
         IdSet fin;  // the distinct live states at the end of the prefix
         if (valid) {
             cs = j * C;
             const int64_t pe = min(cs + kMaxPrefix, min(cs + C, len));
-            // first stage: every incoming state
-            const int n1 = (int)min((int64_t)4, pe - cs);
+            // the image of the first byte's column: the representatives
+            c0 = __ldg(str + cs);
+            const int lo = t.memo_img_off[c0];
+            nr = (int)t.memo_img_off[c0 + 1] - lo;
+            for (int i = 0; i < nr; i++) {
+                const uint32_t v = t.memo_img[lo + i];
+                dv[i * nt] = (uint8_t)v;
+                fin.add(v);
+            }
+            pos = cs + 1;
+            int live = nr - 1;  // entry 0 is the empty set
+            int L = 3, stage = 0;
             uint32_t b[4];
-            load_bytes(str + cs, n1, b);
-            IdSet seen;
-            for (int k = 0; k < K; k++) {
-                const uint32_t v = n1 > 0 ? step_n(proto, (uint32_t)k, b, n1) : (uint32_t)k;
-                map[k * nt] = (uint8_t)v;
-                seen.add(v);
-            }
-            // representatives: the distinct states, in id order
-#pragma unroll
-            for (int w = 0; w < 6; w++) {
-                uint32_t x = seen.word(w);
-                while (x) {
-                    const int id = w * 32 + __ffs(x) - 1;
-                    dv[nr * nt] = (uint8_t)id;
-                    rk[id * nt] = (uint8_t)nr;
-                    nr++;
-                    x &= x - 1;
-                }
-            }
-            for (int k = 0; k < K; k++) map[k * nt] = rk[map[k * nt] * nt];
-            fin = seen;
-            pos = cs + n1;
-            int live = seen.count() - (int)(seen.w0 & 1u);
-            int L = 4, stage = 1;
             // further stages: the representatives only
             while (live > 1 && pos < pe) {
                 const int n = (int)min((int64_t)L, pe - pos);
@@ -212,10 +199,11 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
         if (lane == 31) base = atomicAdd(ntask, (unsigned)incl);
         base = __shfl_sync(FULL, base, 31) + (unsigned)(incl - nl);
         if (valid) {
-            for (int k = 0; k < K; k++) {
-                const uint32_t v = dv[map[k * nt] * nt];
-                slot[j * K + k] = v == 0 ? (uint16_t)0xFFFF : (uint16_t)rk[v * nt];
+            for (int i = 0; i < nr; i++) {
+                const uint32_t v = dv[i * nt];
+                slot[j * K + i] = v == 0 ? (uint16_t)0xFFFF : (uint16_t)rk[v * nt];
             }
+            cb0[j] = (uint8_t)c0;
             int i = 0;
 #pragma unroll
             for (int w = 0; w < 6; w++) {
@@ -234,8 +222,9 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
 }
 
 // first level of the composition, reading the chunk maps straight from the
-// tasks' results: map_j[k] = res[toff[j] + slot[j*K + k]] (0 for the empty
-// set); block b composes chunks [b*G, min((b+1)*G, J)) into out[b]
+// tasks' results: map_j[k] = res[toff[j] + slot[j*K + i]] with i =
+// memo_imgpos[k][cb0[j]] (0 for the empty set); block b composes chunks
+// [b*G, min((b+1)*G, J)) into out[b]
 // Maps m[0..nmap) of K entries in shared memory, m[0] applied first: leaves
 // their composition in m[0].  Pairwise in log2(nmap) levels: at stride d,
 // m[j] <- m[j + d] o m[j] for j a multiple of 2d (composition is
@@ -251,7 +240,8 @@ __device__ void compose_tree(uint16_t* m, int nmap, int K) {
     }
 }
 
-__global__ void k_compose_first(const uint16_t* __restrict__ slot, const unsigned* __restrict__ toff,
+__global__ void k_compose_first(const uint16_t* __restrict__ slot, const uint8_t* __restrict__ cb0,
+                                const uint8_t* __restrict__ imgpos, const unsigned* __restrict__ toff,
                                 const uint16_t* __restrict__ res, long long J, int K, int G,
                                 uint16_t* __restrict__ out) {
     extern __shared__ __align__(16) uint16_t sm16[];
@@ -261,8 +251,9 @@ __global__ void k_compose_first(const uint16_t* __restrict__ slot, const unsigne
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int c = threadIdx.x >> 5; c < nmap; c += warps) {
         const unsigned o = toff[lo + c];
+        const uint32_t b0 = cb0[lo + c];
         for (int k = lane; k < K; k += 32) {
-            const uint16_t r = slot[(lo + c) * K + k];
+            const uint16_t r = slot[(lo + c) * K + __ldg(imgpos + k * 256 + b0)];
             sm16[c * K + k] = r == 0xFFFF ? (uint16_t)0 : res[o + r];
         }
     }
@@ -462,6 +453,7 @@ int64_t long_chunk_auto(const DevTables& t, int64_t len) {
 
 struct MemoLongWs {
     uint16_t *pstart, *slot, *task_state, *res, *maps_a, *maps_b;
+    uint8_t* cb0;
     uint32_t* task_chunk;
     unsigned *toff, *ctr;  // ctr[0]: tasks allotted, ctr[1]: work counter of phase 2
 };
@@ -482,6 +474,7 @@ static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
     uint8_t* p_mb = take(JK * 2);
     uint8_t* p_tc = take(JK * 4);
     uint8_t* p_toff = take((size_t)J * 4);
+    uint8_t* p_cb0 = take((size_t)J);
     uint8_t* p_q = take(256);
     if (o) {
         o->pstart = reinterpret_cast<uint16_t*>(p_pre);
@@ -492,6 +485,7 @@ static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
         o->maps_b = reinterpret_cast<uint16_t*>(p_mb);
         o->task_chunk = reinterpret_cast<uint32_t*>(p_tc);
         o->toff = reinterpret_cast<unsigned*>(p_toff);
+        o->cb0 = p_cb0;
         o->ctr = reinterpret_cast<unsigned*>(p_q);
     }
     return off;
@@ -529,9 +523,9 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return e;
-        int threads = (int)std::min<size_t>(256, ((size_t)optin - tab) / (3 * (size_t)K)) & ~31;
+        int threads = (int)std::min<size_t>(256, ((size_t)optin - tab) / (2 * (size_t)K)) & ~31;
         if (threads < 32) return cudaErrorInvalidConfiguration;
-        const size_t sm = tab + (size_t)threads * 3 * K;
+        const size_t sm = tab + (size_t)threads * 2 * K;
         e = allow_smem(k_chunk_stage, sm);
         int per_sm = 0;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_stage, threads, sm);
@@ -542,7 +536,7 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         {
             ProfScope ps(st);
             k_chunk_stage<<<(unsigned)std::max<long long>(grid, 1), threads, sm, st>>>(
-                t, str, len, C, J, L.slot, L.pstart, L.toff, L.task_chunk, L.task_state, L.ctr);
+                t, str, len, C, J, L.slot, L.cb0, L.pstart, L.toff, L.task_chunk, L.task_state, L.ctr);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -553,7 +547,8 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         // composition, left to right; the first level gathers the chunk maps
         const int G = std::max(2, std::min(512, (48 * 1024) / (K * 2)));
         long long cnt = (J + G - 1) / G;
-        k_compose_first<<<(unsigned)cnt, 256, (size_t)G * K * 2, st>>>(L.slot, L.toff, L.res, J, K, G, L.maps_a);
+        k_compose_first<<<(unsigned)cnt, 256, (size_t)G * K * 2, st>>>(L.slot, L.cb0, t.memo_imgpos, L.toff, L.res,
+                                                                       J, K, G, L.maps_a);
         prof_count(1);
         uint16_t* cur = L.maps_a;
         uint16_t* nxt = L.maps_b;

@@ -54,6 +54,7 @@ struct DevTables {
     // (state 0, the empty set, is always among them: it stays empty)
     const uint16_t* memo_img_off;  // [257]
     const uint8_t* memo_img;
+    const uint8_t* memo_imgpos;    // [K*256] index of T[k][c] in the image of c
     uint32_t memo_start;     // start state * 256
     // cache for unanchored search (start set added after every byte);
     // states >= srch_acc0 hold null (a match ends there)
@@ -106,6 +107,7 @@ struct Compiled {
     std::vector<uint8_t> memo_acc;
     std::vector<uint16_t> memo_img_off;  // 257 (see DevTables::memo_img)
     std::vector<uint8_t> memo_img;
+    std::vector<uint8_t> memo_imgpos;    // K*256
     uint32_t memo_start = 0;
     // two-byte cache: per state a row of 1024 pair successors (entry
     // 32*j + i after bytes lo+i, lo+j) then 256 byte successors, u16 ids
