@@ -437,9 +437,14 @@ def _time(fn, reps, stream, dev):
     return a.elapsed_time(b) / reps
 
 
-def _timed(fn, stream, dev, min_s: float = 0.3, max_reps: int = 2000, min_reps: int = 3):
-    """Mean ms of fn over enough repetitions to last about min_s (CUDA
-    events on `stream`), and the number of repetitions."""
+MIN_SECONDS = [0.3]  # --min-seconds
+
+
+def _timed(fn, stream, dev, min_s: float | None = None, max_reps: int = 2000, min_reps: int = 3):
+    """Mean ms of fn over enough repetitions to last about min_s (default
+    --min-seconds; CUDA events on `stream`), and the number of repetitions."""
+    if min_s is None:
+        min_s = MIN_SECONDS[0]
     one = _time(fn, 1, stream, dev)
     reps = int(max(min_reps, min(max_reps, (min_s * 1e3) / max(one, 1e-3))))
     return _time(fn, reps, stream, dev), reps
@@ -558,7 +563,7 @@ def cfg_small_result(args, dev):
             oracle.o2_batch(nodes, s.data, s.offsets, threads=cores)
         return kk * total, f"the whole batch x{kk}, O2 on {cores} threads", False
 
-    cpu_v, cpu_desc = _cpu_o2(o2_rep, 2.0)
+    cpu_v, cpu_desc = _cpu_o2(o2_rep, 2.0) if not args.no_cpu_baseline else (None, "skipped")
     t = time.perf_counter()
     oracle.o1_batch(nodes, s.data, s.offsets, threads=cores)
     o1_gbs = total / (time.perf_counter() - t) / 1e9
@@ -639,7 +644,7 @@ def cfg_batched_result(args, dev):
         return int(sub.offsets[-1]), f"{kk} random pairs ({mb:.1f} MB), O2 on {cores} threads, equal to the GPU", \
             kk >= n
 
-    cpu_v, cpu_desc = _cpu_o2(o2_pairs, args.cpu_seconds, 2000)
+    cpu_v, cpu_desc = _cpu_o2(o2_pairs, args.cpu_seconds, 2000) if not args.no_cpu_baseline else (None, "skipped")
     infos = [h.info() for h in handles]
     for h in handles:
         h.free()
@@ -713,7 +718,7 @@ def cfg_long_result(args, dev):
             raise SystemExit("chunked mode disagrees with O2 on a prefix")
         return nb, f"first {nb >> 20} MiB of the text, O2 on 1 thread (equal to the chunked GPU result)", nb >= n
 
-    cpu_v, cpu_desc = _cpu_o2(o2_prefix, args.cpu_seconds, 4)
+    cpu_v, cpu_desc = _cpu_o2(o2_prefix, args.cpu_seconds, 4) if not args.no_cpu_baseline else (None, "skipped")
     kernel_ms = kms / max(reps, 1)
     return {"workload": "long text: (R)* with 48 positions over a..z, one 1 GiB text of concatenated language "
                         "samples of R", "value": round(n / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
@@ -841,7 +846,7 @@ def cfg_serving_result(args, dev):
         return int(sub.offsets[-1]), f"{kk} random payloads with their expressions ({mb:.1f} MB), O2 on {cores} " \
                                      "threads", kk >= npay
 
-    cpu_v, cpu_desc = _cpu_o2(o2_req, args.cpu_seconds, 16)
+    cpu_v, cpu_desc = _cpu_o2(o2_req, args.cpu_seconds, 16) if not args.no_cpu_baseline else (None, "skipped")
     best = max(dev_points, key=lambda q: q["req_per_s"])
     best_h = max(host_points, key=lambda q: q["req_per_s"])
     plain_rps = args.plain_requests / el
@@ -899,6 +904,8 @@ def main():
     ap.add_argument("--plain-requests", type=int, default=300)
     ap.add_argument("--paper-strings", type=int, default=48, help="small: strings timed on Section 8's machine")
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="CPU-baseline budget per config")
+    ap.add_argument("--min-seconds", type=float, default=0.3,
+                    help="timed loops of the other configs last about this long (0: three repetitions)")
     ap.add_argument("--variant", default="auto", choices=["auto", "memo", "thread", "sparse", "warp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batched: skip the launch-shape autotuner")
@@ -911,6 +918,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    MIN_SECONDS[0] = args.min_seconds
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -484,7 +484,7 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
                         C.memo_img.push_back((uint8_t)k);
                     }
                 for (int k = 0; k < C.memo_K; k++)
-                    C.memo_imgpos[(size_t)k * 256 + c] = (uint8_t)at[C.memo_T[(size_t)k * 256 + c] / 256u];
+                    C.memo_imgpos[(size_t)c * C.memo_K + k] = (uint8_t)at[C.memo_T[(size_t)k * 256 + c] / 256u];
                 C.memo_img_off[c + 1] = (uint16_t)C.memo_img.size();
             }
         }

@@ -41,7 +41,7 @@ using namespace rx::dev;
 // (relative to toff[j]) of the state image entry i has reached, 0xFFFF if
 // it is the empty set; toff[j] = first task; pstart[j] = prefix bytes
 // consumed.  An incoming state k is then mapped through entry
-// memo_imgpos[k][c].  The prefix is kept short because a warp's 32 chunks
+// memo_imgpos[c*K + k].  The prefix is kept short because a warp's 32 chunks
 // go through it together.  Each thread keeps dv[K] (the representatives'
 // states) and rk[K] (task number of a state id) as bytes in shared memory
 // after the table, interleaved across the block's threads (entry k of
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
 
 // first level of the composition, reading the chunk maps straight from the
 // tasks' results: map_j[k] = res[toff[j] + slot[j*K + i]] with i =
-// memo_imgpos[k][cb0[j]] (0 for the empty set); block b composes chunks
+// memo_imgpos[cb0[j]*K + k] (0 for the empty set); block b composes chunks
 // [b*G, min((b+1)*G, J)) into out[b]
 // Maps m[0..nmap) of K entries in shared memory, m[0] applied first: leaves
 // their composition in m[0].  Pairwise in log2(nmap) levels: at stride d,
@@ -253,7 +253,7 @@ __global__ void k_compose_first(const uint16_t* __restrict__ slot, const uint8_t
         const unsigned o = toff[lo + c];
         const uint32_t b0 = cb0[lo + c];
         for (int k = lane; k < K; k += 32) {
-            const uint16_t r = slot[(lo + c) * K + __ldg(imgpos + k * 256 + b0)];
+            const uint16_t r = slot[(lo + c) * K + __ldg(imgpos + b0 * K + k)];
             sm16[c * K + k] = r == 0xFFFF ? (uint16_t)0 : res[o + r];
         }
     }

@@ -54,7 +54,7 @@ struct DevTables {
     // (state 0, the empty set, is always among them: it stays empty)
     const uint16_t* memo_img_off;  // [257]
     const uint8_t* memo_img;
-    const uint8_t* memo_imgpos;    // [K*256] index of T[k][c] in the image of c
+    const uint8_t* memo_imgpos;    // [256*K] entry c*K + k: index of T[k][c] in the image of c
     uint32_t memo_start;     // start state * 256
     // cache for unanchored search (start set added after every byte);
     // states >= srch_acc0 hold null (a match ends there)

@@ -605,13 +605,9 @@ struct GlobalT8 {
     const uint8_t* __restrict__ T;
     const uint16_t* __restrict__ img_off;
     const uint8_t* __restrict__ img;
+    const uint8_t* __restrict__ imgpos;  // DevTables::memo_imgpos
+    int K;
     __device__ __forceinline__ uint32_t next(uint32_t x, uint32_t c) const { return __ldg(T + x * 256u + c); }
-};
-struct SharedT8 {
-    uint32_t base;  // shared address of row 0
-    const uint16_t* __restrict__ img_off;
-    const uint8_t* __restrict__ img;
-    __device__ __forceinline__ uint32_t next(uint32_t x, uint32_t c) const { return lds8(base + x * 256u + c); }
 };
 
 // one lane, bytes [s, e) (absolute addresses), from cache state id x;
@@ -657,7 +653,8 @@ constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states a
 // state is among them -- the empty set (state 0, always entry 0) stays
 // empty at no cost, and two states that meet stay together -- and each
 // distinct one then runs over the rest.  row holds 2 + K bytes; n = 0
-// marks an empty chunk (the identity).
+// marks an empty chunk (the identity).  An incoming state k maps to
+// row[2 + imgpos[c*K + k]].
 template <class R>
 __device__ inline void chunk_fn_t8(const R& rd, uint64_t cs, uint64_t ce, uint8_t* row) {
     if (ce <= cs) {
@@ -715,26 +712,20 @@ __device__ inline void chunk_fn_t8(const R& rd, uint64_t cs, uint64_t ce, uint8_
     }
 }
 
-// The state a chunk's row (chunk_fn_t8) leads state x to.
+// The state a chunk's row (chunk_fn_t8) leads state x to: the row's entry
+// for x's position in the image of the chunk's first byte.
 template <class R>
 __device__ __forceinline__ uint32_t chunk_apply(const R& rd, const uint8_t* row, uint32_t x) {
-    const int n = row[1];
-    if (n == 0) return x;
-    const uint32_t c = row[0], y = rd.next(x, c);
-    int lo = rd.img_off[c], hi = lo + n - 1;  // the image is ascending and holds y
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (rd.img[mid] < y) lo = mid + 1;
-        else hi = mid;
-    }
-    return row[2 + (lo - rd.img_off[c])];
+    if (row[1] == 0) return x;
+    return row[2 + __ldg(rd.imgpos + (uint32_t)row[0] * rd.K + x)];
 }
 
 // One warp advances the cache state x0 over bytes [s, e) (absolute
 // addresses) and returns the state reached (the same in every lane).  rd
 // reads the one-byte cache rows.  Lane l computes the transfer function of
 // chunk l (of 32) with chunk_fn_t8 into row l of wsm (`stride` >= K + 2
-// bytes each); lane 0 applies the 32 rows to x0 in order.
+// bytes each); lane 0 applies the 32 rows to x0 in order (the rows were
+// just written by this warp, so the chain mostly hits L1).
 template <class R>
 __device__ inline uint32_t warp_chunked_t8(const R& rd, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
     const int lane = threadIdx.x & 31;
@@ -755,7 +746,8 @@ __device__ inline uint32_t warp_chunked_t8(const R& rd, uint32_t x0, uint64_t s,
 // the same with the rows in global memory (the batched and serving forms)
 __device__ inline uint32_t warp_chunked_memo(const DevTables& t, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm,
                                              int stride) {
-    return warp_chunked_t8(GlobalT8{t.memo_T8, t.memo_img_off, t.memo_img}, x0, s, e, wsm, stride);
+    return warp_chunked_t8(GlobalT8{t.memo_T8, t.memo_img_off, t.memo_img, t.memo_imgpos, t.memo_K}, x0, s, e, wsm,
+                           stride);
 }
 
 // ---------------------------------------------------------------------------
