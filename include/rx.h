@@ -457,11 +457,12 @@ typedef struct {
                                     memory is copied at full link speed)  */
     int32_t long_threshold;      /* requests longer than this (bytes) run
                                     the chunked mode (rx_match_long) on
-                                    their own streams; 0 = 32 MiB.  Below
-                                    it, a request with a cache of macro
-                                    steps and more than 2 ticks left takes
-                                    a warp per tick and advances 32 ticks'
-                                    bytes (chunk transfer functions)        */
+                                    their own streams; 0 = 32 MiB; requests
+                                    without a cache of macro steps from
+                                    min(this, 1 MiB).  Below it, a request
+                                    with a cache and more than a tick left
+                                    takes a warp per tick and advances 32
+                                    ticks' bytes (chunk transfer functions) */
 } rx_serve_cfg;
 
 typedef struct {

@@ -224,8 +224,9 @@ struct Request {
     int64_t len;
     int64_t t_submit;
     int slot = -1;
-    bool is_long = false;
+    bool is_long = false;   // runs the chunked mode alone on a side stream
     void* long_ws = nullptr;
+    size_t res_off = 0;     // offset of the result byte in long_ws
     cudaEvent_t ev = nullptr;
     int64_t charged = 0;
 };
@@ -240,6 +241,7 @@ struct rx_server {
     rx_serve_cfg cfg{};
     int device = 0;
     int64_t budget = 0, long_threshold = 1 << 20;
+    static constexpr int64_t kRowsLong = 1 << 20;  // chunked mode for uncached requests from here
     static constexpr int kLongStreams = 4;
     static constexpr int64_t kTickGrow = 8;
     static constexpr size_t kMaxLong = 32;
@@ -309,7 +311,10 @@ void rx_server::run() {
             // admission: by free slots / long capacity and the device-byte budget
             while (!pending.empty()) {
                 Request* r = pending.front();
-                bool lng = r->len > long_threshold && long_supported(r->h->dev);
+                // without a cache a request advances only a few KiB per tick
+                // (bitset steppers), so from 1 MiB it runs the chunked mode
+                const int64_t lt = r->h->dev.memo_K > 0 ? long_threshold : std::min<int64_t>(long_threshold, kRowsLong);
+                bool lng = r->len > lt && long_supported(r->h->dev);
                 int64_t need = (cfg.device_payload == 1 ? 0 : r->len);
                 if (lng) need += (int64_t)long_workspace_bytes(r->h->dev, r->len, long_chunk_auto(r->h->dev, r->len));
                 bool room = lng ? longs.size() < kMaxLong : !free_slots.empty();
@@ -351,17 +356,17 @@ void rx_server::run() {
                 cudaEventRecord(ce, copy_st);
                 cudaStreamWaitEvent(ls, ce, 0);
                 cudaEventDestroy(ce);
-                int64_t C = long_chunk_auto(r->h->dev, r->len);
-                size_t wsb = long_workspace_bytes(r->h->dev, r->len, C);
-                uint8_t* out = nullptr;
+                const int64_t C = long_chunk_auto(r->h->dev, r->len);
+                const size_t wsb = long_workspace_bytes(r->h->dev, r->len, C);
                 if (cudaMallocAsync(&r->long_ws, wsb + 256, ls) != cudaSuccess) {
                     cudaGetLastError();
                     r->long_ws = nullptr;
                     complete(r, 0, RX_ERR_OOM);
                     continue;
                 }
-                out = static_cast<uint8_t*>(r->long_ws) + wsb;
-                cudaError_t e = launch_long(r->h->dev, r->dptr, r->len, C, out, r->long_ws, wsb, ls);
+                r->res_off = wsb;
+                cudaError_t e = launch_long(r->h->dev, r->dptr, r->len, C, static_cast<uint8_t*>(r->long_ws) + wsb,
+                                            r->long_ws, wsb, ls);
                 r->host.clear();
                 r->host.shrink_to_fit();
                 if (e != cudaSuccess) {
@@ -404,8 +409,8 @@ void rx_server::run() {
         for (int i = 0; i < nslot; i++)
             if (slots[i]) {
                 int c = h_slots[i].cls;
-                // a cached request with more than two ticks left takes a warp
-                if (c == kClsMemo && h_slots[i].len - h_slots[i].pos > 2 * tick) c = kClsMemoLong;
+                // a cached request with more than a tick left takes a warp
+                if (c == kClsMemo && h_slots[i].len - h_slots[i].pos > tick) c = kClsMemoLong;
                 cls_slots[c].push_back(i);
                 tick_span[i] = c == kClsMemoLong ? 32 * span[c] : span[c];
             }
@@ -463,9 +468,8 @@ void rx_server::run() {
                 continue;
             }
             uint8_t res = 0;
-            size_t wsb = long_workspace_bytes(r->h->dev, r->len, long_chunk_auto(r->h->dev, r->len));
             if (q == cudaSuccess)
-                q = cudaMemcpy(&res, static_cast<uint8_t*>(r->long_ws) + wsb, 1, cudaMemcpyDeviceToHost);
+                q = cudaMemcpy(&res, static_cast<uint8_t*>(r->long_ws) + r->res_off, 1, cudaMemcpyDeviceToHost);
             longs.erase(longs.begin() + i);
             complete(r, res, q == cudaSuccess ? RX_OK : RX_ERR_CUDA);
         }

@@ -108,6 +108,30 @@ def test_chunked_long_requests_and_warp_ticks_agree():
     assert (lens > 1024).sum() >= 20 and (lens > 8192).sum() >= 8 and (lens > 32 * 512 * 2).sum() >= 5
 
 
+def test_wide_requests_agree():
+    """Requests whose set is too wide for one thread (the warp class, a
+    sixteenth of the tick bytes per tick), from a few bytes to 600 KB,
+    beside short requests of other expressions: every one agrees with O2."""
+    wide = oracle.parse(b"(" + b"|".join(bytes([97 + j % 26]) + bytes([97 + (j * 5) % 26])
+                                         for j in range(200)) + b")*")
+    small = synth.gen_regex(40, 10, synth.LOWER, synth.item_seed(0xF9, 0))
+    pool = [wide, small]
+    rng = np.random.default_rng(0xF9)
+    reqs = []
+    for k in range(40):
+        ri = k % 2
+        lo, hi = ((100 << 10, 600 << 10) if k % 4 == 0 else (0, 60 << 10)) if ri == 0 else (0, 5000)
+        s = synth.gen_strings(pool[ri], 1, lo, hi, synth.LOWER, synth.item_seed(0xFA, k), p_lang=0.8)
+        reqs.append((ri, s.get(0)))
+    handles = [rx.Regex.from_nodes(wide, 0, rx.COMPILE_NO_MEMO), rx.Regex.from_nodes(small)]
+    assert handles[0].info()["words"] > 8
+    assert sum(len(w) > (64 << 10) for ri, w in reqs if ri == 0) >= 5
+    got, _ = serve_all(handles, reqs, max_inflight=64)
+    want = np.array([oracle.o2(pool[ri], w) for ri, w in reqs], np.uint8)
+    assert (got == want).all(), np.nonzero(got != want)[0]
+    assert 0 < want.sum() < len(want)
+
+
 def test_small_budget_admission_is_exact():
     pool, reqs = workload(seed=0xF5, n_req=80)
     handles = compile_pool(pool)
