@@ -205,7 +205,7 @@ __device__ __forceinline__ void stream_round(const S& proto, uint64_t base, cons
     }
 }
 
-// the two-byte stepper is held to 40 registers: three 512-thread blocks// the two-byte stepper is held to 40 registers: three 512-thread blocks
+// the two-byte stepper is held to 40 registers: three 512-thread blocks
 // (48 warps) per SM, which its shared memory (up to 3 planes) also allows
 template <class S>
 __global__ void __launch_bounds__(STREAM_MAX_BLOCK, has_pairs<S>::value ? 3 : 1)
