@@ -417,7 +417,8 @@ void rx_batch_free(rx_batch_handle b);
  * the images of its elements ("exists p in S", Defs 5.1, 5.2) -- and the
  * functions are composed starting from the evolution of {root}.
  *   str          device, len bytes
- *   chunk_bytes  chunk size, 0 = automatic; any value >= 1 is valid
+ *   chunk_bytes  chunk size, 0 = automatic; any value in [1, 2^32) is
+ *                valid (RX_ERR_INVALID_ARG from 2^32 on)
  *   out          device, 1 byte: 1 iff e |v str
  * Errors: as rx_match.
  */

@@ -654,8 +654,9 @@ rx_status rx_match_batch(const rx_handle* handles, size_t n, const uint8_t* stri
 rx_status rx_match_long(rx_handle h, const uint8_t* str, int64_t len, int64_t chunk_bytes, uint8_t* out,
                         void* stream) {
     RX_GUARD_BEGIN
-    if (!h || h->host_only || !out || len < 0 || (len > 0 && !str) || chunk_bytes < 0) {
-        rx::set_error("rx_match_long: bad argument");
+    if (!h || h->host_only || !out || len < 0 || (len > 0 && !str) || chunk_bytes < 0 ||
+        chunk_bytes >= (int64_t(1) << 32)) {
+        rx::set_error("rx_match_long: bad argument (chunk_bytes 0 or in [1, 2^32))");
         return RX_ERR_INVALID_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);

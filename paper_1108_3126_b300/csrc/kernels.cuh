@@ -104,12 +104,18 @@ cudaError_t batch_plan_upload(const BatchPlan& P, const BatchTab* h_tabs, const 
 rx_status collect_pairs(const rx_handle* handles, size_t n, const char* who, std::vector<BatchTab>& tabs,
                         std::vector<uint32_t>& pair_tab, std::vector<uint8_t>& cls);
 
-// Spans of the chunked mode run from given cache states (stream.cu).
-// A task of chunk j starts at j * C + pstart[j] (pstart null: + P).
-cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
-                              const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
-                              const uint16_t* pstart, uint16_t* res, unsigned* queue, long long max_tasks,
-                              cudaStream_t st);
+// Spans of the chunked mode run from given cache states (stream.cu).  A
+// task of chunk j = task_chunk[k] runs from j * C + pstart[j] to the chunk's
+// end with one state (task_state[k] & 0xFF) or, for the ntask[0] tasks at
+// [pair_base, pair_base + ntask[0]), two (the second in bits 8-15); results
+// go to res[task_res[k]] (and + 1).  ntask[1] one-state tasks sit at
+// [0, ntask[1]).
+// warps of the span kernel resident on the whole GPU for this table
+long long span_resident_warps(const DevTables& t);
+cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C,
+                              const uint32_t* task_chunk, const uint16_t* task_state, const uint32_t* task_res,
+                              const unsigned* ntask, long long pair_base, const uint16_t* pstart, uint16_t* res,
+                              unsigned* queue, long long max_tasks, cudaStream_t st);
 
 // Unanchored search over the search cache (stream.cu): out[i] = earliest
 // end of a matching substring of string i, -1 if none.

@@ -35,12 +35,16 @@ using namespace rx::dev;
 // bytes, kMaxPrefix in all) until at most one distinct live state is among
 // them (the empty set, state 0, stays empty at no cost) -- two states that
 // meet stay together, since a macro step is a function of the set (Def
-// 5.2).  Each distinct live state left is one task of phase 2 (the rest of
-// the chunk from that state); the tasks of a warp's 32 chunks are allotted
-// with one atomic add.  Per chunk j: cb0[j] = c; slot[j*K + i] = task index
-// (relative to toff[j]) of the state image entry i has reached, 0xFFFF if
-// it is the empty set; toff[j] = first task; pstart[j] = prefix bytes
-// consumed.  An incoming state k is then mapped through entry
+// 5.2).  Each distinct live state left needs the rest of the chunk (phase
+// 2); its result slot is toff[j] + its rank among them.  Phase 2 tasks take
+// them in pairs (ranks 2m, 2m + 1: one lane steps both, and drops the
+// second once they meet) and an odd last one alone; pair tasks are stored
+// from index pair_base, one-state tasks from 0.  The slots and tasks of a
+// warp's 32 chunks are allotted with one scan and three atomic adds (ctr[0]
+// slots, ctr[2] pair tasks, ctr[3] one-state tasks).  Per chunk j: cb0[j] =
+// c; slot[j*K + i] = result slot (relative to toff[j]) of the state image
+// entry i has reached, 0xFFFF if it is the empty set; toff[j] = first slot;
+// pstart[j] = prefix bytes consumed.  An incoming state k is then mapped through entry
 // memo_imgpos[c*K + k].  The prefix is kept short because a warp's 32 chunks
 // go through it together.  Each thread keeps dv[K] (the representatives'
 // states) and rk[K] (task number of a state id) as bytes in shared memory
@@ -125,7 +129,8 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
                                                      uint8_t* __restrict__ cb0, uint16_t* __restrict__ pstart,
                                                      unsigned* __restrict__ toff, uint32_t* __restrict__ task_chunk,
                                                      uint16_t* __restrict__ task_state,
-                                                     unsigned* __restrict__ ntask) {
+                                                     uint32_t* __restrict__ task_res, long long pair_base,
+                                                     unsigned* __restrict__ ctr) {
     extern __shared__ __align__(16) uint8_t smem[];
     MemoS8::load(t, smem);
     __syncthreads();
@@ -188,16 +193,26 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
                 }
             }
         }
-        // tasks of the warp's chunks: one atomic add
-        int incl = nl;
+        // slots and tasks of the warp's chunks: one scan of the three counts
+        // packed (slots <= 32 * 192 in bits 0-12, pair tasks <= 32 * 96 in
+        // bits 13-24, one-state tasks <= 32 in bits 25-30)
+        const unsigned mine = (unsigned)nl | ((unsigned)(nl >> 1) << 13) | ((unsigned)(nl & 1) << 25);
+        unsigned incl = mine;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int x = __shfl_up_sync(FULL, incl, d);
+            const unsigned x = __shfl_up_sync(FULL, incl, d);
             if (lane >= d) incl += x;
         }
-        unsigned base = 0;
-        if (lane == 31) base = atomicAdd(ntask, (unsigned)incl);
-        base = __shfl_sync(FULL, base, 31) + (unsigned)(incl - nl);
+        unsigned b_slot = 0, b_pair = 0, b_one = 0;
+        if (lane == 31) {
+            b_slot = atomicAdd(ctr, incl & 0x1FFFu);
+            b_pair = atomicAdd(ctr + 2, (incl >> 13) & 0xFFFu);
+            b_one = atomicAdd(ctr + 3, incl >> 25);
+        }
+        const unsigned excl = incl - mine;
+        const unsigned base = __shfl_sync(FULL, b_slot, 31) + (excl & 0x1FFFu);
+        const unsigned pbase = __shfl_sync(FULL, b_pair, 31) + ((excl >> 13) & 0xFFFu);
+        const unsigned obase = __shfl_sync(FULL, b_one, 31) + (excl >> 25);
         if (valid) {
             for (int i = 0; i < nr; i++) {
                 const uint32_t v = dv[i * nt];
@@ -205,15 +220,28 @@ __global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const ui
             }
             cb0[j] = (uint8_t)c0;
             int i = 0;
+            uint32_t first = 0;  // the first state of the pending pair
 #pragma unroll
             for (int w = 0; w < 6; w++) {
                 uint32_t x = fin.word(w) & (w == 0 ? ~1u : ~0u);
                 while (x) {
-                    task_chunk[base + i] = (uint32_t)j;
-                    task_state[base + i] = (uint16_t)(w * 32 + __ffs(x) - 1);
+                    const uint32_t id = (uint32_t)(w * 32 + __ffs(x) - 1);
+                    if (i & 1) {
+                        const long long tk = pair_base + pbase + (i >> 1);
+                        task_chunk[tk] = (uint32_t)j;
+                        task_state[tk] = (uint16_t)(first | (id << 8));
+                        task_res[tk] = base + (unsigned)i - 1u;
+                    } else {
+                        first = id;
+                    }
                     i++;
                     x &= x - 1;
                 }
+            }
+            if (nl & 1) {
+                task_chunk[obase] = (uint32_t)j;
+                task_state[obase] = (uint16_t)first;
+                task_res[obase] = base + (unsigned)nl - 1u;
             }
             toff[j] = base;
             pstart[j] = (uint16_t)(pos - cs);
@@ -437,12 +465,17 @@ cudaError_t compose_rows(const DevTables& t, uint32_t* a, uint32_t* b, long long
 
 int64_t long_chunk_auto(const DevTables& t, int64_t len) {
     if (t.memo_K > 0) {
-        // enough chunks that the converged tasks (about one per chunk) fill
-        // every lane of the GPU a few times over
-        long long target = (long long)sm_count() * 1536 * 2;
-        int64_t C = (len + target - 1) / std::max<long long>(target, 1);
+        // Phase 2 in one wave: every resident warp of the span kernel takes
+        // at most one round of 32 tasks, all of one chunk length, so the
+        // tasks end together.  Tasks run about one per chunk (pairs of live
+        // states share a lane); chunks are sized for up to 1.25 tasks per
+        // chunk.  Fewer, longer chunks also cut phase 1 and the composition,
+        // whose work grows with the number of chunks.
+        const long long warps = std::max<long long>(span_resident_warps(t), 1);
+        const long long target = std::max<long long>(warps * 32 * 4 / 5, 1);
+        int64_t C = (len + target - 1) / target;
         C = std::max<int64_t>(C, 1024);
-        return (C + 31) & ~int64_t(31);
+        return std::min<int64_t>((C + 31) & ~int64_t(31), (int64_t(1) << 32) - 32);
     }
     int groups = (t.nbits + 31) / 32;
     long long target = (long long)sm_count() * 64 * 8 / std::max(groups, 1);
@@ -454,9 +487,15 @@ int64_t long_chunk_auto(const DevTables& t, int64_t len) {
 struct MemoLongWs {
     uint16_t *pstart, *slot, *task_state, *res, *maps_a, *maps_b;
     uint8_t* cb0;
-    uint32_t* task_chunk;
-    unsigned *toff, *ctr;  // ctr[0]: tasks allotted, ctr[1]: work counter of phase 2
+    uint32_t *task_chunk, *task_res;
+    // ctr[0]: result slots allotted, ctr[1]: work counter of phase 2,
+    // ctr[2]: pair tasks, ctr[3]: one-state tasks
+    unsigned *toff, *ctr;
 };
+
+// phase 2 tasks: at most one one-state task per chunk at [0, J), pair tasks
+// (at most K / 2 per chunk) from J on
+static long long memo_long_tasks(long long J, int K) { return J + J * (long long)(K / 2); }
 
 static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
     size_t off = 0;
@@ -465,14 +504,15 @@ static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
         off += al256(b);
         return w ? w + x : nullptr;
     };
-    const size_t JK = (size_t)J * K;
+    const size_t JK = (size_t)J * K, NT = (size_t)memo_long_tasks(J, K);
     uint8_t* p_pre = take((size_t)J * 2);
     uint8_t* p_slot = take(JK * 2);
-    uint8_t* p_ts = take(JK * 2);
+    uint8_t* p_ts = take(NT * 2);
     uint8_t* p_res = take(JK * 2);
     uint8_t* p_ma = take(JK * 2);
     uint8_t* p_mb = take(JK * 2);
-    uint8_t* p_tc = take(JK * 4);
+    uint8_t* p_tc = take(NT * 4);
+    uint8_t* p_tr = take(NT * 4);
     uint8_t* p_toff = take((size_t)J * 4);
     uint8_t* p_cb0 = take((size_t)J);
     uint8_t* p_q = take(256);
@@ -484,6 +524,7 @@ static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
         o->maps_a = reinterpret_cast<uint16_t*>(p_ma);
         o->maps_b = reinterpret_cast<uint16_t*>(p_mb);
         o->task_chunk = reinterpret_cast<uint32_t*>(p_tc);
+        o->task_res = reinterpret_cast<uint32_t*>(p_tr);
         o->toff = reinterpret_cast<unsigned*>(p_toff);
         o->cb0 = p_cb0;
         o->ctr = reinterpret_cast<unsigned*>(p_q);
@@ -536,13 +577,13 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
         {
             ProfScope ps(st);
             k_chunk_stage<<<(unsigned)std::max<long long>(grid, 1), threads, sm, st>>>(
-                t, str, len, C, J, L.slot, L.cb0, L.pstart, L.toff, L.task_chunk, L.task_state, L.ctr);
+                t, str, len, C, J, L.slot, L.cb0, L.pstart, L.toff, L.task_chunk, L.task_state, L.task_res, J, L.ctr);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         // phase 2: the distinct live states over the rest of their chunks
-        e = launch_span_tasks(t, str, len, C, 0, L.task_chunk, L.task_state, L.ctr, L.pstart, L.res, L.ctr + 1,
-                              J * K, st);
+        e = launch_span_tasks(t, str, len, C, L.task_chunk, L.task_state, L.task_res, L.ctr + 2, J, L.pstart, L.res,
+                              L.ctr + 1, memo_long_tasks(J, K), st);
         if (e != cudaSuccess) return e;
         // composition, left to right; the first level gathers the chunk maps
         const int G = std::max(2, std::min(512, (48 * 1024) / (K * 2)));

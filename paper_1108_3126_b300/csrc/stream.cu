@@ -649,19 +649,104 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_search_tasks(const DevTabl
     }
 }
 
-// Tasks of the chunked long-string mode: task i starts the cache of macro
-// steps in state task_state[i] at byte task_chunk[i] * C + pstart[chunk] of the text and
-// runs to the end of that chunk; res[i] receives the final state id.  Tasks
-// come chunk by chunk, so the 32 lanes of a round cover equal-length spans.
+constexpr int kSpanMaxBlock = 768;
+
+// Tasks of the chunked long-string mode.  A task holds one or two live cache
+// states of one chunk and runs from byte j * C + pstart[j] of the text (j =
+// task_chunk[k]) to the end of that chunk.  Two states of one chunk share a
+// lane: they read the same bytes, and since a macro step is a function of
+// the state (Def 5.2), two states that meet -- compared after every 32-byte
+// block -- stay together, so the second is dropped there and takes the
+// first one's result.  The first state's final id goes to res[task_res[k]],
+// the second's to res[task_res[k] + 1].  ntask[0] two-state tasks sit at
+// [pair_base, pair_base + ntask[0]), ntask[1] one-state tasks at
+// [0, ntask[1]); the two-state rounds are taken first.  Spans of one chunk
+// size, so the 32 lanes of a round cover equal-length spans.
+
+// one 32-byte block for both states of the lanes (b: dead where hasb is
+// false); the pair loop when every valid byte of every lane is in the window
 template <class S>
-__global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_span_tasks(const DevTables t, const uint8_t* __restrict__ str,
-                                                               int64_t len, int64_t C, int64_t P,
-                                                               const uint32_t* __restrict__ task_chunk,
-                                                               const uint16_t* __restrict__ task_state,
-                                                               const unsigned* __restrict__ ntask_p,
-                                                               const uint16_t* __restrict__ pstart,
-                                                               uint16_t* __restrict__ res,
-                                                               unsigned* __restrict__ queue) {
+__device__ __forceinline__ void block32_two(S& a, S& b, bool hasb, const Blk32& v, uint32_t mask) {
+    if constexpr (has_pairs<S>::value) {
+        const bool whole = mask == 0u || mask == 0xffffffffu;
+        uint32_t outw = 0;
+        if (whole && mask) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) outw |= a.out_of_window(word_of(v, q));
+        }
+        if (__all_sync(FULL, whole && outw == 0u)) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t w = word_of(v, q);
+                a.step2(w);
+                if (hasb) b.step2(w);
+                a.step2(w >> 16);
+                if (hasb) b.step2(w >> 16);
+            }
+            return;
+        }
+    }
+    block32(a, v, mask);
+    block32(b, v, hasb ? mask : 0u);
+}
+
+// one block of a task's span, then the checks that end, merge or drop its
+// states.  The first state's result slot is ia, the second's ia + 1; tie:
+// the second met the first and takes its result.  two: warp-uniform, some
+// lane of a two-state round still holds two states.
+// rem: bytes of the span from this block's start, skip: bytes of this block
+// before the span (first block only)
+template <class S>
+__device__ __forceinline__ void span_block(S& a, S& b, bool& hasb, bool& tie, bool& active, uint32_t& ia, bool two,
+                                           const Blk32& v, uint32_t rem, uint32_t skip,
+                                           uint16_t* __restrict__ res) {
+    const uint32_t mask = !active ? 0u : (rem >= 32u ? 0xffffffffu : (1u << rem) - 1u) & ~((1u << skip) - 1u);
+    if (two) block32_two(a, b, hasb, v, mask);
+    else block32(a, v, mask);
+    if (!active) return;
+    if (hasb && a.st == b.st) {  // met: the second state follows the first
+        tie = true;
+        hasb = false;
+        b.kill();
+    }
+    if (hasb && b.dead()) {
+        res[ia + 1] = 0;
+        hasb = false;
+    }
+    if (a.dead()) {
+        res[ia] = 0;
+        if (tie) res[ia + 1] = 0;
+        tie = false;
+        if (hasb) {  // the second state carries on alone
+            a = b;
+            ia += 1;
+            hasb = false;
+            b.kill();
+        } else {
+            active = false;
+            return;
+        }
+    }
+    if (rem <= 32u) {
+        const uint16_t f = (uint16_t)a.state_id();
+        res[ia] = f;
+        if (tie || hasb) res[ia + 1] = tie ? f : (uint16_t)b.state_id();
+        a.kill();
+        b.kill();
+        hasb = false;
+        active = false;
+    }
+}
+
+// The pair stepper is held to 40 registers (two 768-thread blocks per SM);
+// the block size is picked per table size from 256, 512 and 768 threads,
+// whichever keeps the most warps resident beside the planes of the table.
+template <class S>
+__global__ void __launch_bounds__(kSpanMaxBlock, has_pairs<S>::value ? 2 : 1)
+    k_span_tasks(const DevTables t, const uint8_t* __restrict__ str, int64_t len, int64_t C,
+                 const uint32_t* __restrict__ task_chunk, const uint16_t* __restrict__ task_state,
+                 const uint32_t* __restrict__ task_res, const unsigned* __restrict__ ntask, long long pair_base,
+                 const uint16_t* __restrict__ pstart, uint16_t* __restrict__ res, unsigned* __restrict__ queue) {
     extern __shared__ __align__(16) uint8_t smem[];
     S::load(t, smem);
     __syncthreads();
@@ -669,74 +754,104 @@ __global__ void __launch_bounds__(STREAM_MAX_BLOCK) k_span_tasks(const DevTables
     proto.bind(t, smem);
     const int lane = threadIdx.x & 31;
     const uint64_t base = reinterpret_cast<uint64_t>(str);
-    const long long n = *ntask_p;
-    const long long nround = (n + 31) / 32;
+    const long long n2 = ntask[0], n1 = ntask[1];
+    const long long r2 = (n2 + 31) / 32, nround = r2 + (n1 + 31) / 32;
     for (;;) {
         unsigned r = 0;
         if (lane == 0) r = atomicAdd(queue, 1u);
         r = __shfl_sync(FULL, r, 0);
         if ((long long)r >= nround) break;
-        const long long k = (long long)r * 32 + lane;
-        const bool valid = k < n;
+        const bool two_round = (long long)r < r2;  // warp-uniform
+        const long long k = (two_round ? (long long)r : (long long)r - r2) * 32 + lane;
+        const bool valid = k < (two_round ? n2 : n1);
+        const long long ti = two_round ? pair_base + k : k;
         uint64_t s = base, e = base;
-        S st = proto;
-        st.kill();
+        S a = proto, b = proto;
+        a.kill();
+        b.kill();
+        uint32_t ia = 0;
+        bool hasb = false, tie = false;
         if (valid) {
-            const int64_t j = task_chunk[k];
+            const int64_t j = task_chunk[ti];
             const int64_t lo = j * C, hi = min(lo + C, len);
-            s += (uint64_t)min(lo + (pstart ? (int64_t)pstart[j] : P), hi);
+            s += (uint64_t)min(lo + (int64_t)pstart[j], hi);
             e += (uint64_t)hi;
-            st.set_state(task_state[k]);
+            const uint32_t ts = task_state[ti];
+            ia = task_res[ti];
+            a.set_state(ts & 0xFFu);
+            if (two_round) {
+                b.set_state(ts >> 8);
+                hasb = true;
+            }
         }
-        bool active = valid && s < e && !st.dead();
-        // the state when the lane's span ends: the warp keeps stepping every
-        // lane while any is active, so a finished lane's state is taken here
-        uint32_t fin = valid ? st.state_id() : 0u;
-        if (!active) st.kill();
+        bool active = valid && s < e;
+        if (valid && !active) {  // the prefix took the whole chunk
+            res[ia] = (uint16_t)a.state_id();
+            if (hasb) res[ia + 1] = (uint16_t)b.state_id();
+        }
+        if (!active) {
+            a.kill();
+            b.kill();
+            hasb = false;
+        }
+        // the span [s, e) as its first aligned block, the bytes from there
+        // to e (spans are below 4 GiB: chunks are) and the bytes skipped
         uint64_t blk = s & ~uint64_t(31);
+        uint32_t rem = (uint32_t)(e - blk), skip = (uint32_t)(s - blk);
         Blk32 va = ld_blk(blk, active);
-        Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
+        Blk32 vb = ld_blk(blk + 32, active && rem > 32u);
         while (__any_sync(FULL, active)) {
-            block32(st, va, valid_mask(blk, s, e, active));
-            if (active && (blk + 32 >= e || st.dead())) {
-                fin = st.state_id();
-                st.kill();
-                active = false;
-            }
-            va = ld_blk(blk + 64, active && blk + 64 < e);
+            // block A at blk, then block B at blk + 32, each refilled two
+            // blocks ahead right after it is consumed
+            span_block(a, b, hasb, tie, active, ia, two_round && __any_sync(FULL, hasb), va, rem, skip, res);
+            va = ld_blk(blk + 64, active && rem > 64u);
             if (!__any_sync(FULL, active)) break;
-            block32(st, vb, valid_mask(blk + 32, s, e, active));
-            if (active && (blk + 64 >= e || st.dead())) {
-                fin = st.state_id();
-                st.kill();
-                active = false;
-            }
-            vb = ld_blk(blk + 96, active && blk + 96 < e);
+            span_block(a, b, hasb, tie, active, ia, two_round && __any_sync(FULL, hasb), vb, rem - 32u, 0u, res);
+            vb = ld_blk(blk + 96, active && rem > 96u);
             blk += 64;
+            rem -= 64u;
+            skip = 0u;
         }
-        if (valid) res[k] = (uint16_t)fin;
+    }
+}
+
+int resident_blocks(const void* kern, int block, size_t smem);
+
+// the block size (of 768, 512, 256) that keeps the most threads of the span
+// kernel resident beside its table; per_sm = 0 when none fits
+template <class S>
+void span_shape(const DevTables& t, int* block, int* per_sm) {
+    const size_t sm = S::smem_bytes(t);
+    const void* kern = reinterpret_cast<const void*>(k_span_tasks<S>);
+    *block = 256;
+    *per_sm = 0;
+    for (int b : {kSpanMaxBlock, 512, 256}) {
+        const int r = resident_blocks(kern, b, sm);
+        if (r * b > *per_sm * *block) {
+            *per_sm = r;
+            *block = b;
+        }
     }
 }
 
 template <class S>
-cudaError_t launch_span_t(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
-                          const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
-                          const uint16_t* pstart, uint16_t* res, unsigned* queue, long long max_tasks,
-                          cudaStream_t st) {
+cudaError_t launch_span_t(const DevTables& t, const uint8_t* str, int64_t len, int64_t C,
+                          const uint32_t* task_chunk, const uint16_t* task_state, const uint32_t* task_res,
+                          const unsigned* ntask, long long pair_base, const uint16_t* pstart, uint16_t* res,
+                          unsigned* queue, long long max_tasks, cudaStream_t st) {
     size_t sm = S::smem_bytes(t);
     auto kern = k_span_tasks<S>;
     cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    const int block = 256;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, sm);
-    if (e != cudaSuccess) return e;
+    int per_sm = 0, block = 256;
+    span_shape<S>(t, &block, &per_sm);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = std::min<long long>((max_tasks + block - 1) / block, (long long)per_sm * sm_count());
     {
         ProfScope ps(st);
-        kern<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, len, C, P, task_chunk, task_state,
-                                                                        ntask_p, pstart, res, queue);
+        kern<<<(unsigned)std::max<long long>(grid, 1), block, sm, st>>>(t, str, len, C, task_chunk, task_state,
+                                                                        task_res, ntask, pair_base, pstart, res,
+                                                                        queue);
     }
     return cudaGetLastError();
 }
@@ -908,15 +1023,22 @@ cudaError_t launch_search_tasks(const DevTables& t, const uint8_t* str, int64_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, int64_t P,
-                              const uint32_t* task_chunk, const uint16_t* task_state, const unsigned* ntask_p,
-                              const uint16_t* pstart, uint16_t* res, unsigned* queue, long long max_tasks,
-                              cudaStream_t st) {
+long long span_resident_warps(const DevTables& t) {
+    int block = 0, per_sm = 0;
+    if (t.bgp_T) span_shape<MemoPairP>(t, &block, &per_sm);
+    else span_shape<MemoS>(t, &block, &per_sm);
+    return (long long)per_sm * (block / 32) * sm_count();
+}
+
+cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t len, int64_t C,
+                              const uint32_t* task_chunk, const uint16_t* task_state, const uint32_t* task_res,
+                              const unsigned* ntask, long long pair_base, const uint16_t* pstart, uint16_t* res,
+                              unsigned* queue, long long max_tasks, cudaStream_t st) {
     if (t.bgp_T)
-        return launch_span_t<MemoPairP>(t, str, len, C, P, task_chunk, task_state, ntask_p, pstart, res, queue,
-                                        max_tasks, st);
-    return launch_span_t<MemoS>(t, str, len, C, P, task_chunk, task_state, ntask_p, pstart, res, queue, max_tasks,
-                                st);
+        return launch_span_t<MemoPairP>(t, str, len, C, task_chunk, task_state, task_res, ntask, pair_base, pstart,
+                                        res, queue, max_tasks, st);
+    return launch_span_t<MemoS>(t, str, len, C, task_chunk, task_state, task_res, ntask, pair_base, pstart, res,
+                                queue, max_tasks, st);
 }
 
 cudaError_t launch_stream_local(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
