@@ -638,6 +638,65 @@ __device__ inline uint32_t run_t8(const R& rd, uint32_t x, uint64_t s, uint64_t 
     return x;
 }
 
+// M states x[0..M) (0 = unused or empty) over bytes [s, e) together: their
+// lookup chains are independent, so their loads overlap.  After every
+// 16-byte block a state equal to an earlier one is dropped (a macro step is
+// a function of the state, Def 5.2: the two stay equal) and at the end
+// takes that one's result.  Returns the states reached in x.
+template <int M, class R>
+__device__ inline void run_t8_multi(const R& rd, uint32_t (&x)[M], uint64_t s, uint64_t e) {
+    static_assert(M >= 2 && M <= 4, "two to four states");
+    uint32_t link = 0;  // per state m: bit 8 + m set if it met state (link >> 2m) & 3
+    auto any_live = [&]() {
+        uint32_t o = 0;
+#pragma unroll
+        for (int m = 0; m < M; m++) o |= x[m];
+        return o != 0;
+    };
+    uint64_t blk = s & ~uint64_t(15);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    bool any = any_live();
+    if (blk < e && any) v = ld_stream(reinterpret_cast<const uint8_t*>(blk));
+    while (blk < e && any) {
+        const uint64_t nb = blk + 16;
+        uint4 vn = make_uint4(0, 0, 0, 0);
+        if (nb < e) vn = ld_stream(reinterpret_cast<const uint8_t*>(nb));
+        const bool whole = blk >= s && nb <= e;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const uint64_t q = blk + k;
+            if (whole || (q >= s && q < e)) {
+                const uint32_t c = byte_of(v, k);
+#pragma unroll
+                for (int m = 0; m < M; m++)
+                    if (x[m]) x[m] = rd.next(x[m], c);
+            }
+        }
+#pragma unroll
+        for (int m = 1; m < M; m++) {
+#pragma unroll
+            for (int p = 0; p < m; p++)
+                if (x[m] && x[m] == x[p]) {
+                    link |= ((uint32_t)p << (2 * m)) | (1u << (8 + m));
+                    x[m] = 0;
+                }
+        }
+        any = any_live();
+        blk = nb;
+        v = vn;
+    }
+#pragma unroll
+    for (int m = 1; m < M; m++)
+        if (link & (1u << (8 + m))) {
+            const uint32_t p = (link >> (2 * m)) & 3u;
+#pragma unroll
+            for (int q = 0; q < m; q++)
+                if (q == (int)p) x[m] = x[q];
+        }
+}
+
+constexpr int kMulti = 4;  // distinct states of a chunk's rest stepped together
+
 constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states are merged
 
 // One lane computes the transfer function of bytes [cs, ce) (absolute
@@ -654,18 +713,20 @@ constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states a
 // empty at no cost, and two states that meet stay together -- and each
 // distinct one then runs over the rest.  row holds 2 + K bytes; n = 0
 // marks an empty chunk (the identity).  An incoming state k maps to
-// row[2 + imgpos[c*K + k]].
+// row[2 + imgpos[c*K + k]].  The rest of the chunk steps the first kMulti
+// distinct states together (run_t8_multi) in a loop picked by the warp's
+// largest count, so all 32 lanes of the warp must call this together.
 template <class R>
 __device__ inline void chunk_fn_t8(const R& rd, uint64_t cs, uint64_t ce, uint8_t* row) {
-    if (ce <= cs) {
-        row[1] = 0;
-        return;
-    }
-    const uint32_t c = __ldg(reinterpret_cast<const uint8_t*>(cs));
-    const int lo = rd.img_off[c], n = (int)rd.img_off[c + 1] - lo;
+    const bool empty = ce <= cs;
+    if (empty) row[1] = 0;
+    const uint32_t c = empty ? 0u : __ldg(reinterpret_cast<const uint8_t*>(cs));
+    const int lo = empty ? 0 : rd.img_off[c], n = empty ? 0 : (int)rd.img_off[c + 1] - lo;
     uint8_t* dv = row + 2;
-    row[0] = (uint8_t)c;
-    row[1] = (uint8_t)n;
+    if (!empty) {
+        row[0] = (uint8_t)c;
+        row[1] = (uint8_t)n;
+    }
     for (int i = 0; i < n; i++) dv[i] = rd.img[lo + i];
     const uint64_t pe = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
     uint64_t pos = cs + 1;
@@ -688,26 +749,44 @@ __device__ inline void chunk_fn_t8(const R& rd, uint64_t cs, uint64_t ce, uint8_
         pos = end;
         len *= 2;
     }
-    // the rest of the chunk, once per distinct state (a small cache of
-    // (state, result) pairs; a repeat beyond it is run again, same result)
-    uint32_t cv[4], cr[4];
+    // the rest of the chunk: the first kMulti distinct live states together
+    // (run_t8_multi), any further one on its own (a repeat beyond the first
+    // kMulti is run again, same result)
+    uint32_t cv[kMulti], cr[kMulti];
     int nc = 0;
+    for (int i = 0; i < n && nc < kMulti; i++) {
+        const uint32_t v = dv[i];
+        bool seen = v == 0;
+#pragma unroll
+        for (int q = 0; q < kMulti; q++)
+            if (q < nc && cv[q] == v) seen = true;
+        if (!seen) {
+#pragma unroll
+            for (int q = 0; q < kMulti; q++)
+                if (q == nc) cv[q] = v;
+            nc++;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kMulti; q++) cr[q] = q < nc ? cv[q] : 0u;
+    const int most = __reduce_max_sync(FULL, (unsigned)nc);  // warp-uniform
+    if (most <= 1) {
+        cr[0] = cr[0] ? run_t8(rd, cr[0], pos, ce) : 0u;
+    } else if (most == 2) {
+        uint32_t x2[2] = {cr[0], cr[1]};
+        run_t8_multi<2>(rd, x2, pos, ce);
+        cr[0] = x2[0];
+        cr[1] = x2[1];
+    } else {
+        run_t8_multi<4>(rd, cr, pos, ce);
+    }
     for (int i = 0; i < n; i++) {
         const uint32_t v = dv[i];
         uint32_t r = 0xffffffffu;
 #pragma unroll
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < kMulti; q++)
             if (q < nc && cv[q] == v) r = cr[q];
-        if (r == 0xffffffffu) {
-            r = v == 0 ? 0u : run_t8(rd, v, pos, ce);
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (q == nc) {
-                    cv[q] = v;
-                    cr[q] = r;
-                }
-            if (nc < 4) nc++;
-        }
+        if (r == 0xffffffffu) r = v == 0 ? 0u : run_t8(rd, v, pos, ce);
         dv[i] = (uint8_t)r;
     }
 }
