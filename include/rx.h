@@ -90,6 +90,7 @@ typedef enum {
                                    matched (used to inspect the compiler)  */
 #define RX_COMPILE_NO_MEMO 2u   /* do not build the macro-step cache       */
 #define RX_COMPILE_SEARCH 4u    /* also build the search cache (rx_search)  */
+#define RX_COMPILE_NO_WIDE 8u   /* do not build the wide cache tier        */
 
 typedef struct {
     int32_t nodes;        /* nodes reachable from the root                  */
@@ -100,7 +101,9 @@ typedef struct {
     uint32_t variants;    /* bit v set iff rx_variant v can run this handle  */
     int64_t device_bytes; /* device memory held by the handle                */
     int32_t search_states; /* search cache size (0: none; RX_COMPILE_SEARCH) */
-    int32_t pad;
+    int32_t wide_states;  /* wide cache tier size: sets of more than 256
+                             positions whose cache outgrows memo_states' 192
+                             (up to 4096 states, two-byte ids); 0 if none */
 } rx_info_t;
 
 /* --------------------------------------------------------------- compiling */

@@ -28,6 +28,7 @@ VARIANT_NAMES = {0: "auto", 1: "memo", 2: "thread", 3: "sparse", 4: "warp", 5: "
 COMPILE_HOST_ONLY = 1
 COMPILE_NO_MEMO = 2
 COMPILE_SEARCH = 4
+COMPILE_NO_WIDE = 8
 RESULT_INVALID = 2      # result byte of a string with invalid offsets
 SEARCH_INVALID = -2     # rx_search result of a string with invalid offsets
 
@@ -46,7 +47,7 @@ class RxError(RuntimeError):
 class _Info(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_int32), ("positions", ctypes.c_int32), ("words", ctypes.c_int32),
                 ("nullable", ctypes.c_int32), ("memo_states", ctypes.c_int32), ("variants", ctypes.c_uint32),
-                ("device_bytes", ctypes.c_int64), ("search_states", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_int64), ("search_states", ctypes.c_int32), ("wide_states", ctypes.c_int32)]
 
 
 class _Opts(ctypes.Structure):

@@ -85,6 +85,9 @@ static rx_status upload(rx_regex* h) {
     size_t o_imo = take(std::max<size_t>(C.memo_img_off.size(), 1) * 2), o_img = take(std::max<size_t>(C.memo_img.size(), 1));
     size_t o_imp = take(std::max<size_t>(C.memo_imgpos.size(), 1));
     size_t o_sT = take(std::max<size_t>(C.srch_T.size(), 1) * 4);
+    size_t o_wT = take(std::max<size_t>(C.wide_T.size(), 1) * 2), o_wacc = take(std::max<size_t>(C.wide_acc.size(), 1));
+    size_t o_wio = take(std::max<size_t>(C.wide_img_off.size(), 1) * 4), o_wim = take(std::max<size_t>(C.wide_img.size(), 1) * 2);
+    size_t o_wip = take(std::max<size_t>(C.wide_imgpos.size(), 1) * 2);
     size_t o_nd = take(C.nodes.size() * sizeof(int4));
     const int spW = (W <= 4) ? 4 : (W <= 8 ? 8 : 0);
     size_t o_sps = take(spW * 4 + 16), o_spB = take((size_t)256 * spW * 4 + 16),
@@ -108,6 +111,11 @@ static rx_status upload(rx_regex* h) {
     put(o_imo, C.memo_img_off.data(), C.memo_img_off.size() * 2);
     put(o_img, C.memo_img.data(), C.memo_img.size());
     put(o_imp, C.memo_imgpos.data(), C.memo_imgpos.size());
+    put(o_wT, C.wide_T.data(), C.wide_T.size() * 2);
+    put(o_wacc, C.wide_acc.data(), C.wide_acc.size());
+    put(o_wio, C.wide_img_off.data(), C.wide_img_off.size() * 4);
+    put(o_wim, C.wide_img.data(), C.wide_img.size() * 2);
+    put(o_wip, C.wide_imgpos.data(), C.wide_imgpos.size() * 2);
     std::vector<int4> pn(C.nodes.size());
     for (size_t i = 0; i < C.nodes.size(); i++)
         pn[i] = make_int4((int)C.nodes[i].kind | ((int)C.nodes[i].byte << 8), C.nodes[i].l, C.nodes[i].r, C.cont[i]);
@@ -164,6 +172,14 @@ static rx_status upload(rx_regex* h) {
     t.memo_img = b + o_img;
     t.memo_imgpos = b + o_imp;
     t.memo_start = C.memo_start;
+    t.wide_K = C.wide_K;
+    t.wide_maximg = C.wide_maximg;
+    t.wide_T = reinterpret_cast<const uint16_t*>(b + o_wT);
+    t.wide_acc = b + o_wacc;
+    t.wide_img_off = reinterpret_cast<const uint32_t*>(b + o_wio);
+    t.wide_img = reinterpret_cast<const uint16_t*>(b + o_wim);
+    t.wide_imgpos = reinterpret_cast<const uint16_t*>(b + o_wip);
+    t.wide_start = C.wide_start;
     t.bgp_T = C.bgp_T.empty() ? nullptr : reinterpret_cast<const uint16_t*>(b + o_bgp);
     t.bg_lo = C.bg_lo;
     t.variants = C.variants;
@@ -321,7 +337,7 @@ rx_status rx_info(rx_handle h, rx_info_t* out) {
     out->variants = h->host.variants;
     out->device_bytes = h->dev_bytes;
     out->search_states = h->host.srch_K;
-    out->pad = 0;
+    out->wide_states = h->host.wide_K;
     return RX_OK;
 }
 
@@ -567,6 +583,7 @@ rx_status rx_profile_read(int64_t* launches, int64_t* timed, double* kernel_ms) 
 static int batch_class(const rx_regex* h) {
     const Compiled& C = h->host;
     if (C.memo_K > 0) return rx::kClsMemo;
+    if (C.wide_K > 0) return rx::kClsWide;
     if (C.gl_ok) return C.W == 1 ? rx::kClsThread1 : rx::kClsThread2;
     if (C.W <= 4) return rx::kClsSparse4;
     if (C.W <= 8) return rx::kClsSparse8;

@@ -10,7 +10,9 @@
 // (L1/L2 resident) since the lanes of a task may use different expressions.
 //
 // Long pairs with a cache of macro steps (kClsMemoLong) would make one lane
-// the critical path of the whole launch, so a warp takes such a pair alone:
+// the critical path of the whole launch, so a warp takes such a pair alone
+// (as it does every pair of an expression with only the wide cache tier,
+// kClsWide, whose sets are too wide for a lane):
 // its 32 lanes cut the string into 32 chunks; each lane computes its chunk's
 // transfer function on cache states (exact: a macro step acts on states,
 // Def 5.2), merging incoming states that meet within a short prefix, and
@@ -32,6 +34,13 @@ __device__ bool warp_long_memo(const DevTables& t, uint64_t s, uint64_t e, uint8
     return t.memo_acc[x] != 0;
 }
 
+// the same on the wide tier (two-byte state ids); not inlined, so that its
+// registers do not press on the other classes' paths
+__device__ __noinline__ bool warp_long_wide(const DevTables& t, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
+    const uint32_t x = warp_chunked_wide(t, t.wide_start, s, e, wsm, stride);
+    return t.wide_acc[x] != 0;
+}
+
 // 64 registers per thread (two 512-thread blocks per SM); the chunk maps of
 // long pairs live in a per-warp slot of global scratch (`maps`, 64 * stride
 // bytes per resident warp), which keeps shared memory free for occupancy
@@ -50,7 +59,7 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchTab* __restrict__ t
         for (int c = 0; c < kBatchClasses; c++) {
             tfirst[c] = acc;
             long long cnt = seg[c + 1] - seg[c];
-            acc += (c == kClsWarp || c == kClsMemoLong) ? cnt : (cnt + 31) / 32;
+            acc += warp_class(c) ? cnt : (cnt + 31) / 32;
         }
         tfirst[kBatchClasses] = acc;
     }
@@ -66,7 +75,7 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchTab* __restrict__ t
         int c = 0;
         while (c + 1 < kBatchClasses && (long long)task >= tfirst[c + 1]) c++;
         const long long g = (long long)task - tfirst[c];
-        if (c == kClsMemoLong || c == kClsWarp) {
+        if (warp_class(c)) {
             // one pair per warp: an invalid pair is answered by lane 0
             const uint32_t p = perm[seg[c] + g];
             uint64_t s, e;
@@ -78,12 +87,13 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchTab* __restrict__ t
                 continue;
             }
         }
-        if (c == kClsMemoLong) {
+        if (c == kClsMemoLong || c == kClsWide) {
             const uint32_t p = perm[seg[c] + g];
             const DevTables& t = tabs[pair_tab[p]].t;
             const uint64_t s = base + (uint64_t)off[p], e = base + (uint64_t)off[p + 1];
             const size_t slot = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-            bool acc = warp_long_memo(t, s, e, maps + slot * 64 * (size_t)stride, stride);
+            uint8_t* wsm = maps + slot * 64 * (size_t)stride;
+            const bool acc = c == kClsWide ? warp_long_wide(t, s, e, wsm, stride) : warp_long_memo(t, s, e, wsm, stride);
             if (lane == 0) out[p] = acc;
             continue;
         }
@@ -177,12 +187,15 @@ size_t batch_workspace_bytes(size_t n, size_t ntabs) {
 }
 
 // chunk functions of long pairs: a row of 2 + K bytes per lane (K the
-// largest cache over the batch's expressions), rounded to 16; none without
-// a cache
+// largest cache over the batch's expressions; on the wide tier 2 + the
+// largest column image two-byte ids), rounded to 16; none without a cache
 int batch_stride(const BatchTab* h_tabs, size_t ntabs) {
     int stride = 0;
-    for (size_t i = 0; i < ntabs; i++)
-        if (h_tabs[i].t.memo_K > 0) stride = std::max(stride, (int)((h_tabs[i].t.memo_K + 2 + 15) & ~15));
+    for (size_t i = 0; i < ntabs; i++) {
+        const DevTables& t = h_tabs[i].t;
+        if (t.memo_K > 0) stride = std::max(stride, (int)((t.memo_K + 2 + 15) & ~15));
+        else if (t.wide_K > 0) stride = std::max(stride, (int)((2 * (t.wide_maximg + 2) + 15) & ~15));
+    }
     return stride;
 }
 

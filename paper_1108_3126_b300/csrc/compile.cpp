@@ -411,6 +411,8 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
     C.memo_K = 0;
     C.memo_T.clear();
     C.memo_acc.clear();
+    C.wide_K = 0;
+    C.wide_T.clear();
     if (!(flags & RX_COMPILE_NO_MEMO)) {
         struct VHash {
             size_t operator()(const std::vector<uint32_t>& v) const {
@@ -438,25 +440,68 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
             if (!groups[c].empty()) labels.push_back(c);
         std::vector<uint32_t> T;
         bool ok = true;
-        for (size_t k = 0; k < states.size(); k++) {
-            if ((int)states.size() > kMemoMaxStates) {
-                ok = false;
-                break;
-            }
-            T.resize((k + 1) * 256, 0u);
-            for (int c : labels) {
-                std::vector<uint32_t> nx(W, 0u);
-                for (int w = 0; w < W; w++) {
-                    uint32_t s = states[k][w] & C.B[(size_t)c * W + w];
-                    while (s) {
-                        int b = __builtin_ctz(s);
-                        s &= s - 1;
-                        const uint32_t* row = &C.follow_bit[(size_t)(w * 32 + b) * W];
-                        for (int z = 0; z < W; z++) nx[z] |= row[z];
+        // explores states [from, ...) until every successor is known or the
+        // count passes `limit` (then false); T gets their rows (ids * 256)
+        long long work = 0;
+        auto explore = [&](size_t from, int limit) {
+            for (size_t k = from; k < states.size(); k++) {
+                if ((int)states.size() > limit || work > kWideMaxWork) return false;
+                T.resize((k + 1) * 256, 0u);
+                for (int c : labels) {
+                    std::vector<uint32_t> nx(W, 0u);
+                    for (int w = 0; w < W; w++) {
+                        uint32_t s = states[k][w] & C.B[(size_t)c * W + w];
+                        while (s) {
+                            int b = __builtin_ctz(s);
+                            s &= s - 1;
+                            const uint32_t* row = &C.follow_bit[(size_t)(w * 32 + b) * W];
+                            for (int z = 0; z < W; z++) nx[z] |= row[z];
+                            work += W;
+                        }
                     }
+                    int t = get(nx);
+                    T[k * 256 + c] = (uint32_t)t * 256u;
                 }
-                int t = get(nx);
-                T[k * 256 + c] = (uint32_t)t * 256u;
+            }
+            return (int)states.size() <= limit;
+        };
+        ok = explore(0, kMemoMaxStates);
+        if (!ok && W > kSparseMaxWords && !(flags & RX_COMPILE_NO_WIDE)) {
+            // 8b. the wide tier, for sets too wide for a thread: go on from
+            // the first state without a row (the first pass stops between rows)
+            if (explore(T.size() / 256, kWideMaxStates)) {
+                const int K = (int)states.size();
+                std::vector<uint32_t> img_off(257, 0);
+                std::vector<uint16_t> img, imgpos((size_t)K * 256, 0);
+                std::vector<int> at(K);
+                int maximg = 0;
+                for (int c = 0; c < 256 && maximg <= kWideMaxImg; c++) {
+                    std::fill(at.begin(), at.end(), -1);
+                    for (int k = 0; k < K; k++) at[T[(size_t)k * 256 + c] / 256u] = 0;
+                    int n = 0;
+                    for (int k = 0; k < K; k++)
+                        if (at[k] >= 0) {
+                            at[k] = n++;
+                            img.push_back((uint16_t)k);
+                        }
+                    for (int k = 0; k < K; k++)
+                        imgpos[(size_t)c * K + k] = (uint16_t)at[T[(size_t)k * 256 + c] / 256u];
+                    img_off[c + 1] = (uint32_t)img.size();
+                    maximg = std::max(maximg, n);
+                }
+                if (maximg <= kWideMaxImg) {
+                    C.wide_K = K;
+                    C.wide_maximg = maximg;
+                    C.wide_T.resize((size_t)K * 256);
+                    for (size_t i = 0; i < C.wide_T.size(); i++) C.wide_T[i] = (uint16_t)(T[i] / 256u);
+                    C.wide_acc.resize(K);
+                    for (int k = 0; k < K; k++)
+                        C.wide_acc[k] = (states[k][C.null_bit >> 5] >> (C.null_bit & 31)) & 1u;
+                    C.wide_start = (uint32_t)s0;
+                    C.wide_img_off.swap(img_off);
+                    C.wide_img.swap(img);
+                    C.wide_imgpos.swap(imgpos);
+                }
             }
         }
         if (ok && (int)states.size() <= kMemoMaxStates) {

@@ -62,13 +62,16 @@ struct BatchTab {
 };
 // kClsMemoLong: memo pairs longer than BatchLaunch::long_bytes (assigned on
 // the device by the planner from the pair's length), one warp per pair,
-// chunked.
-constexpr int kBatchClasses = 7;
+// chunked.  kClsWide: expressions with the wide cache tier only (sets of
+// more than 256 positions), one warp per pair, chunked on two-byte ids.
+constexpr int kBatchClasses = 8;
 // Task order (longest serial work per lane first): the classes whose lanes
-// walk a whole string, the cached pairs up to long_bytes, then the long
-// cached pairs, whose lanes walk 1/32 of one.
+// walk a whole string, the cached pairs up to long_bytes, then the chunked
+// classes, whose lanes walk 1/32 of one.
 enum { kClsWarp = 0, kClsSparse8 = 1, kClsSparse4 = 2, kClsThread2 = 3, kClsThread1 = 4, kClsMemo = 5,
-       kClsMemoLong = 6 };
+       kClsMemoLong = 6, kClsWide = 7 };
+// one warp per pair (task) rather than 32 pairs a task
+__host__ __device__ constexpr bool warp_class(int c) { return c == kClsWarp || c == kClsMemoLong || c == kClsWide; }
 struct BatchLaunch {
     int stride = 0;               // chunk-function row bytes per lane (batch_stride)
     int block = 256;              // threads per block: 128, 256 or 512

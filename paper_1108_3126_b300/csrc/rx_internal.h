@@ -16,6 +16,15 @@ namespace rx {
 
 // Largest macro-step cache kept: rows of 256 x u32 must fit in shared memory.
 constexpr int kMemoMaxStates = 192;
+// Wide tier: a larger cache with two-byte state ids, for expressions whose
+// reachable sets outgrow the one above (global-memory tables, read by the
+// warp-chunked form).  Kept only when every byte's column image holds at
+// most kWideMaxImg states (a chunk function row is then 4 + 2 * n bytes,
+// within the serving slots' 208-byte rows) and the build stays within
+// kWideMaxWork word operations.
+constexpr int kWideMaxStates = 4096;
+constexpr int kWideMaxImg = 100;
+constexpr long long kWideMaxWork = 200000000;
 // Largest group of same-byte positions one thread-variant lookup covers.
 constexpr int kGroupMaxBits = 8;
 // Largest cache for which the two-byte rows are built (2.5 KB per state).
@@ -56,6 +65,15 @@ struct DevTables {
     const uint8_t* memo_img;
     const uint8_t* memo_imgpos;    // [256*K] entry c*K + k: index of T[k][c] in the image of c
     uint32_t memo_start;     // start state * 256
+    // wide tier (memo_K == 0 only): ids in two bytes, same layout otherwise
+    int32_t wide_K;          // states (0: unavailable); state 0 is the empty set
+    int32_t wide_maximg;     // largest column image
+    const uint16_t* wide_T;  // [K*256] next state id
+    const uint8_t* wide_acc; // [K]
+    const uint32_t* wide_img_off;  // [257]
+    const uint16_t* wide_img;
+    const uint16_t* wide_imgpos;   // [256*K]
+    uint32_t wide_start;     // start state id
     // cache for unanchored search (start set added after every byte);
     // states >= srch_acc0 hold null (a match ends there)
     int32_t srch_K;          // 0: unavailable
@@ -109,6 +127,14 @@ struct Compiled {
     std::vector<uint8_t> memo_img;
     std::vector<uint8_t> memo_imgpos;    // K*256
     uint32_t memo_start = 0;
+    // wide tier (see DevTables::wide_T)
+    int wide_K = 0, wide_maximg = 0;
+    uint32_t wide_start = 0;
+    std::vector<uint16_t> wide_T;
+    std::vector<uint8_t> wide_acc;
+    std::vector<uint32_t> wide_img_off;
+    std::vector<uint16_t> wide_img;
+    std::vector<uint16_t> wide_imgpos;
     // two-byte cache: per state a row of 1024 pair successors (entry
     // 32*j + i after bytes lo+i, lo+j) then 256 byte successors, u16 ids
     // (host only; the device gets the planes below)

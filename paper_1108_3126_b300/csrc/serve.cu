@@ -55,6 +55,7 @@ struct ServeSlot {
 int serve_class(const rx_regex* h) {
     const Compiled& C = h->host;
     if (C.memo_K > 0) return kClsMemo;
+    if (C.wide_K > 0) return kClsWide;
     if (C.gl_ok) return C.W == 1 ? kClsThread1 : kClsThread2;
     if (C.W <= 4) return kClsSparse4;
     if (C.W <= 8) return kClsSparse8;
@@ -137,6 +138,26 @@ __device__ void tick_memo_long(const ServeSlot& sl, int64_t tick, uint32_t* stat
     }
 }
 
+// the same on the wide tier (two-byte state ids): every request of such an
+// expression takes a warp, whatever is left
+__device__ void tick_wide(const ServeSlot& sl, int64_t tick, uint32_t* state, uint8_t* status, uint8_t* wsm) {
+    const DevTables& t = *sl.tab;
+    const int lane = threadIdx.x & 31;
+    const uint32_t x0 = sl.pos > 0 ? state[0] : t.wide_start;
+    const uint64_t base = reinterpret_cast<uint64_t>(sl.data);
+    const int64_t end = min(sl.len, sl.pos + 32 * tick);
+    const uint32_t x = warp_chunked_wide(t, x0, base + sl.pos, base + end, wsm, kMapStride);
+    if (lane != 0) return;
+    if (end >= sl.len || x == 0) {
+        status[0] = 1;
+        status[1] = end >= sl.len ? t.wide_acc[x] : 0;
+    } else {
+        state[0] = x;
+        status[0] = 0;
+    }
+}
+static_assert(2 * (kWideMaxImg + 2) <= kMapStride, "a wide chunk row fits a slot's row");
+
 struct Segs {
     int32_t lo[kBatchClasses + 1];   // slot-order segment of each class
     int32_t task[kBatchClasses + 1]; // first task of each class
@@ -171,10 +192,11 @@ __global__ void __launch_bounds__(256) k_serve_tick(const ServeSlot* __restrict_
     while (c + 1 < kBatchClasses && task >= sg.task[c + 1]) c++;
     const int g = task - sg.task[c];
     const int64_t tick = sg.span[c];
-    if (c == kClsMemoLong) {
+    if (c == kClsMemoLong || c == kClsWide) {
         const int slot = order[sg.lo[c] + g];
-        tick_memo_long(slots[slot], tick, state + (size_t)slot * kStateWords, status + 2 * slot,
-                       maps + (size_t)slot * 64 * kMapStride);
+        uint8_t* wsm = maps + (size_t)slot * 64 * kMapStride;
+        if (c == kClsWide) tick_wide(slots[slot], tick, state + (size_t)slot * kStateWords, status + 2 * slot, wsm);
+        else tick_memo_long(slots[slot], tick, state + (size_t)slot * kStateWords, status + 2 * slot, wsm);
         return;
     }
     if (c == kClsWarp) {
@@ -313,7 +335,9 @@ void rx_server::run() {
                 Request* r = pending.front();
                 // without a cache a request advances only a few KiB per tick
                 // (bitset steppers), so from 1 MiB it runs the chunked mode
-                const int64_t lt = r->h->dev.memo_K > 0 ? long_threshold : std::min<int64_t>(long_threshold, kRowsLong);
+                const int64_t lt = (r->h->dev.memo_K > 0 || r->h->dev.wide_K > 0)
+                                       ? long_threshold
+                                       : std::min<int64_t>(long_threshold, kRowsLong);
                 bool lng = r->len > lt && long_supported(r->h->dev);
                 int64_t need = (cfg.device_payload == 1 ? 0 : r->len);
                 if (lng) need += (int64_t)long_workspace_bytes(r->h->dev, r->len, long_chunk_auto(r->h->dev, r->len));
@@ -412,7 +436,7 @@ void rx_server::run() {
                 // a cached request with more than a tick left takes a warp
                 if (c == kClsMemo && h_slots[i].len - h_slots[i].pos > tick) c = kClsMemoLong;
                 cls_slots[c].push_back(i);
-                tick_span[i] = c == kClsMemoLong ? 32 * span[c] : span[c];
+                tick_span[i] = (c == kClsMemoLong || c == kClsWide) ? 32 * span[c] : span[c];
             }
         {
             std::lock_guard<std::mutex> lk(mu);
@@ -427,7 +451,7 @@ void rx_server::run() {
                 sg.task[c] = tasks;
                 for (int i : cls_slots[c]) h_order[k++] = i;
                 int cnt = (int)cls_slots[c].size();
-                tasks += (c == kClsWarp || c == kClsMemoLong) ? cnt : (cnt + 31) / 32;
+                tasks += warp_class(c) ? cnt : (cnt + 31) / 32;
             }
             sg.lo[kBatchClasses] = k;
             sg.task[kBatchClasses] = tasks;

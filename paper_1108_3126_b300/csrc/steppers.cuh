@@ -132,24 +132,6 @@ struct MemoStep8 {
     __device__ __forceinline__ void restore(const uint32_t* p) { st = p[0]; }
 };
 
-// Bitmaps of cache state ids (< 192) for deduplicating states: the rank of
-// a state (number of set ids below it) is its index in the sorted list.
-constexpr int kBmWords = (kMemoMaxStates + 31) / 32;
-__device__ __forceinline__ uint32_t rank_below(const uint32_t (&bm)[kBmWords], uint32_t v) {
-    uint32_t r = 0;
-#pragma unroll
-    for (int w = 0; w < kBmWords; w++) {
-        const uint32_t x = (w < (int)(v >> 5)) ? bm[w] : (w == (int)(v >> 5) ? (bm[w] & ((1u << (v & 31)) - 1u)) : 0u);
-        r += __popc(x);
-    }
-    return r;
-}
-__device__ __forceinline__ void bm_set(uint32_t (&bm)[kBmWords], uint32_t v) {
-#pragma unroll
-    for (int w = 0; w < kBmWords; w++)
-        if (w == (int)(v >> 5)) bm[w] |= 1u << (v & 31);
-}
-
 struct Thread1Step {
     static constexpr int ROW_WORDS = 1;
     const uint2* desc;
@@ -610,6 +592,16 @@ struct GlobalT8 {
     __device__ __forceinline__ uint32_t next(uint32_t x, uint32_t c) const { return __ldg(T + x * 256u + c); }
 };
 
+// The wide tier (DevTables::wide_T): the same with two-byte state ids.
+struct GlobalT16 {
+    const uint16_t* __restrict__ T;
+    const uint32_t* __restrict__ img_off;
+    const uint16_t* __restrict__ img;
+    const uint16_t* __restrict__ imgpos;  // DevTables::wide_imgpos
+    int K;
+    __device__ __forceinline__ uint32_t next(uint32_t x, uint32_t c) const { return __ldg(T + x * 256u + c); }
+};
+
 // one lane, bytes [s, e) (absolute addresses), from cache state id x;
 // returns the state id reached; stops when the set is empty (state 0).
 // The next 16-byte block is loaded while the current one is stepped.
@@ -700,7 +692,7 @@ constexpr int kMulti = 4;  // distinct states of a chunk's rest stepped together
 constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states are merged
 
 // One lane computes the transfer function of bytes [cs, ce) (absolute
-// addresses) on cache states, as a row:
+// addresses) on cache states, as a row of Id (the cache's state id type):
 //   row[0] = the chunk's first byte c, row[1] = n = the size of the image
 //   of column c (the distinct states any incoming state reaches on c),
 //   row[2 + i] = the state reached from image entry i over the rest.
@@ -708,44 +700,42 @@ constexpr int kPairPrefix = 128;  // bytes of a chunk in which incoming states a
 // a macro step is a function of the set, Def 5.2, so k's path after c is
 // that of T[k][c]).  The image is usually a few states, so no incoming
 // state is stepped on its own.  They advance in stages of 3, 6, 12, ...
-// bytes (at most kPairPrefix bytes in all) until at most one distinct live
-// state is among them -- the empty set (state 0, always entry 0) stays
+// bytes (at most kPairPrefix bytes in all) while at least two distinct live
+// states are among them -- the empty set (state 0, always entry 0) stays
 // empty at no cost, and two states that meet stay together -- and each
-// distinct one then runs over the rest.  row holds 2 + K bytes; n = 0
+// distinct one then runs over the rest.  row holds 2 + n entries; n = 0
 // marks an empty chunk (the identity).  An incoming state k maps to
 // row[2 + imgpos[c*K + k]].  The rest of the chunk steps the first kMulti
 // distinct states together (run_t8_multi) in a loop picked by the warp's
 // largest count, so all 32 lanes of the warp must call this together.
-template <class R>
-__device__ inline void chunk_fn_t8(const R& rd, uint64_t cs, uint64_t ce, uint8_t* row) {
+template <class R, class Id>
+__device__ inline void chunk_fn(const R& rd, uint64_t cs, uint64_t ce, Id* row) {
     const bool empty = ce <= cs;
     if (empty) row[1] = 0;
     const uint32_t c = empty ? 0u : __ldg(reinterpret_cast<const uint8_t*>(cs));
-    const int lo = empty ? 0 : rd.img_off[c], n = empty ? 0 : (int)rd.img_off[c + 1] - lo;
-    uint8_t* dv = row + 2;
+    const int lo = empty ? 0 : (int)rd.img_off[c], n = empty ? 0 : (int)rd.img_off[c + 1] - lo;
+    Id* dv = row + 2;
     if (!empty) {
-        row[0] = (uint8_t)c;
-        row[1] = (uint8_t)n;
+        row[0] = (Id)c;
+        row[1] = (Id)n;
     }
     for (int i = 0; i < n; i++) dv[i] = rd.img[lo + i];
     const uint64_t pe = cs + kPairPrefix < ce ? cs + kPairPrefix : ce;
     uint64_t pos = cs + 1;
-    int live = n - 1;  // entry 0 is the empty set
+    bool several = n > 2;  // entry 0 is the empty set
     uint64_t len = 3;
-    uint32_t bm[kBmWords];
-    while (live > 1 && pos < pe) {
+    while (several && pos < pe) {
         const uint64_t end = pos + len < pe ? pos + len : pe;
-#pragma unroll
-        for (int w = 0; w < kBmWords; w++) bm[w] = 0;
+        uint32_t first = 0;
+        several = false;
         for (int i = 0; i < n; i++) {
             const uint32_t v = run_t8(rd, (uint32_t)dv[i], pos, end);
-            dv[i] = (uint8_t)v;
-            bm_set(bm, v);
+            dv[i] = (Id)v;
+            if (v != 0) {
+                if (first == 0) first = v;
+                else if (v != first) several = true;
+            }
         }
-        int cnt = 0;
-#pragma unroll
-        for (int w = 0; w < kBmWords; w++) cnt += __popc(bm[w]);
-        live = cnt - (int)(bm[0] & 1u);
         pos = end;
         len *= 2;
     }
@@ -787,37 +777,38 @@ __device__ inline void chunk_fn_t8(const R& rd, uint64_t cs, uint64_t ce, uint8_
         for (int q = 0; q < kMulti; q++)
             if (q < nc && cv[q] == v) r = cr[q];
         if (r == 0xffffffffu) r = v == 0 ? 0u : run_t8(rd, v, pos, ce);
-        dv[i] = (uint8_t)r;
+        dv[i] = (Id)r;
     }
 }
 
-// The state a chunk's row (chunk_fn_t8) leads state x to: the row's entry
-// for x's position in the image of the chunk's first byte.
-template <class R>
-__device__ __forceinline__ uint32_t chunk_apply(const R& rd, const uint8_t* row, uint32_t x) {
+// The state a chunk's row (chunk_fn) leads state x to: the row's entry for
+// x's position in the image of the chunk's first byte.
+template <class R, class Id>
+__device__ __forceinline__ uint32_t chunk_apply(const R& rd, const Id* row, uint32_t x) {
     if (row[1] == 0) return x;
     return row[2 + __ldg(rd.imgpos + (uint32_t)row[0] * rd.K + x)];
 }
 
 // One warp advances the cache state x0 over bytes [s, e) (absolute
 // addresses) and returns the state reached (the same in every lane).  rd
-// reads the one-byte cache rows.  Lane l computes the transfer function of
-// chunk l (of 32) with chunk_fn_t8 into row l of wsm (`stride` >= K + 2
-// bytes each); lane 0 applies the 32 rows to x0 in order (the rows were
-// just written by this warp, so the chain mostly hits L1).
-template <class R>
-__device__ inline uint32_t warp_chunked_t8(const R& rd, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
+// reads the cache rows.  Lane l computes the transfer function of chunk l
+// (of 32) with chunk_fn into row l of wsm (`stride` bytes each, at least
+// (2 + the largest column image) ids); lane 0 applies the 32 rows to x0 in
+// order (the rows were just written by this warp, so the chain mostly hits
+// L1).
+template <class R, class Id>
+__device__ inline uint32_t warp_chunked(const R& rd, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm, int stride) {
     const int lane = threadIdx.x & 31;
     const uint64_t L = e - s;
     const uint64_t C = ((L + 31) / 32 + 15) & ~uint64_t(15);
     uint64_t cs = s + (uint64_t)lane * C;
     if (cs > e) cs = e;
     const uint64_t ce = cs + C < e ? cs + C : e;
-    chunk_fn_t8(rd, cs, ce, wsm + lane * stride);
+    chunk_fn<R, Id>(rd, cs, ce, reinterpret_cast<Id*>(wsm + lane * stride));
     __syncwarp();
     uint32_t x = x0;
     if (lane == 0)
-        for (int l = 0; l < 32; l++) x = chunk_apply(rd, wsm + l * stride, x);
+        for (int l = 0; l < 32; l++) x = chunk_apply<R, Id>(rd, reinterpret_cast<const Id*>(wsm + l * stride), x);
     __syncwarp();
     return __shfl_sync(FULL, x, 0);
 }
@@ -825,8 +816,15 @@ __device__ inline uint32_t warp_chunked_t8(const R& rd, uint32_t x0, uint64_t s,
 // the same with the rows in global memory (the batched and serving forms)
 __device__ inline uint32_t warp_chunked_memo(const DevTables& t, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm,
                                              int stride) {
-    return warp_chunked_t8(GlobalT8{t.memo_T8, t.memo_img_off, t.memo_img, t.memo_imgpos, t.memo_K}, x0, s, e, wsm,
-                           stride);
+    return warp_chunked<GlobalT8, uint8_t>(GlobalT8{t.memo_T8, t.memo_img_off, t.memo_img, t.memo_imgpos, t.memo_K},
+                                           x0, s, e, wsm, stride);
+}
+
+// the wide tier (two-byte ids; rows of 2 + wide_maximg ids)
+__device__ inline uint32_t warp_chunked_wide(const DevTables& t, uint32_t x0, uint64_t s, uint64_t e, uint8_t* wsm,
+                                             int stride) {
+    return warp_chunked<GlobalT16, uint16_t>(
+        GlobalT16{t.wide_T, t.wide_img_off, t.wide_img, t.wide_imgpos, t.wide_K}, x0, s, e, wsm, stride);
 }
 
 // ---------------------------------------------------------------------------

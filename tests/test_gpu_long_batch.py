@@ -408,3 +408,55 @@ def test_batched_full_size_vs_o2():
         bad = np.nonzero(got != want)[0]
         assert bad.size == 0, (k, bad[:10])
     assert 0.2 < want.mean() < 0.8
+
+
+def wide_tier_pool(count=4):
+    """Expressions of more than 256 positions whose cache of macro steps
+    outgrows 192 states but fits the wide tier (two-byte ids)."""
+    out = []
+    for nd in synth.serving_pool(pool=300):
+        inf = rx.Regex.from_nodes(nd, 0, rx.COMPILE_HOST_ONLY).info()
+        if inf["memo_states"] == 0 and inf["wide_states"] > 0:
+            out.append(nd)
+        if len(out) == count:
+            break
+    assert len(out) == count
+    return out
+
+
+def test_batched_wide_tier_vs_o2():
+    """Pairs of wide-tier expressions (one warp per pair, 32 chunk functions
+    on two-byte state ids, Def 5.2) mixed with cached and uncached pairs:
+    every pair equals O2 for its own expression, in the unprepared call, the
+    prepared batch and the plain per-pair form; the same expressions
+    compiled without the wide tier (bitset warp stepper) agree."""
+    wide = wide_tier_pool(4)
+    small = synth.gen_regex(60, 10, synth.ALL_BYTES, synth.item_seed(0xFB, 1))
+    exprs = wide + [small]
+    rng = np.random.default_rng(0xFB)
+    parts, rid = [], []
+    for k in range(400):
+        ri = k % len(exprs)
+        hi = int(rng.choice([0, 40, 2000, 30000, 70000], p=[0.05, 0.25, 0.3, 0.3, 0.1]))
+        parts.append(synth.gen_strings(exprs[ri], 1, 0, hi, synth.ALL_BYTES, synth.item_seed(0xFC, k),
+                                       p_lang=0.7, log_len=True).get(0))
+        rid.append(ri)
+    s = synth.pack(parts)
+    rid = np.array(rid, np.int32)
+    want = oracle.o2_pairs(exprs, rid, s.data, s.offsets)
+    assert 0.1 < want.mean() < 0.9
+    for flags in (0, rx.COMPILE_NO_WIDE):
+        handles = [rx.Regex.from_nodes(nd, 0, flags) for nd in exprs]
+        assert all((h.info()["wide_states"] > 0) == (flags == 0) for h in handles[:4])
+        hs = rx.handle_array([handles[i] for i in rid])
+        d, o = dev(s.data), dev(s.offsets)
+        outs = [torch.full((s.n,), 7, dtype=torch.uint8, device="cuda") for _ in range(3)]
+        rx.match_batch(hs, d, o, outs[0])
+        b = rx.Batch(hs)
+        b.run(d, o, outs[1])
+        b.free()
+        rx.match_pairs(hs, d, o, outs[2])
+        torch.cuda.synchronize()
+        for k, x in enumerate(outs):
+            bad = np.nonzero(x.cpu().numpy() != want)[0]
+            assert bad.size == 0, (flags, k, bad[:10])

@@ -132,6 +132,42 @@ def test_wide_requests_agree():
     assert 0 < want.sum() < len(want)
 
 
+def test_wide_tier_requests_agree():
+    """Expressions of more than 256 positions whose cache of macro steps
+    outgrows 192 states get the wide tier (two-byte state ids): each of
+    their requests takes warp ticks of 32 chunk functions composed from the
+    saved state, whatever its length.  Requests from empty to 1 MB, with
+    small ticks so that long ones cross many, agree with O2 and with the
+    same expressions served by the bitset warp stepper (no wide tier)."""
+    wide = []
+    for nd in synth.serving_pool(pool=300):
+        inf = rx.Regex.from_nodes(nd, 0, rx.COMPILE_HOST_ONLY).info()
+        if inf["memo_states"] == 0 and inf["wide_states"] > 0:
+            wide.append(nd)
+        if len(wide) == 3:
+            break
+    small = synth.gen_regex(40, 10, synth.ALL_BYTES, synth.item_seed(0xFD, 0))
+    pool = wide + [small]
+    rng = np.random.default_rng(0xFD)
+    reqs = []
+    for k in range(48):
+        ri = k % len(pool)
+        hi = int(rng.choice([0, 100, 20000, 300000, 1 << 20], p=[0.05, 0.25, 0.35, 0.25, 0.1]))
+        w = synth.gen_strings(pool[ri], 1, 0, hi, synth.ALL_BYTES, synth.item_seed(0xFE, k), p_lang=0.7,
+                              log_len=True).get(0)
+        reqs.append((ri, w))
+    sub = synth.pack([w for _, w in reqs])
+    want = oracle.o2_pairs(pool, np.array([ri for ri, _ in reqs], np.int32), sub.data, sub.offsets)
+    assert 0 < want.sum() < len(want)
+    got = {}
+    for flags in (0, rx.COMPILE_NO_WIDE):
+        handles = [rx.Regex.from_nodes(nd, 0, flags) for nd in pool]
+        assert all((h.info()["wide_states"] > 0) == (flags == 0) for h in handles[:3])
+        got[flags], _ = serve_all(handles, reqs, max_inflight=32, tick_bytes=1024)
+        bad = np.nonzero(got[flags] != want)[0]
+        assert bad.size == 0, (flags, bad)
+
+
 def test_small_budget_admission_is_exact():
     pool, reqs = workload(seed=0xF5, n_req=80)
     handles = compile_pool(pool)

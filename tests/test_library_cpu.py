@@ -174,6 +174,62 @@ def test_memo_cache_is_a_cache_of_macro_steps():
     assert no["memo_states"] == 0 and not (no["variants"] & (1 << rx.VARIANT_MEMO))
 
 
+def reachable_macro_states(r):
+    """Every set reachable from the start by macro steps (Def 5.2 on the
+    evolved sets: S' = union of the evolutions of cont p for p in S
+    labelled c), plus the empty set; counted from the compiler's Glushkov
+    tables, which test_tables_match_glushkov_random pins separately."""
+    t = r.tables()
+    m, W = len(t["pos_node"]), t["words"]
+    nodes = r.tree()
+
+    def bits(words):
+        return sum(int(x) << (32 * i) for i, x in enumerate(words))
+
+    fol = {int(t["pos_bit"][p]): bits(t["follow"][p]) for p in range(m)}
+    lab = {}
+    for p in range(m):
+        c = int(nodes["byte"][t["pos_node"][p]])
+        lab[c] = lab.get(c, 0) | (1 << int(t["pos_bit"][p]))
+    start = bits(t["start"])
+    seen, todo = {0, start}, [start]
+    while todo:
+        S = todo.pop()
+        for c, B in lab.items():
+            x, nx = S & B, 0
+            while x:
+                b = (x & -x).bit_length() - 1
+                x &= x - 1
+                nx |= fol[b]
+            if nx not in seen:
+                seen.add(nx)
+                todo.append(nx)
+    return len(seen)
+
+
+def test_cache_sizes_are_the_reachable_macro_states():
+    """The one-byte cache (<= 192 states) and, for sets of more than 256
+    positions beyond it, the wide tier (two-byte ids) each hold exactly the
+    reachable sets; RX_COMPILE_NO_WIDE and RX_COMPILE_NO_MEMO drop them."""
+    for i in range(3):
+        e = synth.gen_regex(64, 10, synth.LOWER, synth.item_seed(0xCC, i))
+        r = host(e)
+        assert r.info()["memo_states"] == reachable_macro_states(r) and r.info()["wide_states"] == 0
+    wide = 0
+    for nd in synth.serving_pool(pool=120):
+        r = host(nd)
+        inf = r.info()
+        if inf["memo_states"] == 0 and inf["wide_states"] > 0:
+            assert inf["words"] > 8 and inf["wide_states"] > 192
+            assert inf["wide_states"] == reachable_macro_states(r)
+            assert host(nd, rx.COMPILE_HOST_ONLY | rx.COMPILE_NO_WIDE).info()["wide_states"] == 0
+            assert host(nd, rx.COMPILE_HOST_ONLY | rx.COMPILE_NO_MEMO).info()["wide_states"] == 0
+            wide += 1
+            if wide == 2:
+                break
+    assert wide == 2
+
+
 def test_host_only_handle_cannot_match():
     r = host(b"abc")
     with pytest.raises(rx.RxError) as ei:
