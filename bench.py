@@ -3,9 +3,11 @@
 Headline workload (N=1): one random 64-node expression over a..z against
 1,048,576 strings with lengths uniform in [1, 1024] (~537 MB packed, int64
 offsets), half language samples and half edited language samples, seeded.
-A step is one call of the public batch entry point (rx_match: length-sort
-planner + lockstep kernel + accept) over the whole batch, inputs resident in
-HBM (537 MB, larger than the 126 MB L2, so no flush is needed between steps).
+A step is one call of the public batch entry point (rx_match: one launch in
+which each block orders its own strings by length in shared memory and runs
+the lockstep steps and the accept test) over the whole batch, inputs
+resident in HBM (537 MB, larger than the 126 MB L2, so no flush is needed
+between steps).
 
 At N=1 the same JSON line also carries, under "configs", the other four
 workloads: small (16 nodes, 4096 strings; with Section 8's machine timed on
@@ -616,7 +618,11 @@ def cfg_batched_result(args, dev):
     # prepared batch: expressions fixed once, every step a replay of the
     # captured graph, after the launch-shape autotuner
     plan = rx.Batch(hs)
-    tuned = plan.autotune(d_str, d_off, out, stream=stream) if not args.no_autotune else None
+    tuned = None
+    if args.long_pair_bytes > 0:
+        plan.set_shape(args.batch_block, args.long_pair_bytes)
+    elif not args.no_autotune:
+        tuned = plan.autotune(d_str, d_off, out, stream=stream)
     for _ in range(3):
         plan.run(d_str, d_off, out, stream=stream)
     ms, reps = _timed(lambda: plan.run(d_str, d_off, out, stream=stream), stream, dev)
@@ -760,10 +766,17 @@ def _serving_sweep(rx, pool, owners, datas, bufs, fresh_nodes, rates, args, payl
         srv.drain(600000)
         st = srv.stats()
         srv.close()
+        # req/s = completed / (first submission -> last completion); the part
+        # of that span after the last arrival is the drain of the requests
+        # still in flight then
+        span = st["completed"] / max(st["req_per_s"], 1e-9)
+        window = float(arrive[-1] - arrive[0])
         points.append({"rate_target": rate, "requests": nreq, "submit_late_ms": round(late / 1e6, 3),
+                       "arrival_window_s": round(window, 4), "drain_ms": round(1e3 * max(span - window, 0.0), 2),
                        "req_per_s": round(st["req_per_s"], 1), "GB/s": round(st["gb_per_s"], 2),
                        "offered_GB/s": round(rate * float(lens.mean()) / 1e9, 2),
                        "p50_ms": round(st["p50_ns"] / 1e6, 3), "p99_ms": round(st["p99_ns"] / 1e6, 3),
+                       "max_ms": round(st["max_ns"] / 1e6, 3),
                        "ticks": st["ticks"], "peak_inflight": st["peak_inflight"],
                        "mean_bytes": int(lens.mean())})
     for h in fresh_all:
@@ -900,7 +913,7 @@ def main():
     ap.add_argument("--payloads", type=int, default=768, help="serving: payloads (device and host copies)")
     ap.add_argument("--rates", type=float, nargs="+", default=[1000, 3000, 10000, 30000, 100000, 200000])
     ap.add_argument("--seconds", type=float, default=0.5, help="serving: arrival window per rate")
-    ap.add_argument("--max-requests", type=int, default=20000)
+    ap.add_argument("--max-requests", type=int, default=60000)
     ap.add_argument("--plain-requests", type=int, default=300)
     ap.add_argument("--paper-strings", type=int, default=48, help="small: strings timed on Section 8's machine")
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="CPU-baseline budget per config")
@@ -909,6 +922,9 @@ def main():
     ap.add_argument("--variant", default="auto", choices=["auto", "memo", "thread", "sparse", "warp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batched: skip the launch-shape autotuner")
+    ap.add_argument("--long-pair-bytes", type=int, default=0,
+                    help="batched: fix the long-pair threshold (with --batch-block) instead of autotuning")
+    ap.add_argument("--batch-block", type=int, default=256, help="batched: threads per block with --long-pair-bytes")
     ap.add_argument("--no-extra", action="store_true",
                     help="streaming: skip the other four configs (run by default at N=1)")
     ap.add_argument("--strings", type=int, default=1 << 20, help="batch size (default: the full workload)")

@@ -385,7 +385,7 @@ rx_status rx_match_pairs(const rx_handle* handles, size_t n, const uint8_t* stri
  *   Errors: RX_ERR_INVALID_ARG, RX_ERR_CUDA.
  * rx_batch_autotune: runs the batch (results written to out) with every
  *   launch shape -- 128, 256 or 512 threads per block; cached pairs longer
- *   than 0.5, 1, 2, 3, 4, 6 or 8 KiB (2 KiB before tuning), or never,
+ *   than 0.5, 1, 2, 3, 4, 6 or 8 KiB (1 KiB before tuning), or never,
  *   taking a whole warp (32 chunks whose transfer functions are composed) --
  *   timed with CUDA events on `stream`, and keeps the fastest for later
  *   runs; *chosen (optional) receives it and its rate.  Synchronous.

@@ -75,7 +75,7 @@ __host__ __device__ constexpr bool warp_class(int c) { return c == kClsWarp || c
 struct BatchLaunch {
     int stride = 0;               // chunk-function row bytes per lane (batch_stride)
     int block = 256;              // threads per block: 128, 256 or 512
-    long long long_bytes = 2048;  // cached pairs longer than this take a warp
+    long long long_bytes = 1024;  // cached pairs longer than this take a warp
     long long grid_cap = 1;       // resident blocks (set by batch_configure)
 };
 
