@@ -450,7 +450,7 @@ typedef struct {
     int32_t max_inflight;        /* concurrent requests on the device      */
     int32_t queue_capacity;      /* pending requests before RX_ERR_BUSY    */
     int64_t tick_bytes;          /* bytes each in-flight request advances
-                                    per device tick (0 = 16 KiB); with k
+                                    per device tick (0 = 8 KiB); with k
                                     short requests in flight a tick covers
                                     tick_bytes * max(1, min(8, 8 / k))     */
     int32_t device_payload;      /* where submit()'s bytes live: 0 = host,

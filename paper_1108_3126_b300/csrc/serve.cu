@@ -517,7 +517,7 @@ rx_status rx_serve_create(const rx_serve_cfg* cfg, rx_server** out) {
         if (cfg) s->cfg = *cfg;
         if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 1024;
         if (s->cfg.queue_capacity <= 0) s->cfg.queue_capacity = 1 << 16;
-        if (s->cfg.tick_bytes <= 0) s->cfg.tick_bytes = 1 << 14;
+        if (s->cfg.tick_bytes <= 0) s->cfg.tick_bytes = 1 << 13;
         s->long_threshold = s->cfg.long_threshold > 0 ? s->cfg.long_threshold : (1 << 25);
         cudaGetDevice(&s->device);
         size_t fr = 0, tot = 0;
