@@ -344,7 +344,9 @@ int64_t rx_device_faults(int32_t reset);
  * strings/offsets/out as in rx_match.  Pairs are bucketed by variant class
  * and length and ordered by serial work per lane (classes whose lanes walk
  * a whole string, longest first; then cached pairs up to the long-pair
- * threshold; then long cached pairs, a warp each, chunked), and drained by
+ * threshold; then long cached pairs, a warp each, chunked; then pairs of
+ * expressions with only the wide cache tier, a warp each, chunked on
+ * two-byte state ids), and drained by
  * a device work queue; the tables of all distinct handles are uploaded
  * once per call.  The paper has no counterpart for the batching (its
  * closing section names persistent threads and task queues as future work).
@@ -465,8 +467,10 @@ typedef struct {
                                     without a cache of macro steps from
                                     min(this, 1 MiB).  Below it, a request
                                     with a cache and more than a tick left
-                                    takes a warp per tick and advances 32
-                                    ticks' bytes (chunk transfer functions) */
+                                    (with the wide cache tier: every
+                                    request) takes a warp per tick and
+                                    advances 32 ticks' bytes (chunk
+                                    transfer functions)                    */
 } rx_serve_cfg;
 
 typedef struct {

@@ -441,7 +441,8 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
         std::vector<uint32_t> T;
         bool ok = true;
         // explores states [from, ...) until every successor is known or the
-        // count passes `limit` (then false); T gets their rows (ids * 256)
+        // count passes `limit` (then false); T gets their rows (ids * 256).
+        // Both passes share one budget of kWideMaxWork word operations.
         long long work = 0;
         auto explore = [&](size_t from, int limit) {
             for (size_t k = from; k < states.size(); k++) {
