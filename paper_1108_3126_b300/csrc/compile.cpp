@@ -629,16 +629,18 @@ rx_status compile_tree(const rx_node* in, size_t n, int32_t root, uint32_t flags
                 }
                 for (int c = 0; c < 256; c++) row[1024 + c] = (uint16_t)(C.memo_T[(size_t)k * 256 + c] / 256u);
             }
-            // planes of 8 states (40 rows x 256 entries each)
-            auto code = [](uint32_t s) { return (uint16_t)((s >> 3) * 320u + (s & 7u)); };
+            // planes of 8 states: 32 pair rows of 258 entries (256 + a 4-byte
+            // pad, so that the second byte moves a lookup across the banks),
+            // then 8 single-byte rows of 256; 10,304 entries a plane
+            auto code = [](uint32_t s) { return (uint16_t)((s >> 3) * 322u + (s & 7u)); };
             const int planes = (K + 7) / 8;
-            C.bgp_T.assign((size_t)planes * 10240, 0);
+            C.bgp_T.assign((size_t)planes * 10304, 0);
             for (int k = 0; k < K; k++) {
-                uint16_t* P = &C.bgp_T[(size_t)(k >> 3) * 10240 + (size_t)(k & 7) * 32];
+                uint16_t* P = &C.bgp_T[(size_t)(k >> 3) * 10304 + (size_t)(k & 7) * 32];
                 const uint16_t* row = &C.bg_T[(size_t)k * 1280];
                 for (int j = 0; j < 32; j++)
-                    for (int i = 0; i < 32; i++) P[j * 256 + i] = code(row[j * 32 + i]);
-                for (int c = 0; c < 256; c++) P[(32 + (c >> 5)) * 256 + (c & 31)] = code(row[1024 + c]);
+                    for (int i = 0; i < 32; i++) P[j * 258 + i] = code(row[j * 32 + i]);
+                for (int c = 0; c < 256; c++) P[8256 + (c >> 5) * 256 + (c & 31)] = code(row[1024 + c]);
             }
         }
     }

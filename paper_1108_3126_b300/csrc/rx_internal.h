@@ -81,13 +81,13 @@ struct DevTables {
     uint32_t srch_start;     // start state * 256
     int32_t srch_acc0;
     // two-byte cache, for labels inside one 32-value window [bg_lo, bg_lo+32),
-    // in planes of 8 states: plane p = s / 8 holds
-    // 40 rows of 512 bytes; row j < 32 holds, for slot q = s % 8 at byte
-    // 64q, the 32 successors after bytes (lo+i, lo+j); rows 32..39 hold the
-    // 256 byte successors (c at row 32 + c/32, entry c % 32).  Entries are
-    // the successor's shared-memory offset / 64 (plane * 320 + slot), so a
-    // lookup is (state offset) + 2 * (b0 & 31 | (b1 & 31) << 8)
-    const uint16_t* bgp_T;   // [ceil(K/8) * 10240], 0 = unavailable
+    // in planes of 8 states: plane p = s / 8 holds 32 pair rows of 516
+    // bytes (512 + a pad) then 8 rows of 512; pair row j holds, for slot
+    // q = s % 8 at byte 64q, the 32 successors after bytes (lo+i, lo+j);
+    // the single rows hold the 256 byte successors (c at single row c/32,
+    // entry c % 32).  Entries are the successor's shared-memory offset / 64
+    // (plane * 322 + slot), so a lookup is (state offset) + 2 * i + 516 * j
+    const uint16_t* bgp_T;   // [ceil(K/8) * 10304], 0 = unavailable
     int32_t bg_lo;
     uint32_t variants;       // bit v: rx_variant v can run
     int32_t nullable;

@@ -406,11 +406,13 @@ __device__ __forceinline__ uint32_t lds16(uint32_t a) {
 }
 
 // The two-byte cache in planes (see DevTables::bgp_T): st = shared address
-// of the state's slot in its plane; a pair lookup adds 2 * (x & 0x1F1F) to
-// it and the entry read back is the successor's offset / 64.
+// of the state's slot in its plane; a pair lookup (first byte i, second j)
+// adds 2 * i + 516 * j to it -- pair rows are 516 bytes apart, so lanes in
+// one state reading pairs with different second bytes fall in different
+// banks -- and the entry read back is the successor's offset / 64.
 struct MemoPairP {
     static constexpr bool kPairs = true;
-    static constexpr uint32_t PLANE = 20480;  // bytes per 8 states
+    static constexpr uint32_t PLANE = 20608;  // bytes per 8 states: 32 x 516 + 8 x 512
     uint32_t st, base, acc, win;
     __host__ __device__ static size_t planes(const DevTables& t) { return (size_t)(t.memo_K + 7) / 8; }
     __host__ __device__ static size_t smem_bytes(const DevTables& t) { return planes(t) * PLANE + align16(t.memo_K); }
@@ -425,16 +427,19 @@ struct MemoPairP {
         win = (uint32_t)t.bg_lo * 0x01010101u;
     }
     __device__ __forceinline__ void step(uint32_t c) {
-        st = base + lds16(st + 16384u + (c >> 5) * 512u + (c & 31u) * 2u) * 64u;
+        st = base + lds16(st + 16512u + (c >> 5) * 512u + (c & 31u) * 2u) * 64u;
     }
     // x: first byte in bits 0-7, second in bits 8-15 (both inside the
-    // window); higher bits are ignored
-    __device__ __forceinline__ void step2(uint32_t x) { st = base + lds16(st + (x & 0x1F1Fu) * 2u) * 64u; }
+    // window); higher bits are ignored.  y = i + 256 j, y >> 7 = 2 j.
+    __device__ __forceinline__ void step2(uint32_t x) {
+        const uint32_t y = x & 0x1F1Fu;
+        st = base + lds16(st + 2u * (y + (y >> 7))) * 64u;
+    }
     __device__ __forceinline__ uint32_t out_of_window(uint32_t w) const { return (w ^ win) & 0xE0E0E0E0u; }
     __device__ __forceinline__ bool dead() const { return st == base; }
     __device__ __forceinline__ uint32_t state_id() const {
-        const uint32_t o = st - base;
-        return (o / PLANE) * 8u + ((o >> 6) & 7u);
+        const uint32_t o = st - base, p = o / PLANE;
+        return p * 8u + ((o - p * PLANE) >> 6);
     }
     __device__ __forceinline__ bool accept() const { return lds8(acc + state_id()) != 0; }
     __device__ __forceinline__ void kill() { st = base; }
