@@ -51,6 +51,9 @@ using namespace rx::dev;
 // after the table, interleaved across the block's threads (entry k of
 // thread x at k * blockDim + x) so that a warp's accesses fall in distinct
 // banks.
+// The kernel is held to 48 registers (five 256-thread blocks per SM), so
+// the chunks of the automatic chunk size (about 0.8 x 32 per resident warp
+// of phase 2) run in one wave of threads.
 constexpr int kMaxPrefix = 128;
 
 // a set of cache state ids (< 192) in six registers
@@ -124,7 +127,7 @@ __device__ __forceinline__ void load_bytes(const uint8_t* p, int n, uint32_t (&b
         if (i < n) b[i >> 2] |= (uint32_t)__ldg(p + i) << (8 * (i & 3));
 }
 
-__global__ void __launch_bounds__(256) k_chunk_stage(const DevTables t, const uint8_t* __restrict__ str, int64_t len,
+__global__ void __launch_bounds__(256, 5) k_chunk_stage(const DevTables t, const uint8_t* __restrict__ str, int64_t len,
                                                      int64_t C, long long J, uint16_t* __restrict__ slot,
                                                      uint8_t* __restrict__ cb0, uint16_t* __restrict__ pstart,
                                                      unsigned* __restrict__ toff, uint32_t* __restrict__ task_chunk,
