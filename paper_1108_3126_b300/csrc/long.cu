@@ -589,14 +589,14 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
                               L.ctr + 1, memo_long_tasks(J, K), st);
         if (e != cudaSuccess) return e;
         // composition, left to right; the first level gathers the chunk maps
-        // the first level gathers through dependent loads (image position,
-        // slot, result), so it takes blocks of at most 64 chunks: more blocks
-        // per SM, more gathers in flight; later levels fold up to 512 maps
-        const int G = std::max(2, std::min(512, (48 * 1024) / (K * 2)));
-        const int G1 = std::min(G, 64);
-        long long cnt = (J + G1 - 1) / G1;
-        k_compose_first<<<(unsigned)cnt, 256, (size_t)G1 * K * 2, st>>>(L.slot, L.cb0, t.memo_imgpos, L.toff, L.res,
-                                                                        J, K, G1, L.maps_a);
+        // blocks of at most 64 maps: the first level gathers through
+        // dependent loads (image position, slot, result) and the later ones
+        // fold in log2(G) barrier-separated steps, so many small blocks keep
+        // more SMs and warps busy than a few large ones
+        const int G = std::max(2, std::min(64, (48 * 1024) / (K * 2)));
+        long long cnt = (J + G - 1) / G;
+        k_compose_first<<<(unsigned)cnt, 256, (size_t)G * K * 2, st>>>(L.slot, L.cb0, t.memo_imgpos, L.toff, L.res,
+                                                                       J, K, G, L.maps_a);
         prof_count(1);
         uint16_t* cur = L.maps_a;
         uint16_t* nxt = L.maps_b;
