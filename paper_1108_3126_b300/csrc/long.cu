@@ -656,7 +656,7 @@ namespace {
 
 constexpr int kSearchPrefix = 64;
 
-__global__ void __launch_bounds__(256) k_search_stage(const DevTables t, const uint8_t* __restrict__ str,
+__global__ void __launch_bounds__(256, 4) k_search_stage(const DevTables t, const uint8_t* __restrict__ str,
                                                       int64_t len, int64_t C, long long J,
                                                       uint16_t* __restrict__ slot, uint8_t* __restrict__ pacc,
                                                       unsigned* __restrict__ toff, uint32_t* __restrict__ task_chunk,
@@ -916,7 +916,7 @@ cudaError_t launch_search_long(const DevTables& t, const uint8_t* str, int64_t l
     k_search_pairs<<<(unsigned)std::max<long long>(g3, 1), 256, 0, st>>>(L.slot, L.pacc, L.toff, L.res, L.res_acc, J,
                                                                          K, L.fj, L.aj);
     prof_count(1);
-    const int G = (int)std::max<size_t>(2, std::min<size_t>(256, (40 * 1024) / ((size_t)K * 10 + 8)));
+    const int G = (int)std::max<size_t>(2, std::min<size_t>(64, (40 * 1024) / ((size_t)K * 10 + 8)));
     const size_t csm = (size_t)G * K * 10 + (size_t)G * 8 + 16;
     const uint16_t* fi = L.fj;
     const int64_t* ai = L.aj;
