@@ -8,9 +8,10 @@
 
 namespace rx {
 
-// Length buckets used to order strings longest first: 16-byte-wide buckets
-// below 2 KiB (the lanes of a round then end within one 32-byte block of each
-// other), quarter-octave buckets above.
+// Length buckets used to order strings longest first: below 2 KiB one
+// bucket per number of 32-byte blocks a string touches (the lanes of a round
+// then start and end their strings in the same block iterations),
+// quarter-octave buckets above.
 constexpr int kLenBuckets = 384;
 
 struct Workspace {

@@ -3,12 +3,14 @@
 // One lane walks one string, one macro step of the lockstep machine
 // (Rathnayake & Thielecke, SOS 2011, Def 5.2) per byte, the active set in
 // registers (or a state id of the cache of macro steps) and the tables in
-// shared memory.  Work distribution: the planner orders the strings by
-// length, longest first; persistent warps take rounds of 32 consecutive
-// entries from a global counter, so the lanes of a round have (nearly) the
-// same length and finish together, and the longest rounds start first.
-// Input: every lane reads its string in aligned 32-byte blocks (one full
-// sector, two 16-byte loads) with loads issued two blocks ahead.
+// shared memory.  Work distribution: the strings are ordered by length,
+// longest first -- by default each block orders its own range in shared
+// memory (k_stream_local), otherwise the planner orders the whole batch
+// (k_stream) -- and warps take rounds of 32 consecutive entries from a
+// counter, so the lanes of a round have (nearly) the same length and finish
+// together, and the longest rounds start first.  Input: every lane reads its
+// string in aligned 32-byte blocks (one full sector, one 256-bit load) with
+// loads issued two blocks ahead.
 #include <algorithm>
 #include <map>
 #include <mutex>
