@@ -636,6 +636,12 @@ def cfg_batched_result(args, dev):
     plain_ms = _time(lambda: rx.match_pairs(hs, d_str, d_off, out, stream=stream), 1, stream, dev)
     if not (out.cpu().numpy() == res_batch).all():
         raise SystemExit("batched and plain forms disagree")
+    # the plain form's fixed cost per pair: 1-byte strings for the first
+    # 20,000 pairs' expressions
+    k1 = min(n, 20000)
+    one = synth.pack([b"a"] * k1)
+    o_str, o_off = torch.from_numpy(one.data).to(dev), torch.from_numpy(one.offsets).to(dev)
+    ms_1 = _time(lambda: rx.match_pairs(hs[:k1], o_str, o_off, out[:k1], stream=stream), 1, stream, dev)
     clk = clocks.stop()
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(0x5EED0003)
@@ -667,7 +673,8 @@ def cfg_batched_result(args, dev):
             "unprepared_call": {"ms": round(ms_call, 4), "GB/s": round(total / (ms_call * 1e-3) / 1e9, 2),
                                 "gpu_launches_per_call": launches / max(timed, 1)},
             "plain_per_pair": {"ms": round(plain_ms, 2), "GB/s": round(total / (plain_ms * 1e-3) / 1e9, 3),
-                               "launches": n, "us_per_pair": round(1e3 * plain_ms / n, 2)},
+                               "launches": n, "us_per_pair": round(1e3 * plain_ms / n, 2),
+                               "us_per_pair_1_byte": round(1e3 * ms_1 / k1, 2)},
             "batched_over_plain": round(plain_ms / ms, 1),
             "roofline": _roofline(total + 8 * (n + 1) + n, kernel_ms, "k_batch (unprepared call)", ms),
             "cpu_baseline": {"value": cpu_v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": cpu_desc},
