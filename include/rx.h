@@ -80,7 +80,9 @@ typedef enum {
     RX_VARIANT_MEMO = 1,   /* cached macro steps: one table lookup per byte      */
     RX_VARIANT_THREAD = 2, /* one thread per string, register bitset (<= 63 pos) */
     RX_VARIANT_SPARSE = 3, /* one thread per string, bitset words + follow rows  */
-    RX_VARIANT_WARP = 4,   /* one warp per string, lane-owned bitset words       */
+    RX_VARIANT_WARP = 4,   /* one warp per string, lane-owned bitset words; for
+                              an expression with the wide cache tier, 32 chunk
+                              functions on it instead                           */
     RX_VARIANT_PAPER = 5   /* Section 8's machine: one thread per node, c/n
                               stamp vectors, one launch per micro-step          */
 } rx_variant;

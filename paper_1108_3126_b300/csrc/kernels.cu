@@ -118,6 +118,59 @@ __global__ void __launch_bounds__(256) k_warp(const DevTables t, const uint8_t* 
     }
 }
 
+// One warp per string on the wide cache tier (two-byte state ids, sets of
+// more than 256 positions): 32 chunk functions composed from the start
+// state (warp_chunked_wide), their rows in shared memory (32 rows of
+// `stride` bytes per warp), so the call needs no scratch.
+constexpr int kWideBlock = 256;
+__global__ void __launch_bounds__(kWideBlock) k_warp_wide(const DevTables t, const uint8_t* __restrict__ str,
+                                                          const int64_t* __restrict__ off,
+                                                          const uint32_t* __restrict__ perm, long long n,
+                                                          uint8_t* __restrict__ out, unsigned* __restrict__ queue,
+                                                          unsigned long long* __restrict__ bad, int stride) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint8_t* wsm = smem + (size_t)(threadIdx.x >> 5) * 32 * stride;
+    const int lane = threadIdx.x & 31;
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    for (;;) {
+        unsigned task = 0;
+        if (lane == 0) task = atomicAdd(queue, 1u);
+        task = __shfl_sync(FULL, task, 0);
+        if ((long long)task >= n) break;
+        const long long id = perm ? (long long)perm[task] : (long long)task;
+        uint64_t s, e;
+        if (!string_span(off, id, base, s, e)) {  // warp-uniform
+            if (lane == 0) {
+                out[id] = kResultInvalid;
+                count_bad(bad);
+            }
+            continue;
+        }
+        const uint32_t x = warp_chunked_wide(t, t.wide_start, s, e, wsm, stride);
+        if (lane == 0) out[id] = t.wide_acc[x];
+    }
+}
+
+cudaError_t launch_warp_wide(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
+                             const uint32_t* perm, uint8_t* out, unsigned* queue, cudaStream_t st) {
+    const int stride = (2 * (t.wide_maximg + 2) + 15) & ~15;
+    const size_t sm = (size_t)(kWideBlock / 32) * 32 * stride;
+    cudaError_t err = allow_smem(k_warp_wide, sm);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_wide, kWideBlock, sm);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = std::min<long long>((long long)per_sm * sm_count(), (n * 32 + kWideBlock - 1) / kWideBlock);
+    if (grid < 1) grid = 1;
+    {
+        ProfScope ps(st);
+        k_warp_wide<<<(unsigned)grid, kWideBlock, sm, st>>>(t, str, off, perm, n, out, queue, bad_offsets_counter(),
+                                                             stride);
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------- length-sort planner
 // Counting sort of the strings by (class, length bucket), longest first
 // within a class, in two launches:
@@ -575,6 +628,7 @@ cudaError_t launch_match(const DevTables& t, int variant, size_t n, const uint8_
         if (t.W <= 4) return launch_thread_kernel<SparseStep<4>>(t, nn, str, off, perm, out, queue, block, st);
         return launch_thread_kernel<SparseStep<8>>(t, nn, str, off, perm, out, queue, block, st);
     case RX_VARIANT_WARP:
+        if (t.wide_K > 0) return launch_warp_wide(t, nn, str, off, perm, out, queue, st);
         if (t.W <= 32) return launch_warp_kernel<1>(t, nn, str, off, perm, out, queue, block, st);
         if (t.W <= 64) return launch_warp_kernel<2>(t, nn, str, off, perm, out, queue, block, st);
         return launch_warp_kernel<4>(t, nn, str, off, perm, out, queue, block, st);

@@ -460,3 +460,29 @@ def test_batched_wide_tier_vs_o2():
         for k, x in enumerate(outs):
             bad = np.nonzero(x.cpu().numpy() != want)[0]
             assert bad.size == 0, (flags, k, bad[:10])
+
+
+def test_match_wide_tier_vs_o2():
+    """rx_match on expressions with only the wide cache tier (one warp per
+    string, 32 chunk functions on two-byte ids, rows in shared memory):
+    every string equals O2, in input order and in length order, and equals
+    the bitset warp stepper (the same expression without the tier)."""
+    wide = wide_tier_pool(2)
+    for e, nd in enumerate(wide):
+        rng = np.random.default_rng(0xFE0 + e)
+        parts = [synth.gen_strings(nd, 1, 0, int(rng.choice([0, 30, 500, 5000, 40000])), synth.ALL_BYTES,
+                                   synth.item_seed(0xFE1 + e, k), p_lang=0.7, log_len=True).get(0)
+                 for k in range(300)]
+        s = synth.pack(parts)
+        want = oracle.o2_batch(nd, s.data, s.offsets)
+        assert 0 < want.sum() < len(want)
+        r = rx.Regex.from_nodes(nd)
+        r0 = rx.Regex.from_nodes(nd, 0, rx.COMPILE_NO_WIDE)
+        assert r.info()["wide_states"] > 0 and r0.info()["wide_states"] == 0
+        d, o = dev(s.data), dev(s.offsets)
+        for h, sort in ((r, -1), (r, 0), (r, 1), (r0, -1)):
+            out = torch.full((s.n,), 7, dtype=torch.uint8, device="cuda")
+            rx.match(h, d, o, out, sort=sort)
+            torch.cuda.synchronize()
+            bad = np.nonzero(out.cpu().numpy() != want)[0]
+            assert bad.size == 0, (e, sort, bad[:10])
