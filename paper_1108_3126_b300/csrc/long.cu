@@ -464,7 +464,100 @@ cudaError_t compose_rows(const DevTables& t, uint32_t* a, uint32_t* b, long long
     return cudaGetLastError();
 }
 
+// ---- chunked mode on the wide cache tier (two-byte state ids)
+// The text is cut into segments; a warp takes a segment, computes the
+// transfer functions of its 32 chunks on the tier (chunk_fn, rows in shared
+// memory) and composes them into one row of the segment in the same image
+// form -- first byte c, image size n, and for each image entry i the state
+// reached from img[c][i] at the segment's end -- its lanes taking the
+// entries.  Rows compose pairwise, (c1, n1, r1) then (c2, n2, r2) =
+// (c1, n1, i -> r2[imgpos[c2][r1[i]]]), level by level; the last row is
+// applied to the start state.  Exact: chunk functions act on states (Def
+// 5.2).  Rows are wide_maximg + 2 entries apart in global memory.
+__device__ __forceinline__ uint32_t wide_apply(const DevTables& t, const uint16_t* row, uint32_t x) {
+    if (row[1] == 0) return x;
+    return row[2 + __ldg(t.wide_imgpos + (uint32_t)row[0] * t.wide_K + x)];
+}
+
+constexpr int kWideSegBlock = 256;
+
+__global__ void __launch_bounds__(kWideSegBlock) k_wide_segments(const DevTables t, const uint8_t* __restrict__ str,
+                                                                 int64_t len, int64_t seg, long long S,
+                                                                 uint16_t* __restrict__ rows, int rs, int stride) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint8_t* wsm = smem + (size_t)(threadIdx.x >> 5) * 32 * stride;
+    const int lane = threadIdx.x & 31;
+    const GlobalT16 rd{t.wide_T, t.wide_img_off, t.wide_img, t.wide_imgpos, t.wide_K};
+    const uint64_t base = reinterpret_cast<uint64_t>(str);
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long k = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < S; k += wstride) {
+        const int64_t a0 = k * seg < len ? k * seg : len, a1 = (k + 1) * seg < len ? (k + 1) * seg : len;
+        const uint64_t s = base + (uint64_t)a0, e = base + (uint64_t)a1;
+        const uint64_t L = e - s;
+        const uint64_t C = ((L + 31) / 32 + 15) & ~uint64_t(15);
+        uint64_t cs = s + (uint64_t)lane * C;
+        if (cs > e) cs = e;
+        const uint64_t ce = cs + C < e ? cs + C : e;
+        chunk_fn<GlobalT16, uint16_t>(rd, cs, ce, reinterpret_cast<uint16_t*>(wsm + lane * stride));
+        __syncwarp();
+        const uint16_t* r0 = reinterpret_cast<const uint16_t*>(wsm);
+        uint16_t* out = rows + (size_t)k * rs;
+        const int n0 = r0[1];
+        if (lane == 0) {
+            out[0] = r0[0];
+            out[1] = (uint16_t)n0;
+        }
+        for (int i = lane; i < n0; i += 32) {
+            uint32_t x = r0[2 + i];
+            for (int l = 1; l < 32; l++) x = wide_apply(t, reinterpret_cast<const uint16_t*>(wsm + l * stride), x);
+            out[2 + i] = (uint16_t)x;
+        }
+        __syncwarp();
+    }
+}
+
+// one level: row p of out = row 2p of in, then row 2p + 1 (if any); a warp
+// per pair, its lanes over the first row's image entries
+__global__ void k_wide_compose(const DevTables t, const uint16_t* __restrict__ in, long long cnt,
+                               uint16_t* __restrict__ out, int rs) {
+    const int lane = threadIdx.x & 31;
+    const long long np = (cnt + 1) / 2;
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long p = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < np; p += wstride) {
+        const uint16_t* a = in + (size_t)(2 * p) * rs;
+        const uint16_t* b = 2 * p + 1 < cnt ? in + (size_t)(2 * p + 1) * rs : nullptr;
+        uint16_t* o = out + (size_t)p * rs;
+        const int na = a[1];
+        const uint16_t* first = (na == 0 && b) ? b : a;  // an empty first row is the identity
+        const uint16_t* second = (na == 0) ? nullptr : b;
+        const int n = first[1];
+        if (lane == 0) {
+            o[0] = first[0];
+            o[1] = (uint16_t)n;
+        }
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t x = first[2 + i];
+            o[2 + i] = (uint16_t)(second ? wide_apply(t, second, x) : x);
+        }
+    }
+}
+
+__global__ void k_wide_finish(const DevTables t, const uint16_t* __restrict__ row, int has_row, uint8_t* out) {
+    if (threadIdx.x == 0) {
+        const uint32_t x = has_row ? wide_apply(t, row, t.wide_start) : t.wide_start;
+        out[0] = t.wide_acc[x];
+    }
+}
+
 }  // namespace
+
+// wide tier: a row per segment (two buffers); 32 rows a warp in shared
+// memory in the segment kernel
+static size_t wide_row_entries(const DevTables& t) { return (size_t)t.wide_maximg + 2; }
+static size_t wide_seg_smem(const DevTables& t) {
+    const size_t stride = (2 * wide_row_entries(t) + 15) & ~size_t(15);
+    return (size_t)(kWideSegBlock / 32) * 32 * stride;
+}
 
 int64_t long_chunk_auto(const DevTables& t, int64_t len) {
     if (t.memo_K > 0) {
@@ -478,6 +571,21 @@ int64_t long_chunk_auto(const DevTables& t, int64_t len) {
         const long long target = std::max<long long>(warps * 32 * 4 / 5, 1);
         int64_t C = (len + target - 1) / target;
         C = std::max<int64_t>(C, 1024);
+        return std::min<int64_t>((C + 31) & ~int64_t(31), (int64_t(1) << 32) - 32);
+    }
+    if (t.wide_K > 0) {
+        // one segment per resident warp of the segment kernel, at least 4 KiB
+        // (128 bytes a chunk)
+        int per_sm = 0;
+        if (allow_smem(k_wide_segments, wide_seg_smem(t)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wide_segments, kWideSegBlock,
+                                                          wide_seg_smem(t)) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        const long long warps = std::max<long long>(1, (long long)per_sm * (kWideSegBlock / 32) * sm_count());
+        int64_t C = (len + warps - 1) / warps;
+        C = std::max<int64_t>(C, 4096);
         return std::min<int64_t>((C + 31) & ~int64_t(31), (int64_t(1) << 32) - 32);
     }
     int groups = (t.nbits + 31) / 32;
@@ -538,13 +646,15 @@ static size_t memo_long_layout(long long J, int K, uint8_t* w, MemoLongWs* o) {
 size_t long_workspace_bytes(const DevTables& t, int64_t len, int64_t C) {
     long long J = (len + C - 1) / C;
     if (t.memo_K > 0) return memo_long_layout(std::max(J, 1LL), t.memo_K, nullptr, nullptr) + 256;
+    if (t.wide_K > 0) return 2 * al256((size_t)std::max(J, 1LL) * wide_row_entries(t) * 2) + 256;
     int k = rows_kind(t);
     if (!k) return 0;
     int RW = (k == 1) ? 1 : (k == 2 ? 2 : k);
     return 2 * al256((size_t)J * t.nbits * RW * 4) + 256;
 }
 
-bool long_supported(const DevTables& t) { return t.memo_K > 0 || rows_kind(t) != 0; }
+bool long_supported(const DevTables& t) { return t.memo_K > 0 || t.wide_K > 0 || rows_kind(t) != 0; }
+
 
 cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int64_t C, uint8_t* out, void* ws,
                         size_t ws_bytes, cudaStream_t st) {
@@ -608,6 +718,45 @@ cudaError_t launch_long(const DevTables& t, const uint8_t* str, int64_t len, int
             cnt = nb;
         }
         k_finish_memo<<<1, 32, 0, st>>>(t, cur, 1, out);
+        prof_count(1);
+        return cudaGetLastError();
+    }
+    if (t.wide_K > 0) {
+        const int rs = (int)wide_row_entries(t);
+        const int stride = (int)((2 * (size_t)rs + 15) & ~size_t(15));
+        if (J == 0) {
+            k_wide_finish<<<1, 32, 0, st>>>(t, nullptr, 0, out);
+            prof_count(1);
+            return cudaGetLastError();
+        }
+        uint16_t* ra = reinterpret_cast<uint16_t*>(w);
+        uint16_t* rb = reinterpret_cast<uint16_t*>(w + al256((size_t)J * rs * 2));
+        const size_t sm = wide_seg_smem(t);
+        e = allow_smem(k_wide_segments, sm);
+        int per_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wide_segments, kWideSegBlock, sm);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const long long wpb = kWideSegBlock / 32;
+        long long grid = std::min<long long>((J + wpb - 1) / wpb, (long long)per_sm * sm_count());
+        {
+            ProfScope ps(st);
+            k_wide_segments<<<(unsigned)std::max<long long>(grid, 1), kWideSegBlock, sm, st>>>(t, str, len, C, J, ra,
+                                                                                             rs, stride);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        long long cnt = J;
+        while (cnt > 1) {
+            const long long np = (cnt + 1) / 2;
+            const long long g = std::min<long long>((np + 7) / 8, (long long)sm_count() * 16);
+            k_wide_compose<<<(unsigned)std::max<long long>(g, 1), 256, 0, st>>>(t, ra, cnt, rb, rs);
+            prof_count(1);
+            std::swap(ra, rb);
+            cnt = np;
+        }
+        k_wide_finish<<<1, 32, 0, st>>>(t, ra, 1, out);
         prof_count(1);
         return cudaGetLastError();
     }

@@ -486,3 +486,38 @@ def test_match_wide_tier_vs_o2():
             torch.cuda.synchronize()
             bad = np.nonzero(out.cpu().numpy() != want)[0]
             assert bad.size == 0, (e, sort, bad[:10])
+
+
+def test_long_wide_tier_vs_o2():
+    """rx_match_long on an expression with only the wide cache tier: segments
+    of 32 chunk functions on two-byte ids, composed pairwise (Def 5.2).
+    Texts in the language of (e)* and their flipped-last-byte copies, of
+    several lengths and segment sizes, equal O2 and the sequential run."""
+    wide = None
+    for nd in synth.serving_pool(pool=300):
+        st = synth.wrap_star(nd)
+        inf = rx.Regex.from_nodes(st, 0, rx.COMPILE_HOST_ONLY).info()
+        if inf["memo_states"] == 0 and inf["wide_states"] > 0:
+            wide = (nd, st)
+            break
+    assert wide is not None
+    nd, st = wide
+    r = rx.Regex.from_nodes(st)
+    assert r.info()["wide_states"] > 0
+    for total, seed in ((0, 1), (100, 2), (5000, 3), (1 << 20, 4), (6 << 20, 5)):
+        text = synth.star_text(nd, max(total, 1), seed)[:total]
+        texts = [text.tobytes()]
+        if total:
+            flipped = bytearray(texts[0])
+            flipped[-1] ^= 0x55
+            texts.append(bytes(flipped))
+        for t in texts:
+            want = oracle.o2(st, t)
+            d = dev(np.frombuffer(t, np.uint8)) if t else dev(np.zeros(1, np.uint8))
+            for chunk in (0, 4096, 1 << 20):
+                assert long_match(r, d, len(t), chunk) == want, (total, chunk)
+            if len(t) <= 1 << 20:
+                out = torch.full((1,), 7, dtype=torch.uint8, device="cuda")
+                rx.match_seq(r, d, len(t), out)
+                torch.cuda.synchronize()
+                assert int(out.item()) == want, total
