@@ -422,7 +422,11 @@ void rx_batch_free(rx_batch_handle b);
  * step (Def 5.2) over the chunk is computed in parallel from every possible
  * incoming state -- exact because a macro step maps a set to the union of
  * the images of its elements ("exists p in S", Defs 5.1, 5.2) -- and the
- * functions are composed starting from the evolution of {root}.
+ * functions are composed starting from the evolution of {root}.  With the
+ * cache of macro steps the functions act on its states; with only the wide
+ * cache tier a warp takes each chunk (`chunk_bytes` is then the segment a
+ * warp cuts into 32); otherwise on bitset rows of singleton images (sets up
+ * to 256 bits), else the call runs rx_match_seq.
  *   str          device, len bytes
  *   chunk_bytes  chunk size, 0 = automatic; any value in [1, 2^32) is
  *                valid (RX_ERR_INVALID_ARG from 2^32 on)
