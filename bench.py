@@ -56,10 +56,9 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the dominant kernel from an ncu
 # capture, keyed by a hash of that kernel's sources at capture time (null
-# when they have changed since).  Captured on the first 262,144 strings
-# (134.45 MB: 125.60 MB read + 5.95 MB written) and scaled to the full
-# launch by input bytes (537.36 / 134.45).
-TRAFFIC = {("k_stream_local<MemoPairP>", "a11945a9b4c72a0c"): 525.7e6}
+# when they have changed since).  Captured on the full launch (1,048,576
+# strings, 0.55 GB on the device): 564.75 MB read + 5.13 MB written.
+TRAFFIC = {("k_stream_local<MemoPairA>", "2704045033c85ceb"): 569.9e6}
 
 
 def kernel_source_hash() -> str:
@@ -374,9 +373,12 @@ def run_streaming(args, world, rank, local):
         return
     chosen_v = tuned["variant"] if tuned else (variant or (1 if info["memo_states"] else 2))
     chosen_b = tuned["block"] if tuned else 0
+    # the block-local kernel takes the absolute-address form of the two-byte
+    # cache when it fits in 3 planes of 8 states (MemoPairT::abs_fits)
+    local = "k_stream_local<MemoPairA>" if 0 < info["memo_states"] <= 24 else "k_stream_local<MemoPairP>"
     kname = {1: ("k_stream<MemoS>" if (chosen_b & 1) or not info.get("pair", True) else
                  "k_stream_tma<MemoPairP>" if chosen_b & 28 else
-                 "k_stream_local<MemoPairP>" if chosen_b in (0, 768) and n >= 4096 else "k_stream<MemoPairP>"),
+                 local if chosen_b in (0, 768) and n >= 4096 else "k_stream<MemoPairP>"),
              2: "k_stream<Thread1S|Thread2S>", 3: "k_thread<SparseStep>", 4: "k_warp"}[chosen_v]
     src_hash = kernel_source_hash()
     traffic = TRAFFIC.get((kname, src_hash))

@@ -400,8 +400,8 @@ struct MemoS {
 };
 
 __device__ __forceinline__ uint32_t lds16(uint32_t a) {
-    uint16_t v;
-    asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    uint32_t v;
+    asm("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 
@@ -410,30 +410,63 @@ __device__ __forceinline__ uint32_t lds16(uint32_t a) {
 // adds 2 * i + 516 * j to it -- pair rows are 516 bytes apart, so lanes in
 // one state reading pairs with different second bytes fall in different
 // banks -- and the entry read back is the successor's offset / 64.
-struct MemoPairP {
+// kAbs: the copy in shared memory holds the successor's shared address
+// itself (base + offset), so a lookup needs no multiply-add after it; only
+// for tables whose addresses fit in 16 bits (kAbsPlanes planes, checked by
+// abs_fits on the host).
+template <bool kAbs>
+struct MemoPairT {
     static constexpr bool kPairs = true;
     static constexpr uint32_t PLANE = 20608;  // bytes per 8 states: 32 x 516 + 8 x 512
+    static constexpr int kAbsPlanes = 3;
     uint32_t st, base, acc, win;
     __host__ __device__ static size_t planes(const DevTables& t) { return (size_t)(t.memo_K + 7) / 8; }
     __host__ __device__ static size_t smem_bytes(const DevTables& t) { return planes(t) * PLANE + align16(t.memo_K); }
+    // the largest entry, base + offset of the last slot, below 2^16 when the
+    // dynamic shared memory starts at or below smem_start
+    __host__ __device__ static bool abs_fits(const DevTables& t, size_t smem_start) {
+        return planes(t) <= (size_t)kAbsPlanes && smem_start + (planes(t) - 1) * PLANE + 7 * 64 < 65536;
+    }
     __device__ static void load(const DevTables& t, uint8_t* sm) {
-        copy_to_smem(sm, t.bgp_T, planes(t) * PLANE);
+        if constexpr (kAbs) {
+            const uint32_t b = smem_addr(sm);
+            const uint32_t* __restrict__ src = reinterpret_cast<const uint32_t*>(t.bgp_T);
+            uint32_t* d = reinterpret_cast<uint32_t*>(sm);
+            const uint32_t n = (uint32_t)(planes(t) * PLANE / 4);
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                const uint32_t v = __ldg(src + i);
+                d[i] = ((b + (v & 0xFFFFu) * 64u) & 0xFFFFu) | ((b + (v >> 16) * 64u) << 16);
+            }
+        } else {
+            copy_to_smem(sm, t.bgp_T, planes(t) * PLANE);
+        }
         copy_to_smem(sm + planes(t) * PLANE, t.memo_acc, t.memo_K);
     }
+    // the state after the entry at shared address a
+    __device__ __forceinline__ uint32_t next(uint32_t a) const { return kAbs ? lds16(a) : base + lds16(a) * 64u; }
     __device__ void bind(const DevTables& t, uint8_t* sm) {
         base = smem_addr(sm);
         acc = base + (uint32_t)(planes(t) * PLANE);
         set_state(t.memo_start >> 8);
         win = (uint32_t)t.bg_lo * 0x01010101u;
     }
-    __device__ __forceinline__ void step(uint32_t c) {
-        st = base + lds16(st + 16512u + (c >> 5) * 512u + (c & 31u) * 2u) * 64u;
-    }
+    __device__ __forceinline__ void step(uint32_t c) { st = next(st + 16512u + (c >> 5) * 512u + (c & 31u) * 2u); }
     // x: first byte in bits 0-7, second in bits 8-15 (both inside the
     // window); higher bits are ignored.  y = i + 256 j, y >> 7 = 2 j.
     __device__ __forceinline__ void step2(uint32_t x) {
         const uint32_t y = x & 0x1F1Fu;
-        st = base + lds16(st + 2u * (y + (y >> 7))) * 64u;
+        st = next(st + 2u * (y + (y >> 7)));
+    }
+    // both pairs of a word w (all four bytes inside the window): (b0, b1)
+    // then (b2, b3).  With z = w & 0x1F1F1F1F, z << 1 holds 2 b0 + 512 b1 in
+    // its low half and 2 b2 + 512 b3 in its high half, and
+    // (z >> 6) & 0x007C007C adds 4 b1 and 4 b3 (the rows' pads): the two
+    // offsets 2 i + 516 j of step2, from one word.
+    __device__ __forceinline__ void step4(uint32_t w) {
+        const uint32_t z = w & 0x1F1F1F1Fu;
+        const uint32_t u = (z << 1) + ((z >> 6) & 0x007C007Cu);
+        st = next(st + (u & 0xFFFFu));
+        st = next(st + (u >> 16));
     }
     __device__ __forceinline__ uint32_t out_of_window(uint32_t w) const { return (w ^ win) & 0xE0E0E0E0u; }
     __device__ __forceinline__ bool dead() const { return st == base; }
@@ -445,6 +478,8 @@ struct MemoPairP {
     __device__ __forceinline__ void kill() { st = base; }
     __device__ __forceinline__ void set_state(uint32_t s) { st = base + (s >> 3) * PLANE + (s & 7u) * 64u; }
 };
+using MemoPairP = MemoPairT<false>;
+using MemoPairA = MemoPairT<true>;
 
 // The search cache (the start set added back after every byte): rows of
 // 256 successors as shared addresses, like MemoS.  Accepting states have the

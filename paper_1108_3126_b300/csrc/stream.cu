@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "plan.cuh"
@@ -45,6 +46,17 @@ __device__ __forceinline__ Blk32 ld_blk(uint64_t addr, bool on) {
                        "=r"(r.b.w)
                      : "l"(addr));
     return r;
+}
+
+// the same load at addr + OFF, issued only when `on`; when it is not, the
+// registers keep their values
+template <int OFF>
+__device__ __forceinline__ void ld_blk_if(Blk32& r, uint64_t addr, bool on) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %9, 0;\n"
+        " @p ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+%10];\n}"
+        : "+r"(r.a.x), "+r"(r.a.y), "+r"(r.a.z), "+r"(r.a.w), "+r"(r.b.x), "+r"(r.b.y), "+r"(r.b.z), "+r"(r.b.w)
+        : "l"(addr), "r"((uint32_t)on), "n"(OFF));
 }
 
 __device__ __forceinline__ uint32_t word_of(const Blk32& v, int q) {
@@ -135,11 +147,7 @@ __device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
         const unsigned f = __reduce_or_sync(FULL, (whole ? 0u : 1u) | (out ? 2u : 0u));
         if (f == 0u) {
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                uint32_t w = word_of(v, q);
-                st.step2(w);
-                st.step2(w >> 16);
-            }
+            for (int q = 0; q < 8; q++) st.step4(word_of(v, q));
             return;
         }
         if (f == 1u) {
@@ -168,9 +176,44 @@ __device__ __forceinline__ void block32(S& st, const Blk32& v, uint32_t mask) {
     }
 }
 
+// A block that lies wholly inside the string of every lane still walking
+// one: no masks and no ends.  `live`: the lane's set is not empty (a lane
+// whose set is empty, or that has no string, skips the lookups).  With the
+// two-byte table every label lies inside its 32-value window, so a byte
+// outside it matches no position and empties the set (Def 5.2): the lane
+// steps the block's pairs with the window bits dropped, then empties its
+// set if any byte was outside.
+template <class S>
+__device__ __forceinline__ void block32_whole(S& st, const Blk32& v, bool live) {
+    if constexpr (has_pairs<S>::value) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) x |= word_of(v, q) ^ st.win;
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) st.step4(word_of(v, q));
+        }
+        if (x & 0xE0E0E0E0u) st.kill();
+    } else {
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t w = word_of(v, q);
+#pragma unroll
+                for (int k = 0; k < 4; k++) st.step(byte_k(w, k));
+            }
+        }
+    }
+}
+
 // One round: lane l walks string `id` (valid: the lane has a string) from
 // its first 32-byte block to its end, or until its set empties (stuck), and
-// writes its result; the warp steps while any lane is active.
+// writes its result; the warp steps while any lane is active.  A string
+// touching nb blocks has whole blocks 1 .. nb-2; the lanes of a round (one
+// length bucket) mostly share nb, so the round runs as its first block with
+// per-lane masks, then the blocks that are whole for every lane with no
+// per-lane bookkeeping, then the rest with masks and ends again.  Each
+// lane's loads run two blocks ahead of its lookups.
 template <class S>
 __device__ __forceinline__ void stream_round(const S& proto, uint64_t base, const int64_t* __restrict__ off,
                                              long long id, bool valid, uint8_t* __restrict__ out,
@@ -182,28 +225,58 @@ __device__ __forceinline__ void stream_round(const S& proto, uint64_t base, cons
     if (valid && !active) out[id] = ok ? (uint8_t)st.accept() : kResultInvalid;
     if (!ok) count_bad(bad);
     if (!active) st.kill();
-    uint64_t blk = s & ~uint64_t(31);
+    if (!__any_sync(FULL, active)) return;
+    const uint64_t blk = s & ~uint64_t(31);
+    // blocks touched (saturated: a string of 128 GiB or more counts 2^32 - 1;
+    // the middle loop stops by 2^31 blocks and the rest compares addresses)
+    const uint64_t nb64 = (e - blk + 31) >> 5;
+    const uint32_t nb = active ? (nb64 < 0xffffffffull ? (uint32_t)nb64 : 0xffffffffu) : 0u;
+    const uint32_t nb_lo = min(__reduce_min_sync(FULL, active ? nb : 0xffffffffu), 0x80000000u);
     Blk32 va = ld_blk(blk, active);
-    Blk32 vb = ld_blk(blk + 32, active && blk + 32 < e);
+    Blk32 vb = ld_blk(blk + 32, nb > 1);
+    // block 0
+    block32(st, va, valid_mask(blk, s, e, active));
+    if (active && (nb == 1 || st.dead())) {
+        out[id] = st.accept();
+        st.kill();
+        active = false;
+    }
+    ld_blk_if<64>(va, blk, active && nb > 2);
+    // vb holds block k and va block k + 1 (p = address of block k); blocks
+    // k and k + 1 are whole for every lane while k + 3 <= nb_lo, and block
+    // k + 2 exists for every lane still walking (k + 2 < nb_lo <= nb)
+    uint32_t k = 1;
+    uint64_t p = blk + 32;
+    while (k + 3 <= nb_lo) {
+        bool live = !st.dead();
+        block32_whole(st, vb, live);
+        ld_blk_if<64>(vb, p, live);
+        live = !st.dead();
+        block32_whole(st, va, live);
+        ld_blk_if<96>(va, p, live && k + 3 < nb);
+        k += 2;
+        p += 64;
+        if (!__any_sync(FULL, live)) break;
+    }
+    // the rest: per-lane masks and ends (vb holds the block at p, va the
+    // block at p + 32)
     while (__any_sync(FULL, active)) {
-        // block A at blk, then block B at blk + 32; each buffer is
-        // refilled two blocks ahead right after it is consumed
-        block32(st, va, valid_mask(blk, s, e, active));
-        if (active && (blk + 32 >= e || st.dead())) {
+        block32(st, vb, valid_mask(p, s, e, active));
+        if (active && (p + 32 >= e || st.dead())) {
             out[id] = st.accept();
             st.kill();
             active = false;
         }
-        va = ld_blk(blk + 64, active && blk + 64 < e);
+        ld_blk_if<64>(vb, p, active && p + 64 < e);
         if (!__any_sync(FULL, active)) break;
-        block32(st, vb, valid_mask(blk + 32, s, e, active));
-        if (active && (blk + 64 >= e || st.dead())) {
+        block32(st, va, valid_mask(p + 32, s, e, active));
+        if (active && (p + 64 >= e || st.dead())) {
             out[id] = st.accept();
             st.kill();
             active = false;
         }
-        vb = ld_blk(blk + 96, active && blk + 96 < e);
-        blk += 64;
+        ld_blk_if<96>(va, p, active && p + 96 < e);
+        p += 64;
     }
 }
 
@@ -296,6 +369,10 @@ __global__ void __launch_bounds__(kLocalThreads, has_pairs<S>::value ? 2 : 1)
     S::load(t, smem);
     S proto;
     proto.bind(t, smem);
+    // the host checked that the 16-bit addresses fit; a layout where they
+    // do not would give wrong results, so it counts a fault
+    if constexpr (std::is_same<S, MemoPairA>::value)
+        if (threadIdx.x == 0 && !S::abs_fits(t, smem_addr(smem))) atomicAdd(&g_wait_faults, 1u);
     const int lane = threadIdx.x & 31;
     const uint64_t base = reinterpret_cast<uint64_t>(str);
     const long long lo = min((long long)blockIdx.x * per_block, n), hi = min(lo + per_block, n);
@@ -1043,10 +1120,31 @@ cudaError_t launch_span_tasks(const DevTables& t, const uint8_t* str, int64_t le
                                 queue, max_tasks, st);
 }
 
+// An upper bound on the shared address where the dynamic shared memory of
+// the absolute-address kernel starts: the block's reserved shared memory,
+// then its static shared memory, plus 1 KiB of slack (65536 when the
+// attributes cannot be read: the absolute form is then never taken).
+static size_t local_abs_smem_start() {
+    static const size_t v = [] {
+        cudaFuncAttributes a{};
+        int dev = 0, reserved = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(k_stream_local<MemoPairA>)) != cudaSuccess ||
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return (size_t)65536;
+        }
+        return (size_t)reserved + a.sharedSizeBytes + 1024;
+    }();
+    return v;
+}
+
 cudaError_t launch_stream_local(const DevTables& t, long long n, const uint8_t* str, const int64_t* off,
                                 uint8_t* out, cudaStream_t st, bool* launched) {
     *launched = false;
     if (!t.bgp_T) return cudaSuccess;
+    if (MemoPairA::abs_fits(t, local_abs_smem_start()))
+        return launch_stream_local_t<MemoPairA>(t, n, str, off, out, st, launched);
     return launch_stream_local_t<MemoPairP>(t, n, str, off, out, st, launched);
 }
 
