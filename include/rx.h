@@ -431,8 +431,10 @@ void rx_batch_free(rx_batch_handle b);
  * warp cuts into 32); otherwise on bitset rows of singleton images (sets up
  * to 256 bits), else the call runs rx_match_seq.
  *   str          device, len bytes
- *   chunk_bytes  chunk size, 0 = automatic; any value in [1, 2^32) is
- *                valid (RX_ERR_INVALID_ARG from 2^32 on)
+ *   chunk_bytes  chunk size, 0 = automatic; any value in [1, 2^32 - 32)
+ *                is valid (RX_ERR_INVALID_ARG from 2^32 - 32 on: a span's
+ *                byte count, with the bytes before it in its first 32-byte
+ *                block, is kept in 32 bits)
  *   out          device, 1 byte: 1 iff e |v str
  * Errors: as rx_match.
  */

@@ -672,8 +672,8 @@ rx_status rx_match_long(rx_handle h, const uint8_t* str, int64_t len, int64_t ch
                         void* stream) {
     RX_GUARD_BEGIN
     if (!h || h->host_only || !out || len < 0 || (len > 0 && !str) || chunk_bytes < 0 ||
-        chunk_bytes >= (int64_t(1) << 32)) {
-        rx::set_error("rx_match_long: bad argument (chunk_bytes 0 or in [1, 2^32))");
+        chunk_bytes >= (int64_t(1) << 32) - 32) {
+        rx::set_error("rx_match_long: bad argument (chunk_bytes 0 or in [1, 2^32 - 32))");
         return RX_ERR_INVALID_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -76,6 +76,21 @@ def test_long_text_chunk_sizes_vs_seq_and_o2(long_case):
     assert long_match(r_bits, d, 50000, 1) == w
 
 
+def test_long_chunk_size_bound(long_case):
+    """chunk_bytes up to 2^32 - 33 is taken (one chunk for a short text),
+    2^32 - 32 and above are rejected: a span's byte count, with the bytes
+    before it in its first 32-byte block, must fit in 32 bits."""
+    nodes, text = long_case
+    r = rx.Regex.from_nodes(nodes)
+    t = text[:100001]
+    d = dev(t)
+    assert long_match(r, d, len(t), (1 << 32) - 33) == oracle.o2(nodes, t.tobytes())
+    for bad in ((1 << 32) - 32, 1 << 32):
+        with pytest.raises(rx.RxError) as ei:
+            long_match(r, d, len(t), bad)
+        assert rx.STATUS[ei.value.status] == "RX_ERR_INVALID_ARG"
+
+
 def test_long_random_expressions_and_edges():
     for i in range(30):
         alpha = [b"abc", synth.LOWER, synth.ALL_BYTES][i % 3]
