@@ -346,6 +346,45 @@ def test_pair_kernel_fallback_outside_the_byte_window():
         assert (run(r, junk) == wantj).all()
 
 
+def test_block_local_kernel_both_table_forms_and_window_bytes():
+    """From 4,096 strings rx_match takes the block-local streaming kernel: a
+    cache of at most 24 states in the form whose two-byte entries are shared
+    addresses, 25-64 states in the form whose entries are offsets / 64.
+    Both forms on 9,000 strings, clean and with bytes outside the label
+    window sprinkled through a third of them -- inside the blocks that are
+    whole for every lane of a round (there such a byte empties the lane's
+    set) as well as in first and last blocks -- against O2, also over the
+    planner's global order and in input order, and no device fault
+    counted."""
+    rng = np.random.default_rng(11)
+    forms = set()
+    rx.device_faults(reset=True)
+    for size, i in ((64, 0), (64, 2), (64, 38), (96, 0)):
+        e = synth.gen_regex(size, 10, synth.LOWER, synth.item_seed(0xE1, size * 100 + i))
+        r = rx.Regex.from_nodes(e)
+        k = r.info()["memo_states"]
+        assert 0 < k <= 64
+        forms.add(k <= 24)
+        s = synth.gen_strings(e, 9000, 1, 700, synth.LOWER, synth.item_seed(0xE2, size * 100 + i), p_lang=0.8)
+        assert (run(r, s) == oracle.o2_batch(e, s.data, s.offsets)).all(), (size, i, k)
+        data = s.data.copy()
+        for j in range(0, s.n, 3):
+            a, b = int(s.offsets[j]), int(s.offsets[j + 1])
+            if b > a:
+                pos = rng.integers(a, b, size=max(1, (b - a) // 131))
+                data[pos] = rng.choice([0x00, 0x41, 0x5F, 0x80, 0x7B, 0xFF], size=len(pos))
+        mixed = synth.Strings(data, s.offsets, s.kind, 0)
+        want = oracle.o2_batch(e, data, s.offsets)
+        got = run(r, mixed)
+        assert (got == want).all(), (size, i, k, np.nonzero(got != want)[0][:10])
+        # the same rounds over the planner's global length order, and in
+        # input order (lengths mixed within a round: mostly the masked blocks)
+        for order in (2, 3):
+            assert (run(r, mixed, sort=order) == want).all(), (size, i, k, order)
+    assert forms == {True, False}
+    assert rx.device_faults() == 0
+
+
 def test_autotune_records_and_is_used():
     w = synth.cfg_streaming(seed=synth.SEED_BASE + 77, n=20000)
     nodes = w.regexes[0]
