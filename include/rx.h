@@ -334,8 +334,8 @@ rx_status rx_search_long(rx_handle h, const uint8_t* str, int64_t len, int64_t c
  * its grid barrier, whose strings then keep their input order; the
  * block-local streaming kernel, in its form whose two-byte cache holds
  * 16-bit shared addresses, counts one per block whose shared memory starts
- * too high for them, a layout the host check rules out, whose results are
- * then not to be trusted).  0 in normal operation.  reset != 0 clears the counter after reading.  Synchronises
+ * too high for them, a layout the host check rules out; that block's
+ * strings get RX_RESULT_INVALID).  0 in normal operation.  reset != 0 clears the counter after reading.  Synchronises
  * the device.  The paper has no counterpart.
  */
 int64_t rx_device_faults(int32_t reset);

@@ -369,13 +369,19 @@ __global__ void __launch_bounds__(kLocalThreads, has_pairs<S>::value ? 2 : 1)
     S::load(t, smem);
     S proto;
     proto.bind(t, smem);
-    // the host checked that the 16-bit addresses fit; a layout where they
-    // do not would give wrong results, so it counts a fault
-    if constexpr (std::is_same<S, MemoPairA>::value)
-        if (threadIdx.x == 0 && !S::abs_fits(t, smem_addr(smem))) atomicAdd(&g_wait_faults, 1u);
+    const long long lo = min((long long)blockIdx.x * per_block, n), hi = min(lo + per_block, n);
+    // the host checked that the table's 16-bit shared addresses fit; in a
+    // layout where they do not (block-uniform), the block counts a fault and
+    // marks its strings invalid instead of walking them
+    if constexpr (std::is_same<S, MemoPairA>::value) {
+        if (!S::abs_fits(t, smem_addr(smem))) {
+            if (threadIdx.x == 0) atomicAdd(&g_wait_faults, 1u);
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) out[i] = kResultInvalid;
+            return;
+        }
+    }
     const int lane = threadIdx.x & 31;
     const uint64_t base = reinterpret_cast<uint64_t>(str);
-    const long long lo = min((long long)blockIdx.x * per_block, n), hi = min(lo + per_block, n);
     for (long long t0 = lo; t0 < hi; t0 += kLocalTile) {
         const int m = (int)min((long long)kLocalTile, hi - t0);
         for (int b = threadIdx.x; b < kLenBuckets; b += blockDim.x) cnt[b] = 0;
