@@ -385,6 +385,32 @@ def test_block_local_kernel_both_table_forms_and_window_bytes():
     assert rx.device_faults() == 0
 
 
+def test_block_local_rounds_of_mixed_block_counts():
+    """6,000 strings (the block-local kernel) of 1 to 20,000 bytes: from 2 KiB
+    on the length buckets are log-spaced, so the lanes of a round touch
+    different numbers of 32-byte blocks (the loop over whole blocks stops
+    at the round's smallest count, the masked loop finishes the rest);
+    every seventh string cut to a multiple of 32 bytes (0 to 256), and the
+    packing shifted so that the strings start at other offsets within
+    their 32-byte blocks.  Both two-byte table forms, against O2."""
+    rng = np.random.default_rng(21)
+    for size, i in ((64, 0), (64, 38)):
+        e = synth.gen_regex(size, 10, synth.LOWER, synth.item_seed(0xE1, size * 100 + i))
+        r = rx.Regex.from_nodes(e)
+        s = synth.gen_strings(e, 6000, 1, 20000, synth.LOWER, synth.item_seed(0xE3, i), p_lang=0.8, log_len=True)
+        pieces = [s.get(j) for j in range(s.n)]
+        for j in range(0, s.n, 7):
+            pieces[j] = pieces[j][:32 * int(rng.integers(0, 9))]
+        packed = synth.pack(pieces)
+        assert max(len(x) for x in pieces) > 4096
+        want = oracle.o2_batch(e, packed.data, packed.offsets)
+        for shift in (0, 5, 17):
+            data = np.concatenate([np.full(shift, ord("z"), np.uint8), packed.data])
+            shifted = synth.Strings(data, packed.offsets + shift, packed.kind, 0)
+            got = run(r, shifted)
+            assert (got == want).all(), (size, i, shift, np.nonzero(got != want)[0][:10])
+
+
 def test_autotune_records_and_is_used():
     w = synth.cfg_streaming(seed=synth.SEED_BASE + 77, n=20000)
     nodes = w.regexes[0]
